@@ -1,0 +1,229 @@
+"""FP64 CPU oracle for the decolorization hot path (test infrastructure).
+
+TEST INFRASTRUCTURE ONLY: the test suite, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py`` may import this package; the product package never
+does.  The arithmetic lives in ``decolor_oracle.c`` (plain IEEE double, built with
+``-O2 -ffp-contract=off``, no fast-math); this module only marshals numpy arrays.
+It shares no code with the CUDA library.
+
+Functions follow the paper: Eq. 1-6 (Sec. II-B) for the luminance, the centred
+sigmoid global curve (Sec. III-B-1) and smoothed local-histogram equalisation
+(Sec. III-B-2).  The readings of what the paper leaves open are listed in the
+header of ``decolor_oracle.c``.  Parity of the tone-mapping parameters is
+unpinned by the paper (it prints none); the closed forms and invariants that pin
+the operators live in ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "decolor_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+DT_U8, DT_F16, DT_F32 = 0, 1, 2
+BETA_R, BETA_K = 0.55, 0.8  # Sec. II-B: "(beta_R = 0.55; beta_k = 0.8)"
+MODE_SIGMOID, MODE_HISTEQ = 0, 1
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_up = ctypes.POINTER(ctypes.c_uint32)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain IEEE double; no contraction, no fast-math)."""
+    with _lock:
+        if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+            tmp = _LIB + ".tmp%d" % os.getpid()
+            subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC",
+                                   "-shared", "-o", tmp, _SRC, "-lm"])
+            os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_LIB)
+        lib.oracle_luminance.restype = ctypes.c_double
+        lib.oracle_luminance.argtypes = [ctypes.c_double] * 5
+        lib.oracle_decolorize.restype = ctypes.c_int
+        lib.oracle_decolorize.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int64, ctypes.c_int32, ctypes.c_double,
+                                          ctypes.c_double, _dp]
+        lib.oracle_log_stats.restype = None
+        lib.oracle_log_stats.argtypes = [_dp, ctypes.c_int64, ctypes.c_double, _dp, _dp, _dp]
+        lib.oracle_gray_hist.restype = None
+        lib.oracle_gray_hist.argtypes = [_dp, ctypes.c_int64, _up]
+        lib.oracle_log_hist.restype = None
+        lib.oracle_log_hist.argtypes = [_dp, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, _up]
+        lib.oracle_tone_sigmoid.restype = None
+        lib.oracle_tone_sigmoid.argtypes = [_dp, ctypes.c_int64, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_double, _dp]
+        lib.oracle_tone_histeq_ldr.restype = None
+        lib.oracle_tone_histeq_ldr.argtypes = [_dp, ctypes.c_int64, _up, _dp]
+        lib.oracle_tone_histeq_hdr.restype = None
+        lib.oracle_tone_histeq_hdr.argtypes = [_dp, ctypes.c_int64, ctypes.c_double,
+                                               ctypes.c_double, ctypes.c_double, _up, _dp]
+        lib.oracle_tone_local.restype = ctypes.c_int
+        lib.oracle_tone_local.argtypes = [_dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                          ctypes.c_double, _dp]
+        _lib = lib
+    return _lib
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def _uptr(a: np.ndarray):
+    return a.ctypes.data_as(_up)
+
+
+def dtype_code(a: np.ndarray) -> int:
+    if a.dtype == np.uint8:
+        return DT_U8
+    if a.dtype == np.float16:
+        return DT_F16
+    if a.dtype == np.float32:
+        return DT_F32
+    raise TypeError("unsupported sample type %s" % a.dtype)
+
+
+# ---------------------------------------------------------------- Eq. 1-6 ----
+def luminance(R: float, G: float, B: float, beta_R: float = BETA_R, beta_k: float = BETA_K) -> float:
+    """Eq. 1-6 for one pixel with channel values in linear units (8-bit codes / 255)."""
+    return _load().oracle_luminance(float(R), float(G), float(B), float(beta_R), float(beta_k))
+
+
+def decolorize(img: np.ndarray, beta_R: float = BETA_R, beta_k: float = BETA_K) -> np.ndarray:
+    """Eq. 1-6 over an interleaved (H, W, 3) image (any row stride); returns float64 (H, W)."""
+    if img.ndim != 3 or img.shape[2] != 3:
+        raise ValueError("expected (H, W, 3)")
+    H, W = img.shape[:2]
+    esz = img.dtype.itemsize
+    if H > 0 and W > 0 and (img.strides[2] != esz or img.strides[1] != 3 * esz):
+        img = np.ascontiguousarray(img)
+    out = np.empty((H, W), dtype=np.float64)
+    if H == 0 or W == 0:
+        return out
+    rc = _load().oracle_decolorize(ctypes.c_void_p(img.ctypes.data), W, H, img.strides[0],
+                                   dtype_code(img), beta_R, beta_k, _dptr(out))
+    if rc != 0:
+        raise ValueError("oracle_decolorize failed (%d)" % rc)
+    return out
+
+
+# ------------------------------------------------------- global statistics ----
+def log_stats(L: np.ndarray, delta: float = 1e-4):
+    """(mu, lmin, lmax) of ln(L + delta) over the plane."""
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    mu, lo, hi = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _load().oracle_log_stats(_dptr(L), L.size, delta, ctypes.byref(mu), ctypes.byref(lo),
+                             ctypes.byref(hi))
+    return mu.value, lo.value, hi.value
+
+
+def gray_hist(L: np.ndarray) -> np.ndarray:
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    h = np.zeros(256, dtype=np.uint32)
+    _load().oracle_gray_hist(_dptr(L), L.size, _uptr(h))
+    return h
+
+
+def log_hist(L: np.ndarray, delta: float, lmin: float, lmax: float) -> np.ndarray:
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    h = np.zeros(256, dtype=np.uint32)
+    _load().oracle_log_hist(_dptr(L), L.size, delta, lmin, lmax, _uptr(h))
+    return h
+
+
+def gray_code(L: np.ndarray) -> np.ndarray:
+    """8-bit code floor(255 L + 1/2) clamped to [0, 255] (used for u8 output too)."""
+    return np.clip(np.floor(255.0 * np.asarray(L, dtype=np.float64) + 0.5), 0, 255).astype(np.uint8)
+
+
+# ------------------------------------------------------------ tone curves ----
+def tonemap_global_plane(L: np.ndarray, ldr: bool, mode: int = MODE_SIGMOID, k: float = 1.0,
+                         delta: float = 1e-4):
+    """Global tone curve of a luminance plane; returns (y, stats dict)."""
+    Lc = np.ascontiguousarray(L, dtype=np.float64)
+    mu, lmin, lmax = log_stats(Lc, delta)
+    y = np.empty_like(Lc)
+    hist = np.zeros(256, dtype=np.uint32)
+    lib = _load()
+    if mode == MODE_SIGMOID:
+        lib.oracle_tone_sigmoid(_dptr(Lc), Lc.size, k, delta, mu, _dptr(y))
+        if ldr:
+            hist = gray_hist(Lc)
+    elif mode == MODE_HISTEQ:
+        if ldr:
+            hist = gray_hist(Lc)
+            lib.oracle_tone_histeq_ldr(_dptr(Lc), Lc.size, _uptr(hist), _dptr(y))
+        else:
+            hist = log_hist(Lc, delta, lmin, lmax)
+            lib.oracle_tone_histeq_hdr(_dptr(Lc), Lc.size, delta, lmin, lmax, _uptr(hist), _dptr(y))
+    else:
+        raise ValueError("unknown global mode %r" % mode)
+    stats = {"mu": mu, "lmin": lmin, "lmax": lmax, "hist": hist, "n": Lc.size}
+    return y.reshape(np.shape(L)), stats
+
+
+def tonemap_local_plane(L: np.ndarray, ldr: bool, block_s: int = 32, radius_blocks: int = 2,
+                        bins: int = 32, alpha: float = 1.0, delta: float = 1e-4) -> np.ndarray:
+    """Smoothed local-histogram equalisation of a luminance plane (float64 (H, W))."""
+    Lc = np.ascontiguousarray(L, dtype=np.float64)
+    H, W = Lc.shape
+    lmin = lmax = 0.0
+    if not ldr:
+        _, lmin, lmax = log_stats(Lc, delta)
+    y = np.empty_like(Lc)
+    rc = _load().oracle_tone_local(_dptr(Lc), W, H, 1 if ldr else 0, block_s, radius_blocks, bins,
+                                   alpha, delta, lmin, lmax, _dptr(y))
+    if rc != 0:
+        raise ValueError("oracle_tone_local failed (%d)" % rc)
+    return y
+
+
+def tonemap_global(img: np.ndarray, mode: int = MODE_SIGMOID, k: float = 1.0, delta: float = 1e-4,
+                   beta_R: float = BETA_R, beta_k: float = BETA_K):
+    """Decolorize then apply the global curve; LDR iff 8-bit input. Returns (y, stats)."""
+    L = decolorize(img, beta_R, beta_k)
+    return tonemap_global_plane(L, img.dtype == np.uint8, mode, k, delta)
+
+
+def tonemap_local(img: np.ndarray, block_s: int = 32, radius_blocks: int = 2, bins: int = 32,
+                  alpha: float = 1.0, delta: float = 1e-4, beta_R: float = BETA_R,
+                  beta_k: float = BETA_K) -> np.ndarray:
+    """Decolorize then apply the local operator; LDR iff 8-bit input."""
+    L = decolorize(img, beta_R, beta_k)
+    return tonemap_local_plane(L, img.dtype == np.uint8, block_s, radius_blocks, bins, alpha, delta)
+
+
+def u8_boundary_mask(y: np.ndarray, eps: float = 1e-5) -> np.ndarray:
+    """True where y lies within eps of an 8-bit rounding boundary (k + 1/2)/255."""
+    t = 255.0 * np.asarray(y, dtype=np.float64)
+    frac = t - np.floor(t)
+    return np.abs(frac - 0.5) < 255.0 * eps
+
+
+def f16_boundary_mask(y: np.ndarray, eps: float = 1e-5) -> np.ndarray:
+    """True where y lies within eps (relative) of a binary16 rounding midpoint."""
+    y = np.asarray(y, dtype=np.float64)
+    h = y.astype(np.float16).astype(np.float64)
+    up = np.nextafter(y.astype(np.float16), np.float16(np.inf)).astype(np.float64)
+    dn = np.nextafter(y.astype(np.float16), np.float16(-np.inf)).astype(np.float64)
+    mid_up = 0.5 * (h + up)
+    mid_dn = 0.5 * (h + dn)
+    tol = eps * np.maximum(1.0, np.abs(y))
+    return (np.abs(y - mid_up) < tol) | (np.abs(y - mid_dn) < tol)
