@@ -1,0 +1,223 @@
+/*
+ * decolor.h - C ABI of the GB300 colour-temperature decolorization library
+ * (libdecolor.so, built for sm_103a).
+ *
+ * The library computes the luminance of Eq. 1-6 of Ambalathankandy, Ou and Ikebe,
+ * "A color temperature-based high-speed decolorization: an empirical approach for
+ * tone mapping applications" (arXiv 2108.13656), Sec. II-B, and fuses it with the
+ * global tone curve of Sec. III-B-1 and the smoothed local-histogram-equalisation
+ * tone mapping of Sec. III-B-2.  Every call is one persistent CUDA launch over a
+ * (possibly ragged) batch of images.
+ *
+ * Conventions shared by every entry point
+ *  - Images are interleaved RGB (R, G, B per pixel, no padding between pixels),
+ *    row-major, with an arbitrary row stride in bytes.  Samples are 8-bit codes
+ *    (DC_U8, read as code/255, no linearisation), IEEE binary16 (DC_F16) or
+ *    binary32 (DC_F32) linear values.  Negative samples are read as 0.
+ *  - 8-bit input is "LDR"; binary16/binary32 input is "HDR".  The tone-mapping
+ *    statistics use L for LDR and ln(L + delta) for HDR (see each call).
+ *  - Outputs are one channel of the same width and height: DC_U8 (the value y in
+ *    [0,1] rounded to floor(255 y + 1/2), clamped), DC_F16 (round to nearest even)
+ *    or DC_F32.
+ *  - All pointers inside dc_image_in / dc_image_out, `stats` and `ws` are DEVICE
+ *    pointers owned by the caller.  The descriptor arrays `in` and `out` and the
+ *    parameter structs are HOST memory, read during the call only.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream).  They never allocate device memory and never synchronise.  Input must
+ *    not overlap output.  Two calls that share a workspace must be ordered (same
+ *    stream or an event between them).
+ *  - Return value: DC_OK or a DC_ERR_* code; nothing is enqueued when a call
+ *    returns an error.  Errors found on the device while the launch runs (a
+ *    dependency wait that ran out of time) are recorded in the workspace and read
+ *    with dc_query_status.
+ *  - Vector path: when an image's data pointers and row strides are 16-byte
+ *    aligned, pixels move in 16-byte vectors; otherwise the image takes a scalar
+ *    path with the same results.
+ *  - Limits: width, height >= 1; width * height <= 2^28 per image; at most
+ *    DC_MAX_BATCH images per call.
+ */
+#ifndef DECOLOR_H
+#define DECOLOR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define DC_API __attribute__((visibility("default")))
+#else
+#define DC_API
+#endif
+
+/* ---- status codes ---- */
+#define DC_OK 0
+#define DC_ERR_INVALID_ARG 1       /* a size, stride, pointer or parameter is out of range */
+#define DC_ERR_UNSUPPORTED_DTYPE 2 /* a dtype is not DC_U8 / DC_F16 / DC_F32 */
+#define DC_ERR_WORKSPACE 3         /* ws is NULL, misaligned (256 B) or smaller than needed */
+#define DC_ERR_CUDA 4              /* a CUDA runtime call failed (launch, memset, attribute) */
+#define DC_ERR_TIMEOUT 5           /* device side: a dependency wait ran past its limit */
+#define DC_ERR_TOO_MANY 6          /* more than DC_MAX_BATCH images */
+
+/* ---- sample types ---- */
+#define DC_U8 0
+#define DC_F16 1
+#define DC_F32 2
+
+/* ---- operations (for dc_workspace_bytes and the tuning table) ---- */
+#define DC_OP_DECOLORIZE 0
+#define DC_OP_GLOBAL 1
+#define DC_OP_LOCAL 2
+
+/* ---- global curve modes ---- */
+#define DC_SIGMOID 0 /* centred sigmoid (Sec. III-B-1) */
+#define DC_HISTEQ 1  /* histogram equalisation (global analogue of Sec. III-B-2) */
+
+#define DC_MAX_BATCH 4096
+#define DC_MAX_BINS 32
+
+typedef struct {
+    const void* data;     /* device pointer to the first pixel of the first row */
+    int32_t width;        /* pixels per row, >= 1 */
+    int32_t height;       /* rows, >= 1 */
+    int64_t stride_bytes; /* bytes between rows, >= 3 * width * sample size */
+    int32_t dtype;        /* DC_U8, DC_F16 or DC_F32 */
+    int32_t reserved;     /* must be 0 */
+} dc_image_in;
+
+typedef struct {
+    void* data;           /* device pointer, width x height samples of `dtype` */
+    int64_t stride_bytes; /* bytes between rows, >= width * sample size */
+    int32_t dtype;        /* DC_U8, DC_F16 or DC_F32 */
+    int32_t reserved;     /* must be 0 */
+} dc_image_out;
+
+/* Eq. 3 and Eq. 6 weights; the paper uses beta_r = 0.55 and beta_k = 0.8
+ * (Sec. II-B).  The paper states 0.5 < beta < 1; the library accepts [0, 1]. */
+typedef struct {
+    float beta_r;
+    float beta_k;
+} dc_decolor_params;
+
+/* Global curve (Sec. III-B-1 names it a centred sigmoid and prints no formula):
+ *  DC_SIGMOID: y = 1 / (1 + exp(-gain_k * (ln(L + delta) - mu))), mu = mean of
+ *              ln(L + delta) over the image, so y = 1/2 at the log-mean.
+ *  DC_HISTEQ : LDR: y = (number of pixels with gray code <= q) / N, q = the 8-bit
+ *              gray code floor(255 L + 1/2);
+ *              HDR: u = (ln(L+delta) - lmin) / (lmax - lmin) (1/2 when lmax = lmin),
+ *              256 bins over u, y = piecewise-linear cumulative histogram at u.
+ * Defaults: gain_k = 1, delta = 1e-4.  gain_k >= 0, delta > 0 and finite. */
+typedef struct {
+    int32_t mode;
+    float gain_k;
+    float delta;
+    int32_t reserved; /* must be 0 */
+} dc_global_params;
+
+/* Local operator: smoothed local-histogram equalisation (Sec. III-B-2; the paper
+ * cites Kass and Solomon's smoothed local histogram filters and gives no formula).
+ * u = L (LDR) or the normalised log luminance as in DC_HISTEQ (HDR).  Each pixel
+ * adds tent weights to the two nearest of `bins` bin centres (j + 1/2)/bins;
+ * histograms are summed over block_s x block_s blocks and then over a
+ * (2 radius_blocks + 1)^2 window of blocks, truncated at the image border; each
+ * block's tone curve is its window's cumulative histogram with every bin's mass
+ * spread uniformly over the bin; a pixel's value is the bilinear blend of the four
+ * nearest block curves (nominal block centres, clamped at the border) evaluated at
+ * its own u, then y = alpha * F + (1 - alpha) * u.
+ * Defaults: block_s = 32, radius_blocks = 2, bins = 32, alpha = 1, delta = 1e-4.
+ * Limits: 1 <= block_s <= 256, 0 <= radius_blocks <= 16, 2 <= bins <= DC_MAX_BINS,
+ * alpha in [0, 1]. */
+typedef struct {
+    int32_t block_s;
+    int32_t radius_blocks;
+    int32_t bins;
+    float alpha;
+    float delta;
+    int32_t reserved; /* must be 0 */
+} dc_local_params;
+
+/* Per-image statistics of the global pass (device memory, written by the call). */
+typedef struct {
+    float mu;             /* mean of ln(L + delta) */
+    float logmin;         /* min of ln(L + delta) */
+    float logmax;         /* max of ln(L + delta) */
+    float reserved0;
+    int64_t logsum_fixed; /* exact sum over pixels of ln(L + delta) in units of 2^-20,
+                             each 16/8/4-pixel vector group rounded once */
+    int64_t npix;         /* width * height */
+    uint32_t hist[256];   /* LDR: 8-bit gray-code histogram (always filled);
+                             HDR: the DC_HISTEQ u-bin histogram (zeros in DC_SIGMOID) */
+} dc_global_stats;
+
+/* Kernel launch shape used for one (operation, input sample type): threads per CTA
+ * (128, 256 or 512), tile rows and columns (columns a multiple of 16; for the local
+ * operator the tile is block_s rows high and columns are rounded up to a multiple of
+ * block_s) and resident CTAs per SM (0 = as many as fit).  None of these change
+ * results: every reduction in the library is exact integer arithmetic. */
+typedef struct {
+    int32_t threads;
+    int32_t tile_rows;
+    int32_t tile_cols;
+    int32_t ctas_per_sm;
+} dc_tuning;
+
+/* Eq. 1-6 (Sec. II-B): out = L per pixel.  ws: see dc_workspace_bytes. */
+DC_API int dc_decolorize(const dc_image_in* in, const dc_image_out* out, int32_t n,
+                         const dc_decolor_params* params, void* ws, size_t ws_bytes, void* stream);
+
+/* Eq. 1-6 then the global curve of Sec. III-B-1 (dc_global_params).  `stats` is
+ * NULL or a device array of n dc_global_stats, written in input order. */
+DC_API int dc_decolorize_tonemap_global(const dc_image_in* in, const dc_image_out* out, int32_t n,
+                                        const dc_decolor_params* params,
+                                        const dc_global_params* gparams, dc_global_stats* stats,
+                                        void* ws, size_t ws_bytes, void* stream);
+
+/* Eq. 1-6 then the local operator of Sec. III-B-2 (dc_local_params). */
+DC_API int dc_decolorize_tonemap_local(const dc_image_in* in, const dc_image_out* out, int32_t n,
+                                       const dc_decolor_params* params,
+                                       const dc_local_params* lparams, void* ws, size_t ws_bytes,
+                                       void* stream);
+
+/* Workspace bytes a call of `op` (DC_OP_*) needs for these inputs; op_params is
+ * NULL (DC_OP_DECOLORIZE, DC_OP_GLOBAL) or a dc_local_params* (DC_OP_LOCAL).
+ * Returns 0 when the arguments are invalid.  The workspace must be 256-byte
+ * aligned; its contents need no initialisation (each call resets what it uses). */
+DC_API size_t dc_workspace_bytes(int32_t op, const dc_image_in* in, int32_t n,
+                                 const void* op_params);
+
+/* Synchronises `stream`, then reads the device-side error word that the last call
+ * using workspace `ws` left there: DC_OK or DC_ERR_TIMEOUT.  Returns DC_ERR_CUDA if
+ * the copy fails. */
+DC_API int dc_query_status(const void* ws, void* stream);
+
+/* Static English description of a status code. */
+DC_API const char* dc_status_string(int status);
+
+/* Launch-shape table used by later calls (per operation and input sample type);
+ * used by the autotuner.  Returns DC_ERR_INVALID_ARG for values out of range. */
+DC_API int dc_set_tuning(int32_t op, int32_t in_dtype, const dc_tuning* t);
+DC_API int dc_get_tuning(int32_t op, int32_t in_dtype, dc_tuning* t);
+
+/* Upper limit, in nanoseconds, of every device-side dependency wait in later calls
+ * (default 2e9).  A wait that runs past it records DC_ERR_TIMEOUT and the launch
+ * drains without writing further output.  Values below 1000 are rejected. */
+DC_API int dc_set_wait_timeout_ns(uint64_t ns);
+
+/* Test hook for the timeout path: when nonzero, later calls never publish the
+ * completion of their first pass, so every dependent wait runs out (bounded by the
+ * timeout above).  Default 0. */
+DC_API int dc_debug_withhold_ready(int32_t on);
+
+/* Number of kernels the last successful call on this thread enqueued. */
+DC_API int dc_last_launch_count(void);
+
+/* ABI version (major * 100 + minor). */
+DC_API int dc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DECOLOR_H */

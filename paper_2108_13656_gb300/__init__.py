@@ -1,1 +1,39 @@
-"""GB300-native colour-temperature decolorization (placeholder, filled in below)."""
+"""GB300-native colour-temperature decolorization with fused tone mapping.
+
+Implements the luminance of Eq. 1-6 (Sec. II-B) of arXiv 2108.13656 and the global
+(Sec. III-B-1) and local (Sec. III-B-2) tone-mapping passes applied to it, as
+hand-written CUDA kernels for sm_103a behind the C ABI of include/decolor.h.  This
+package is the Python binding (argument marshalling only) plus the seeded synthetic
+input generators; PyTorch provides device memory and streams.  No CPU fallback
+exists: calls raise when libdecolor.so cannot be loaded.
+"""
+from ._abi import (  # noqa: F401
+    BETA_K,
+    BETA_R,
+    DC_F16,
+    DC_F32,
+    DC_HISTEQ,
+    DC_OP_DECOLORIZE,
+    DC_OP_GLOBAL,
+    DC_OP_LOCAL,
+    DC_SIGMOID,
+    DC_U8,
+    STATS_BYTES,
+    DcError,
+    Workspace,
+    debug_withhold_ready,
+    decolorize,
+    decolorize_tonemap_global,
+    decolorize_tonemap_local,
+    get_tuning,
+    last_launch_count,
+    library_path,
+    load,
+    local_params,
+    parse_stats,
+    query_status,
+    set_tuning,
+    set_wait_timeout_ns,
+    status_string,
+    workspace_bytes,
+)

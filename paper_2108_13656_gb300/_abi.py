@@ -1,0 +1,332 @@
+"""Thin ctypes binding of include/decolor.h (argument marshalling only).
+
+Every step of the hot path runs inside libdecolor.so; this module converts torch
+tensors into the ABI's plain descriptors (device pointers, sizes, strides, sample
+types) and passes torch's current CUDA stream.  There is no fallback: when the
+library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build_lib
+
+DC_OK, DC_ERR_INVALID_ARG, DC_ERR_UNSUPPORTED_DTYPE, DC_ERR_WORKSPACE = 0, 1, 2, 3
+DC_ERR_CUDA, DC_ERR_TIMEOUT, DC_ERR_TOO_MANY = 4, 5, 6
+DC_U8, DC_F16, DC_F32 = 0, 1, 2
+DC_OP_DECOLORIZE, DC_OP_GLOBAL, DC_OP_LOCAL = 0, 1, 2
+DC_SIGMOID, DC_HISTEQ = 0, 1
+BETA_R, BETA_K = 0.55, 0.8
+
+
+class DcError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__("%s failed: %s (status %d)" % (what, status_string(status), status))
+        self.status = status
+
+
+class dc_image_in(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("stride_bytes", ctypes.c_int64), ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class dc_image_out(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("stride_bytes", ctypes.c_int64), ("dtype", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
+class dc_decolor_params(ctypes.Structure):
+    _fields_ = [("beta_r", ctypes.c_float), ("beta_k", ctypes.c_float)]
+
+
+class dc_global_params(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("gain_k", ctypes.c_float), ("delta", ctypes.c_float),
+                ("reserved", ctypes.c_int32)]
+
+
+class dc_local_params(ctypes.Structure):
+    _fields_ = [("block_s", ctypes.c_int32), ("radius_blocks", ctypes.c_int32), ("bins", ctypes.c_int32),
+                ("alpha", ctypes.c_float), ("delta", ctypes.c_float), ("reserved", ctypes.c_int32)]
+
+
+class dc_tuning(ctypes.Structure):
+    _fields_ = [("threads", ctypes.c_int32), ("tile_rows", ctypes.c_int32), ("tile_cols", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32)]
+
+
+STATS_BYTES = 4 * 4 + 8 + 8 + 256 * 4  # sizeof(dc_global_stats)
+
+# Every exported symbol of include/decolor.h with its ctypes signature.
+_SIGS = {
+    "dc_decolorize": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p,
+                                     ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "dc_decolorize_tonemap_global": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                    ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "dc_decolorize_tonemap_local": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                   ctypes.c_size_t, ctypes.c_void_p]),
+    "dc_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "dc_query_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
+    "dc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "dc_set_tuning": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
+    "dc_get_tuning": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
+    "dc_set_wait_timeout_ns": (ctypes.c_int, [ctypes.c_uint64]),
+    "dc_debug_withhold_ready": (ctypes.c_int, [ctypes.c_int32]),
+    "dc_last_launch_count": (ctypes.c_int, []),
+    "dc_version": (ctypes.c_int, []),
+}
+
+_lib = None
+_lib_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return build_lib.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libdecolor.so (building it first when allowed); raises when unavailable."""
+    global _lib
+    with _lib_lock:
+        if _lib is not None:
+            return _lib
+        path = build_lib.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError("libdecolor.so is not built (run __graft_entry__.build())")
+            build_lib.build()
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def status_string(status: int) -> str:
+    try:
+        return load(build_if_missing=False).dc_status_string(int(status)).decode()
+    except Exception:  # library not loadable: still give a message
+        return "status %d" % status
+
+
+# ------------------------------------------------------------ descriptors ----
+def _torch():
+    import torch
+    return torch
+
+
+def dtype_code(t) -> int:
+    torch = _torch()
+    if t.dtype == torch.uint8:
+        return DC_U8
+    if t.dtype == torch.float16:
+        return DC_F16
+    if t.dtype == torch.float32:
+        return DC_F32
+    raise TypeError("unsupported sample type %s (uint8, float16 or float32)" % t.dtype)
+
+
+def _in_desc(t) -> dc_image_in:
+    if t.dim() != 3 or t.shape[2] != 3:
+        raise ValueError("input must be (H, W, 3) interleaved RGB, got %s" % (tuple(t.shape),))
+    if t.stride(2) != 1 or t.stride(1) != 3:
+        raise ValueError("input pixels must be interleaved (channel stride 1, pixel stride 3)")
+    d = dc_image_in()
+    d.data = t.data_ptr()
+    d.height, d.width = int(t.shape[0]), int(t.shape[1])
+    d.stride_bytes = int(t.stride(0)) * t.element_size()
+    d.dtype = dtype_code(t)
+    d.reserved = 0
+    return d
+
+
+def _out_desc(t) -> dc_image_out:
+    if t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("output must be a (H, W) plane with unit column stride")
+    d = dc_image_out()
+    d.data = t.data_ptr()
+    d.stride_bytes = int(t.stride(0)) * t.element_size()
+    d.dtype = dtype_code(t)
+    d.reserved = 0
+    return d
+
+
+def _arrays(inputs, outputs):
+    if len(inputs) == 0:
+        raise ValueError("empty batch")
+    ins = (dc_image_in * len(inputs))(*[_in_desc(t) for t in inputs])
+    outs = None
+    if outputs is not None:
+        if len(outputs) != len(inputs):
+            raise ValueError("inputs and outputs differ in length")
+        for a, b in zip(inputs, outputs):
+            if tuple(b.shape) != (a.shape[0], a.shape[1]):
+                raise ValueError("output shape %s does not match input %s" % (tuple(b.shape), tuple(a.shape)))
+        outs = (dc_image_out * len(outputs))(*[_out_desc(t) for t in outputs])
+    return ins, outs
+
+
+def _as_list(x):
+    return list(x) if isinstance(x, (list, tuple)) else [x]
+
+
+def _stream_handle(stream):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Workspace:
+    """Device workspace owned by torch's allocator, grown on demand (256-byte aligned)."""
+
+    def __init__(self, device=None):
+        self.device = device
+        self.buf = None
+
+    def get(self, nbytes: int):
+        torch = _torch()
+        nbytes = max(int(nbytes), 256)
+        if self.buf is None or self.buf.numel() < nbytes:
+            self.buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device or "cuda")
+        ptr = self.buf.data_ptr()
+        assert ptr % 256 == 0
+        return ptr, self.buf.numel()
+
+
+_default_ws: dict = {}
+
+
+def _workspace(op, ins, n, lp, ws):
+    lib = load()
+    need = lib.dc_workspace_bytes(op, ins, n, ctypes.byref(lp) if lp is not None else None)
+    if need == 0:
+        raise DcError(DC_ERR_INVALID_ARG, "dc_workspace_bytes")
+    if ws is None:
+        torch = _torch()
+        dev = torch.cuda.current_device()
+        ws = _default_ws.setdefault(dev, Workspace(device="cuda:%d" % dev))
+    ptr, size = ws.get(need)
+    return ptr, size, ws
+
+
+# ------------------------------------------------------------------ calls ----
+def decolorize(inputs, outputs, beta_r: float = BETA_R, beta_k: float = BETA_K, workspace=None,
+               stream=None):
+    """Eq. 1-6 over a (ragged) batch: outputs[i] = L(inputs[i])."""
+    inputs, outputs = _as_list(inputs), _as_list(outputs)
+    ins, outs = _arrays(inputs, outputs)
+    p = dc_decolor_params(beta_r, beta_k)
+    ptr, size, _ = _workspace(DC_OP_DECOLORIZE, ins, len(inputs), None, workspace)
+    rc = load().dc_decolorize(ins, outs, len(inputs), ctypes.byref(p), ctypes.c_void_p(ptr), size,
+                              _stream_handle(stream))
+    if rc != DC_OK:
+        raise DcError(rc, "dc_decolorize")
+    return outputs
+
+
+def decolorize_tonemap_global(inputs, outputs, mode: str | int = "sigmoid", gain_k: float = 1.0,
+                              delta: float = 1e-4, stats=None, beta_r: float = BETA_R,
+                              beta_k: float = BETA_K, workspace=None, stream=None):
+    """Eq. 1-6 then the global curve; `stats` is None or a uint8 CUDA tensor of n*STATS_BYTES."""
+    inputs, outputs = _as_list(inputs), _as_list(outputs)
+    ins, outs = _arrays(inputs, outputs)
+    m = {"sigmoid": DC_SIGMOID, "histeq": DC_HISTEQ}.get(mode, mode)
+    p = dc_decolor_params(beta_r, beta_k)
+    g = dc_global_params(int(m), gain_k, delta, 0)
+    sp = None
+    if stats is not None:
+        if stats.numel() * stats.element_size() < STATS_BYTES * len(inputs) or not stats.is_cuda:
+            raise ValueError("stats buffer too small")
+        sp = ctypes.c_void_p(stats.data_ptr())
+    ptr, size, _ = _workspace(DC_OP_GLOBAL, ins, len(inputs), None, workspace)
+    rc = load().dc_decolorize_tonemap_global(ins, outs, len(inputs), ctypes.byref(p), ctypes.byref(g), sp,
+                                             ctypes.c_void_p(ptr), size, _stream_handle(stream))
+    if rc != DC_OK:
+        raise DcError(rc, "dc_decolorize_tonemap_global")
+    return outputs
+
+
+def local_params(block_s: int = 32, radius_blocks: int = 2, bins: int = 32, alpha: float = 1.0,
+                 delta: float = 1e-4) -> dc_local_params:
+    return dc_local_params(block_s, radius_blocks, bins, alpha, delta, 0)
+
+
+def decolorize_tonemap_local(inputs, outputs, block_s: int = 32, radius_blocks: int = 2, bins: int = 32,
+                             alpha: float = 1.0, delta: float = 1e-4, beta_r: float = BETA_R,
+                             beta_k: float = BETA_K, workspace=None, stream=None):
+    """Eq. 1-6 then smoothed local-histogram equalisation."""
+    inputs, outputs = _as_list(inputs), _as_list(outputs)
+    ins, outs = _arrays(inputs, outputs)
+    p = dc_decolor_params(beta_r, beta_k)
+    lp = local_params(block_s, radius_blocks, bins, alpha, delta)
+    ptr, size, _ = _workspace(DC_OP_LOCAL, ins, len(inputs), lp, workspace)
+    rc = load().dc_decolorize_tonemap_local(ins, outs, len(inputs), ctypes.byref(p), ctypes.byref(lp),
+                                            ctypes.c_void_p(ptr), size, _stream_handle(stream))
+    if rc != DC_OK:
+        raise DcError(rc, "dc_decolorize_tonemap_local")
+    return outputs
+
+
+def workspace_bytes(op: int, inputs, lparams: dc_local_params | None = None) -> int:
+    inputs = _as_list(inputs)
+    ins, _ = _arrays(inputs, None)
+    return int(load().dc_workspace_bytes(op, ins, len(inputs), ctypes.byref(lparams) if lparams else None))
+
+
+def query_status(workspace=None, stream=None) -> int:
+    torch = _torch()
+    if workspace is None:
+        workspace = _default_ws.get(torch.cuda.current_device())
+    if workspace is None or workspace.buf is None:
+        return DC_OK
+    return int(load().dc_query_status(ctypes.c_void_p(workspace.buf.data_ptr()), _stream_handle(stream)))
+
+
+def set_tuning(op: int, in_dtype: int, threads: int, tile_rows: int, tile_cols: int, ctas_per_sm: int = 0):
+    t = dc_tuning(threads, tile_rows, tile_cols, ctas_per_sm)
+    rc = load().dc_set_tuning(op, in_dtype, ctypes.byref(t))
+    if rc != DC_OK:
+        raise DcError(rc, "dc_set_tuning")
+
+
+def get_tuning(op: int, in_dtype: int) -> tuple[int, int, int, int]:
+    t = dc_tuning()
+    rc = load().dc_get_tuning(op, in_dtype, ctypes.byref(t))
+    if rc != DC_OK:
+        raise DcError(rc, "dc_get_tuning")
+    return (t.threads, t.tile_rows, t.tile_cols, t.ctas_per_sm)
+
+
+def set_wait_timeout_ns(ns: int):
+    rc = load().dc_set_wait_timeout_ns(int(ns))
+    if rc != DC_OK:
+        raise DcError(rc, "dc_set_wait_timeout_ns")
+
+
+def debug_withhold_ready(on: bool):
+    load().dc_debug_withhold_ready(1 if on else 0)
+
+
+def last_launch_count() -> int:
+    return int(load().dc_last_launch_count())
+
+
+def parse_stats(buf, n: int) -> list[dict]:
+    """Decode n dc_global_stats records from a uint8 tensor or bytes."""
+    raw = bytes(buf.cpu().numpy().tobytes()) if hasattr(buf, "cpu") else bytes(buf)
+    out = []
+    for i in range(n):
+        rec = raw[i * STATS_BYTES:(i + 1) * STATS_BYTES]
+        f = np.frombuffer(rec[:16], dtype=np.float32)
+        q = np.frombuffer(rec[16:32], dtype=np.int64)
+        h = np.frombuffer(rec[32:], dtype=np.uint32).copy()
+        out.append({"mu": float(f[0]), "lmin": float(f[1]), "lmax": float(f[2]), "logsum_fixed": int(q[0]),
+                    "npix": int(q[1]), "hist": h})
+    return out

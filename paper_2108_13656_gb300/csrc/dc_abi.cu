@@ -1,0 +1,505 @@
+// Host side of the C ABI declared in include/decolor.h: argument validation,
+// workspace layout, the tile schedule (segment table) and the launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "dc_internal.h"
+
+using namespace dc;
+
+namespace {
+
+constexpr int kOpkDecolor = 0, kOpkGlobal = 1, kOpkLocal = 2;
+constexpr int64_t kHeaderBytes = 256;
+constexpr int64_t kMaxPixels = int64_t(1) << 28;
+constexpr int kMaxLocalSide = 1 << 16;
+constexpr int kLocMaxBlocksX = 64;
+
+std::mutex g_mu;
+dc_tuning g_tune[3][3] = {
+    {{256, 4, 4096, 0}, {256, 4, 4096, 0}, {256, 4, 4096, 0}},
+    {{256, 4, 4096, 0}, {256, 4, 4096, 0}, {256, 4, 4096, 0}},
+    {{256, 32, 256, 0}, {256, 32, 256, 0}, {256, 32, 256, 0}},
+};
+unsigned long long g_timeout_ns = 2000000000ull;
+int g_withhold = 0;
+thread_local int g_last_launches = 0;
+
+int esz(int dt) { return dt == DC_U8 ? 1 : (dt == DC_F16 ? 2 : 4); }
+bool dt_ok(int dt) { return dt == DC_U8 || dt == DC_F16 || dt == DC_F32; }
+bool finite_in(float v, float lo, float hi) { return std::isfinite(v) && v >= lo && v <= hi; }
+bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+struct OpArgs {
+    int opk;
+    const dc_global_params* g;
+    const dc_local_params* l;
+    dc_global_stats* stats;
+};
+
+int validate_image(const dc_image_in& in, const dc_image_out* out, bool local)
+{
+    if (!dt_ok(in.dtype)) return DC_ERR_UNSUPPORTED_DTYPE;
+    if (in.reserved != 0 || in.width < 1 || in.height < 1) return DC_ERR_INVALID_ARG;
+    if ((int64_t)in.width * in.height > kMaxPixels) return DC_ERR_INVALID_ARG;
+    if (local && (in.width > kMaxLocalSide || in.height > kMaxLocalSide)) return DC_ERR_INVALID_ARG;
+    const int ie = esz(in.dtype);
+    if (in.data == nullptr || in.stride_bytes < (int64_t)3 * in.width * ie) return DC_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(in.data) % ie) != 0 || (in.stride_bytes % ie) != 0) return DC_ERR_INVALID_ARG;
+    if (out) {
+        if (!dt_ok(out->dtype)) return DC_ERR_UNSUPPORTED_DTYPE;
+        if (out->reserved != 0 || out->data == nullptr) return DC_ERR_INVALID_ARG;
+        const int oe = esz(out->dtype);
+        if (out->stride_bytes < (int64_t)in.width * oe) return DC_ERR_INVALID_ARG;
+        if ((reinterpret_cast<uintptr_t>(out->data) % oe) != 0 || (out->stride_bytes % oe) != 0)
+            return DC_ERR_INVALID_ARG;
+    }
+    return DC_OK;
+}
+
+int validate_params(const dc_decolor_params* p, const OpArgs& op)
+{
+    if (!p || !finite_in(p->beta_r, 0.f, 1.f) || !finite_in(p->beta_k, 0.f, 1.f)) return DC_ERR_INVALID_ARG;
+    if (op.opk == kOpkGlobal) {
+        const dc_global_params* g = op.g;
+        if (!g || (g->mode != DC_SIGMOID && g->mode != DC_HISTEQ) || g->reserved != 0) return DC_ERR_INVALID_ARG;
+        if (!finite_in(g->gain_k, 0.f, 1e6f) || !std::isfinite(g->delta) || !(g->delta > 0.f)) return DC_ERR_INVALID_ARG;
+    } else if (op.opk == kOpkLocal) {
+        const dc_local_params* l = op.l;
+        if (!l || l->reserved != 0) return DC_ERR_INVALID_ARG;
+        if (l->block_s < 1 || l->block_s > 256 || l->radius_blocks < 0 || l->radius_blocks > 16) return DC_ERR_INVALID_ARG;
+        if (l->bins < 2 || l->bins > DC_MAX_BINS || !finite_in(l->alpha, 0.f, 1.f)) return DC_ERR_INVALID_ARG;
+        if (!std::isfinite(l->delta) || !(l->delta > 0.f)) return DC_ERR_INVALID_ARG;
+    }
+    return DC_OK;
+}
+
+int gcd_i(int a, int b) { return b == 0 ? a : gcd_i(b, a % b); }
+
+// Local tile width: a multiple of lcm(block_s, 16), at most kLocMaxBlocksX blocks.
+int local_tile_cols(int s, int want)
+{
+    const int l = s / gcd_i(s, 16) * 16;
+    int m = std::max(1, want / l);
+    while (m > 1 && (l * m) / s > kLocMaxBlocksX) --m;
+    return l * m;
+}
+
+struct Geometry {
+    DcImage im;
+    int tiles[kMaxPhases];
+    int64_t local_bytes;
+};
+
+struct LaunchPlan {
+    int in_dt;
+    std::vector<int> idx;  // positions in the caller's arrays
+};
+
+// Phase chain of an operation for one input class.
+int phase_list(const OpArgs& op, bool ldr, int32_t* kinds)
+{
+    if (op.opk == kOpkDecolor) {
+        kinds[0] = PK_DECOLOR;
+        return 1;
+    }
+    if (op.opk == kOpkGlobal) {
+        kinds[0] = PK_STATS;
+        if (op.g->mode == DC_HISTEQ && !ldr) {
+            kinds[1] = PK_LOGHIST;
+            kinds[2] = PK_APPLY_G;
+            return 3;
+        }
+        kinds[1] = PK_APPLY_G;
+        return 2;
+    }
+    int n = 0;
+    if (!ldr) kinds[n++] = PK_STATS;
+    kinds[n++] = PK_BLOCKH;
+    kinds[n++] = PK_CDF;
+    kinds[n++] = PK_APPLY_L;
+    return n;
+}
+
+void make_geometry(const dc_image_in& in, const dc_image_out& out, const OpArgs& op, const dc_tuning& tu,
+                   int n_phase, const int32_t* kinds, Geometry& g, int tile_rows, int tile_cols, int loc_cols)
+{
+    DcImage& im = g.im;
+    std::memset(&im, 0, sizeof(im));
+    const int ie = esz(in.dtype), oe = esz(out.dtype);
+    const int W = in.width, H = in.height;
+    im.in = static_cast<const uint8_t*>(in.data);
+    im.out = static_cast<uint8_t*>(out.data);
+    im.out_dt = out.dtype;
+    im.prow = H;
+    im.pcol = W;
+    const bool dense = in.stride_bytes == (int64_t)3 * W * ie && out.stride_bytes == (int64_t)W * oe;
+    if (op.opk != kOpkLocal && dense) {
+        im.rows = 1;
+        im.cols = W * H;
+        im.in_stride = (int64_t)3 * W * H * ie;
+        im.out_stride = (int64_t)W * H * oe;
+    } else {
+        im.rows = H;
+        im.cols = W;
+        im.in_stride = in.stride_bytes;
+        im.out_stride = out.stride_bytes;
+    }
+    bool vec = al16(in.data) && al16(out.data);
+    if (im.rows > 1) vec = vec && (in.stride_bytes % 16 == 0) && (out.stride_bytes % 16 == 0);
+    im.flags = vec ? IF_VEC : 0u;
+    if (op.opk != kOpkDecolor && in.dtype != DC_U8 && out.dtype == DC_F32) im.flags |= IF_LPLANE;
+    im.tiles_x = (im.cols + tile_cols - 1) / tile_cols;
+    const int tiles_y = (im.rows + tile_rows - 1) / tile_rows;
+    g.local_bytes = 0;
+    if (op.opk == kOpkLocal) {
+        const int s = op.l->block_s, B = op.l->bins;
+        im.Hb = (H + s - 1) / s;
+        im.Wb = (W + s - 1) / s;
+        im.tiles_x_loc = (W + loc_cols - 1) / loc_cols;
+        const int64_t hist_bytes = align_up((int64_t)im.Hb * im.Wb * B * 8, 256);
+        const int64_t cdf_bytes = align_up((int64_t)im.Hb * im.Wb * (B + 1) * 4, 256);
+        g.local_bytes = hist_bytes + cdf_bytes;
+    }
+    (void)tu;
+    for (int p = 0; p < n_phase; ++p) {
+        if (op.opk == kOpkLocal)
+            g.tiles[p] = kinds[p] == PK_CDF ? im.Hb : im.Hb * im.tiles_x_loc;
+        else
+            g.tiles[p] = tiles_y * im.tiles_x;
+    }
+}
+
+template <int CAP>
+int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::vector<int>& idx,
+                     const dc_decolor_params* p, const OpArgs& op, uint8_t* ws, bool first, int64_t* need,
+                     void* stream, bool launch)
+{
+    const int n = (int)idx.size();
+    const int in_dt = in[idx[0]].dtype;
+    const bool ldr = in_dt == DC_U8;
+    dc_tuning tu;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        tu = g_tune[op.opk][in_dt];
+    }
+    DcBatch<CAP>* b = new (std::nothrow) DcBatch<CAP>();
+    if (!b) return DC_ERR_INVALID_ARG;
+    std::memset(b, 0, sizeof(DcBatch<CAP>));
+    b->n_phase = phase_list(op, ldr, b->phase_kind);
+    b->tile_rows = std::max(1, tu.tile_rows);
+    b->tile_cols = std::max(16, (tu.tile_cols + 15) / 16 * 16);
+    b->loc_tile_cols = op.opk == kOpkLocal ? local_tile_cols(op.l->block_s, tu.tile_cols) : 0;
+    b->beta_r = p->beta_r;
+    b->beta_k = p->beta_k;
+    b->ldr = ldr ? 1 : 0;
+    b->withhold_ready = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        b->timeout_ns = g_timeout_ns;
+        b->withhold_ready = g_withhold ? 1u : 0u;
+    }
+    if (op.opk == kOpkGlobal) {
+        b->mode = op.g->mode;
+        b->gain_k = op.g->gain_k;
+        b->delta = op.g->delta;
+        b->gain_is_one = op.g->gain_k == 1.0f;
+        b->need_gray_hist = ldr && (op.g->mode == DC_HISTEQ || op.stats != nullptr);
+        b->stats = op.stats;
+    } else if (op.opk == kOpkLocal) {
+        b->block_s = op.l->block_s;
+        b->radius = op.l->radius_blocks;
+        b->bins = op.l->bins;
+        b->alpha = op.l->alpha;
+        b->delta = op.l->delta;
+    }
+    // workspace layout: header | ctrl | per-image local buffers
+    const int64_t ctrl_bytes = align_up((int64_t)sizeof(DcCtrl) + (int64_t)n * sizeof(DcImgCtrl), 256);
+    int64_t off = kHeaderBytes + ctrl_bytes;
+    std::vector<Geometry> geo(n);
+    for (int k = 0; k < n; ++k) {
+        make_geometry(in[idx[k]], out[idx[k]], op, tu, b->n_phase, b->phase_kind, geo[k], b->tile_rows,
+                      b->tile_cols, b->loc_tile_cols);
+        geo[k].im.ws_hist = off;
+        off += geo[k].local_bytes;
+        b->img[k] = geo[k].im;
+        b->stats_index[k] = idx[k];
+    }
+    *need = std::max(*need, off);
+    // segment table: wave w holds (image w - p, phase p), phases ascending
+    bool rev[kMaxPhases];
+    {
+        bool dir = false;
+        for (int ph = 0; ph < b->n_phase; ++ph) {
+            if (b->phase_kind[ph] == PK_CDF) {
+                rev[ph] = false;
+            } else {
+                rev[ph] = dir;
+                dir = !dir;
+            }
+        }
+    }
+    int64_t total = 0;
+    int nseg = 0;
+    for (int w = 0; w < n + b->n_phase - 1; ++w) {
+        for (int ph = 0; ph < b->n_phase; ++ph) {
+            const int i = w - ph;
+            if (i < 0 || i >= n) continue;
+            DcSegment& sg = b->seg[nseg++];
+            sg.start = (int32_t)total;
+            sg.img = (int16_t)i;
+            sg.phase = (int8_t)ph;
+            sg.reverse = rev[ph] ? 1 : 0;
+            total += geo[i].tiles[ph];
+        }
+    }
+    if (total <= 0 || total > INT32_MAX - 65536) {
+        delete b;
+        return DC_ERR_INVALID_ARG;
+    }
+    b->n_img = n;
+    b->n_seg = nseg;
+    b->total_tiles = (int32_t)total;
+    if (!launch) {
+        delete b;
+        return DC_OK;
+    }
+    b->ws = ws;
+    b->err = reinterpret_cast<uint32_t*>(ws);
+    b->ctrl = reinterpret_cast<DcCtrl*>(ws + kHeaderBytes);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t clear_bytes = first ? (size_t)(kHeaderBytes + ctrl_bytes) : (size_t)ctrl_bytes;
+    uint8_t* clear_ptr = first ? ws : ws + kHeaderBytes;
+    if (cudaMemsetAsync(clear_ptr, 0, clear_bytes, st) != cudaSuccess) {
+        delete b;
+        return DC_ERR_CUDA;
+    }
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        delete b;
+        return DC_ERR_CUDA;
+    }
+    int occ = in_dt == DC_U8 ? occupancy_u8(CAP, op.opk) : (in_dt == DC_F16 ? occupancy_f16(CAP, op.opk) : occupancy_f32(CAP, op.opk));
+    if (occ <= 0) occ = 1;
+    const int per_sm = tu.ctas_per_sm > 0 ? std::min(tu.ctas_per_sm, occ) : occ;
+    LaunchShape ls;
+    ls.threads = 256;
+    ls.grid = (int)std::min<int64_t>(total, (int64_t)per_sm * nsm);
+    int rc;
+    if (in_dt == DC_U8)
+        rc = launch_engine_u8(b, CAP, op.opk, ls, stream);
+    else if (in_dt == DC_F16)
+        rc = launch_engine_f16(b, CAP, op.opk, ls, stream);
+    else
+        rc = launch_engine_f32(b, CAP, op.opk, ls, stream);
+    delete b;
+    return rc;
+}
+
+int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_decolor_params* p, const OpArgs& op,
+        void* ws, size_t ws_bytes, void* stream, size_t* query)
+{
+    if (!in || n < 1) return DC_ERR_INVALID_ARG;
+    if (n > DC_MAX_BATCH) return DC_ERR_TOO_MANY;
+    if (!query && !out) return DC_ERR_INVALID_ARG;
+    int rc = validate_params(p, op);
+    if (rc != DC_OK) return rc;
+    for (int k = 0; k < n; ++k) {
+        rc = validate_image(in[k], query ? nullptr : &out[k], op.opk == kOpkLocal);
+        if (rc != DC_OK) return rc;
+    }
+    if (!query) {
+        // input must not overlap output
+        for (int k = 0; k < n; ++k) {
+            const uint8_t* a0 = static_cast<const uint8_t*>(in[k].data);
+            const uint8_t* a1 = a0 + (in[k].height - 1) * in[k].stride_bytes + (int64_t)3 * in[k].width * esz(in[k].dtype);
+            const uint8_t* b0 = static_cast<const uint8_t*>(out[k].data);
+            const uint8_t* b1 = b0 + (in[k].height - 1) * out[k].stride_bytes + (int64_t)in[k].width * esz(out[k].dtype);
+            if (a0 < b1 && b0 < a1) return DC_ERR_INVALID_ARG;
+        }
+    }
+    // group by input sample type, keep caller order inside a group, chunk by capacity
+    std::vector<LaunchPlan> plans;
+    for (int dt = DC_U8; dt <= DC_F32; ++dt) {
+        LaunchPlan cur;
+        cur.in_dt = dt;
+        for (int k = 0; k < n; ++k) {
+            if (in[k].dtype != dt) continue;
+            cur.idx.push_back(k);
+            if ((int)cur.idx.size() == kCapLarge) {
+                plans.push_back(cur);
+                cur.idx.clear();
+            }
+        }
+        if (!cur.idx.empty()) plans.push_back(cur);
+    }
+    // a fake (valid) output descriptor for size queries
+    std::vector<dc_image_out> fake;
+    const dc_image_out* outs = out;
+    if (query) {
+        fake.resize(n);
+        for (int k = 0; k < n; ++k) {
+            fake[k].data = reinterpret_cast<void*>(uintptr_t(256));
+            fake[k].stride_bytes = (int64_t)in[k].width * 4;
+            fake[k].dtype = DC_F32;
+            fake[k].reserved = 0;
+        }
+        outs = fake.data();
+    }
+    int64_t need = kHeaderBytes;
+    for (const LaunchPlan& pl : plans) {
+        const int cnt = (int)pl.idx.size();
+        int r2;
+        if (cnt <= kCapSmall)
+            r2 = build_and_launch<kCapSmall>(in, outs, pl.idx, p, op, nullptr, false, &need, nullptr, false);
+        else if (cnt <= kCapMid)
+            r2 = build_and_launch<kCapMid>(in, outs, pl.idx, p, op, nullptr, false, &need, nullptr, false);
+        else
+            r2 = build_and_launch<kCapLarge>(in, outs, pl.idx, p, op, nullptr, false, &need, nullptr, false);
+        if (r2 != DC_OK) return r2;
+    }
+    if (query) {
+        *query = (size_t)need;
+        return DC_OK;
+    }
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < (size_t)need) return DC_ERR_WORKSPACE;
+    int launches = 0;
+    bool first = true;
+    for (const LaunchPlan& pl : plans) {
+        const int cnt = (int)pl.idx.size();
+        int64_t dummy = 0;
+        uint8_t* w = static_cast<uint8_t*>(ws);
+        int r2;
+        if (cnt <= kCapSmall)
+            r2 = build_and_launch<kCapSmall>(in, out, pl.idx, p, op, w, first, &dummy, stream, true);
+        else if (cnt <= kCapMid)
+            r2 = build_and_launch<kCapMid>(in, out, pl.idx, p, op, w, first, &dummy, stream, true);
+        else
+            r2 = build_and_launch<kCapLarge>(in, out, pl.idx, p, op, w, first, &dummy, stream, true);
+        if (r2 != DC_OK) return r2;
+        first = false;
+        ++launches;
+    }
+    g_last_launches = launches;
+    return DC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+DC_API int dc_decolorize(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_decolor_params* params,
+                         void* ws, size_t ws_bytes, void* stream)
+{
+    OpArgs op{kOpkDecolor, nullptr, nullptr, nullptr};
+    return run(in, out, n, params, op, ws, ws_bytes, stream, nullptr);
+}
+
+DC_API int dc_decolorize_tonemap_global(const dc_image_in* in, const dc_image_out* out, int32_t n,
+                                        const dc_decolor_params* params, const dc_global_params* gparams,
+                                        dc_global_stats* stats, void* ws, size_t ws_bytes, void* stream)
+{
+    OpArgs op{kOpkGlobal, gparams, nullptr, stats};
+    return run(in, out, n, params, op, ws, ws_bytes, stream, nullptr);
+}
+
+DC_API int dc_decolorize_tonemap_local(const dc_image_in* in, const dc_image_out* out, int32_t n,
+                                       const dc_decolor_params* params, const dc_local_params* lparams, void* ws,
+                                       size_t ws_bytes, void* stream)
+{
+    OpArgs op{kOpkLocal, nullptr, lparams, nullptr};
+    return run(in, out, n, params, op, ws, ws_bytes, stream, nullptr);
+}
+
+DC_API size_t dc_workspace_bytes(int32_t op, const dc_image_in* in, int32_t n, const void* op_params)
+{
+    static const dc_decolor_params kBeta = {0.55f, 0.8f};
+    static const dc_global_params kGlobal = {DC_SIGMOID, 1.0f, 1e-4f, 0};
+    OpArgs a{0, nullptr, nullptr, nullptr};
+    if (op == DC_OP_DECOLORIZE) {
+        a.opk = kOpkDecolor;
+    } else if (op == DC_OP_GLOBAL) {
+        a.opk = kOpkGlobal;
+        a.g = &kGlobal;
+    } else if (op == DC_OP_LOCAL) {
+        a.opk = kOpkLocal;
+        a.l = static_cast<const dc_local_params*>(op_params);
+        if (!a.l) return 0;
+    } else {
+        return 0;
+    }
+    size_t need = 0;
+    if (run(in, nullptr, n, &kBeta, a, nullptr, 0, nullptr, &need) != DC_OK) return 0;
+    return need;
+}
+
+DC_API int dc_query_status(const void* ws, void* stream)
+{
+    if (!ws) return DC_ERR_INVALID_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return DC_ERR_CUDA;
+    uint32_t err = 0;
+    if (cudaMemcpy(&err, ws, sizeof(err), cudaMemcpyDeviceToHost) != cudaSuccess) return DC_ERR_CUDA;
+    return (int)err;
+}
+
+DC_API const char* dc_status_string(int status)
+{
+    switch (status) {
+    case DC_OK: return "ok";
+    case DC_ERR_INVALID_ARG: return "invalid argument";
+    case DC_ERR_UNSUPPORTED_DTYPE: return "unsupported sample type";
+    case DC_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case DC_ERR_CUDA: return "CUDA runtime error";
+    case DC_ERR_TIMEOUT: return "device-side dependency wait timed out";
+    case DC_ERR_TOO_MANY: return "too many images in one call";
+    default: return "unknown status";
+    }
+}
+
+DC_API int dc_set_tuning(int32_t op, int32_t in_dtype, const dc_tuning* t)
+{
+    if (op < DC_OP_DECOLORIZE || op > DC_OP_LOCAL || !dt_ok(in_dtype) || !t) return DC_ERR_INVALID_ARG;
+    if (t->threads != 256) return DC_ERR_INVALID_ARG;
+    if (t->tile_rows < 1 || t->tile_rows > 4096 || t->tile_cols < 16 || t->tile_cols > (1 << 20) || (t->tile_cols % 16) != 0)
+        return DC_ERR_INVALID_ARG;
+    if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return DC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tune[op][in_dtype] = *t;
+    return DC_OK;
+}
+
+DC_API int dc_get_tuning(int32_t op, int32_t in_dtype, dc_tuning* t)
+{
+    if (op < DC_OP_DECOLORIZE || op > DC_OP_LOCAL || !dt_ok(in_dtype) || !t) return DC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    *t = g_tune[op][in_dtype];
+    return DC_OK;
+}
+
+DC_API int dc_set_wait_timeout_ns(uint64_t ns)
+{
+    if (ns < 1000) return DC_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_timeout_ns = ns;
+    return DC_OK;
+}
+
+DC_API int dc_debug_withhold_ready(int32_t on)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_withhold = on ? 1 : 0;
+    return DC_OK;
+}
+
+DC_API int dc_last_launch_count(void) { return g_last_launches; }
+
+DC_API int dc_version(void) { return 100; }
+
+}  // extern "C"

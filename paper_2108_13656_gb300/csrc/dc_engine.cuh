@@ -1,0 +1,377 @@
+// Persistent engine kernel: decolorization (Eq. 1-6, Sec. II-B) fused with the
+// global (Sec. III-B-1) and local (Sec. III-B-2) tone-mapping passes.
+//
+// Layout and schedule (see dc_internal.h): a batch of images, each a chain of
+// phases, each phase cut into tiles; CTAs pull tile numbers from one atomic
+// counter.  Pixels are read as 48-byte groups (16 u8 / 8 f16 / 4 f32 pixels) with
+// three 16-byte vector loads when the image is 16-byte aligned; everything else
+// (ragged row tails, unaligned images) takes a per-pixel path with identical
+// arithmetic.  All arithmetic is binary32; every cross-thread reduction is exact
+// integer arithmetic (the log-sum in 2^-20 fixed point, min/max on ordered bit
+// patterns, histograms as counts), so results do not depend on the launch shape.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "dc_internal.h"
+
+namespace dc {
+
+constexpr int kThreads = 256;
+constexpr int kLocMaxBlocksX = 64;    // max blocks per local tile row
+constexpr int kCdfChunk = 64;         // block columns per CDF sub-pass
+constexpr int kMaxRadius = 16;
+
+template <int IN_DT> struct InT;
+template <> struct InT<DC_U8> { static constexpr int G = 16; static constexpr int ESZ = 1; };
+template <> struct InT<DC_F16> { static constexpr int G = 8; static constexpr int ESZ = 2; };
+template <> struct InT<DC_F32> { static constexpr int G = 4; static constexpr int ESZ = 4; };
+
+enum OpKind { OPK_DECOLOR = 0, OPK_GLOBAL = 1, OPK_LOCAL = 2 };
+
+// ------------------------------------------------------------ memory access ---
+__device__ __forceinline__ uint4 ld_stream16(const void* p)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ float4 ld_cg_f4(const float* p)
+{
+    float4 v;
+    asm volatile("ld.global.cg.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ float ld_cg_f(const float* p)
+{
+    float v;
+    asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long* p)
+{
+    unsigned long long v;
+    asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_cg_u32(const uint32_t* p)
+{
+    uint32_t v;
+    asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p)
+{
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p)
+{
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// ------------------------------------------------------------- Eq. 1-6 -------
+struct Beta {
+    float bR, one_m_bR, bk, one_m_bk;
+};
+
+// Eq. 1-6 in binary32 for one pixel.  R+G+B = 0 gives 0 (continuous extension).
+__device__ __forceinline__ float luminance_f32(float R, float G, float B, const Beta& be)
+{
+    const float S = R + G + B;
+    const float L_WHITE = sqrtf(fmaf(R, R, fmaf(G, G, B * B)) * (1.0f / 3.0f));  // Eq. 1
+    const float L_B = B;                                                       // Eq. 2
+    const float L_GR = sqrtf(fmaf(be.bR, R * R, be.one_m_bR * (G * G)));        // Eq. 3
+    const float inv = 1.0f / S;
+    const float r = R * inv, b = B * inv;
+    const float L_WARM = fmaf(r, L_GR - L_WHITE, L_WHITE);                      // Eq. 4
+    const float L_COOL = fmaf(b, L_WHITE - L_B, L_B);                           // Eq. 5
+    const float L = sqrtf(fmaf(be.bk, L_WARM * L_WARM, be.one_m_bk * (L_COOL * L_COOL)));  // Eq. 6
+    return S > 0.0f ? L : 0.0f;
+}
+
+// Linear samples of arbitrary magnitude: Eq. 1-6 are 1-homogeneous, so scale the
+// pixel by a power of two into a safe range first (exact), then scale back.
+__device__ __forceinline__ float luminance_hdr(float R, float G, float B, const Beta& be)
+{
+    R = fmaxf(R, 0.0f);
+    G = fmaxf(G, 0.0f);
+    B = fmaxf(B, 0.0f);
+    const float m = fmaxf(R, fmaxf(G, B));
+    if (m > 0x1p60f || (m < 0x1p-60f && m > 0.0f)) {
+        int e;
+        frexpf(m, &e);
+        const float s = ldexpf(1.0f, -e);
+        return ldexpf(luminance_f32(R * s, G * s, B * s, be), e);
+    }
+    return luminance_f32(R, G, B, be);
+}
+
+// 8-bit code of y in [0,1]: floor(255 y + 1/2), clamped.
+__device__ __forceinline__ uint32_t quant_u8(float y)
+{
+    float t = fmaxf(fminf(fmaf(y, 255.0f, 0.5f), 255.0f), 0.0f);
+    return __float_as_uint(__fadd_rd(t, 8388608.0f)) & 0xFFu;
+}
+
+// u8 sample -> float via the exponent-bias trick (2^23 + v, minus 2^23): exact.
+__device__ __forceinline__ float u8_at(const uint32_t (&w)[12], int idx)
+{
+    return __uint_as_float(__byte_perm(w[idx >> 2], 0x4B00u, 0x5440u | (uint32_t)(idx & 3))) - 8388608.0f;
+}
+
+// ordered-uint encoding of floats (monotone), for exact atomic min/max
+__device__ __forceinline__ uint32_t ord_enc(float f)
+{
+    uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float ord_dec(uint32_t o)
+{
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o);
+}
+
+// ------------------------------------------------------------ group I/O ------
+template <int IN_DT>
+struct GroupIO {
+    static constexpr int G = InT<IN_DT>::G;
+    static constexpr int ESZ = InT<IN_DT>::ESZ;
+
+    // Luminance in [0,1] units (8-bit codes / 255; linear values as they are)
+    // of the n pixels starting at (r, c).  vec: full 16-byte aligned group.
+    __device__ static void luminance(const DcImage& im, int r, int c, int n, bool vec,
+                                     const Beta& be, float (&Lv)[G])
+    {
+        const uint8_t* p = im.in + (int64_t)r * im.in_stride + (int64_t)c * 3 * ESZ;
+        if (vec) {
+            uint4 a = ld_stream16(p), b = ld_stream16(p + 16), d = ld_stream16(p + 32);
+            if constexpr (IN_DT == DC_U8) {
+                const uint32_t w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, d.x, d.y, d.z, d.w};
+#pragma unroll
+                for (int k = 0; k < G; ++k)
+                    Lv[k] = luminance_f32(u8_at(w, 3 * k), u8_at(w, 3 * k + 1), u8_at(w, 3 * k + 2), be) *
+                            (1.0f / 255.0f);
+            } else if constexpr (IN_DT == DC_F16) {
+                const uint32_t w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, d.x, d.y, d.z, d.w};
+                float f[24];
+#pragma unroll
+                for (int k = 0; k < 12; ++k) {
+                    __half2 h;
+                    memcpy(&h, &w[k], 4);
+                    float2 v = __half22float2(h);
+                    f[2 * k] = v.x;
+                    f[2 * k + 1] = v.y;
+                }
+#pragma unroll
+                for (int k = 0; k < G; ++k) Lv[k] = luminance_hdr(f[3 * k], f[3 * k + 1], f[3 * k + 2], be);
+            } else {
+                const float f[12] = {__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z),
+                                     __uint_as_float(a.w), __uint_as_float(b.x), __uint_as_float(b.y),
+                                     __uint_as_float(b.z), __uint_as_float(b.w), __uint_as_float(d.x),
+                                     __uint_as_float(d.y), __uint_as_float(d.z), __uint_as_float(d.w)};
+#pragma unroll
+                for (int k = 0; k < G; ++k) Lv[k] = luminance_hdr(f[3 * k], f[3 * k + 1], f[3 * k + 2], be);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                if (k < n) {
+                    const uint8_t* q = p + k * 3 * ESZ;
+                    if constexpr (IN_DT == DC_U8) {
+                        Lv[k] = luminance_f32((float)__ldg(q), (float)__ldg(q + 1), (float)__ldg(q + 2), be) *
+                                (1.0f / 255.0f);
+                    } else if constexpr (IN_DT == DC_F16) {
+                        const __half* h = reinterpret_cast<const __half*>(q);
+                        Lv[k] = luminance_hdr(__half2float(h[0]), __half2float(h[1]), __half2float(h[2]), be);
+                    } else {
+                        const float* f = reinterpret_cast<const float*>(q);
+                        Lv[k] = luminance_hdr(__ldg(f), __ldg(f + 1), __ldg(f + 2), be);
+                    }
+                } else {
+                    Lv[k] = 0.0f;
+                }
+            }
+        }
+    }
+
+    // Luminance from the f32 plane an earlier phase wrote into `out`.
+    __device__ static void from_plane(const DcImage& im, int r, int c, int n, bool vec, float (&Lv)[G])
+    {
+        const float* p = reinterpret_cast<const float*>(im.out + (int64_t)r * im.out_stride) + c;
+        if (vec) {
+#pragma unroll
+            for (int k = 0; k < G; k += 4) {
+                float4 v = ld_cg_f4(p + k);
+                Lv[k] = v.x;
+                Lv[k + 1] = v.y;
+                Lv[k + 2] = v.z;
+                Lv[k + 3] = v.w;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < G; ++k) Lv[k] = (k < n) ? ld_cg_f(p + k) : 0.0f;
+        }
+    }
+
+    // Store n values (in [0,1] units) at (r, c) in the output sample type.
+    __device__ static void store(const DcImage& im, int r, int c, int n, bool vec, const float (&y)[G])
+    {
+        uint8_t* base = im.out + (int64_t)r * im.out_stride;
+        if (im.out_dt == DC_U8) {
+            uint8_t* p = base + c;
+            if (vec) {
+                uint32_t w[(G + 3) / 4];
+#pragma unroll
+                for (int k = 0; k < (G + 3) / 4; ++k) w[k] = 0;
+#pragma unroll
+                for (int k = 0; k < G; ++k) w[k >> 2] |= quant_u8(y[k]) << (8 * (k & 3));
+                if constexpr (G == 16) {
+                    *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+                } else if constexpr (G == 8) {
+                    *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+                } else {
+                    *reinterpret_cast<uint32_t*>(p) = w[0];
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < G; ++k)
+                    if (k < n) p[k] = (uint8_t)quant_u8(y[k]);
+            }
+        } else if (im.out_dt == DC_F16) {
+            __half* p = reinterpret_cast<__half*>(base) + c;
+            if (vec) {
+                uint32_t w[G / 2];
+#pragma unroll
+                for (int k = 0; k < G / 2; ++k) {
+                    __half2 h = __floats2half2_rn(y[2 * k], y[2 * k + 1]);
+                    memcpy(&w[k], &h, 4);
+                }
+                if constexpr (G == 16) {
+                    reinterpret_cast<uint4*>(p)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                    reinterpret_cast<uint4*>(p)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                } else if constexpr (G == 8) {
+                    *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+                } else {
+                    *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < G; ++k)
+                    if (k < n) p[k] = __float2half_rn(y[k]);
+            }
+        } else {
+            float* p = reinterpret_cast<float*>(base) + c;
+            if (vec) {
+#pragma unroll
+                for (int k = 0; k < G; k += 4)
+                    *reinterpret_cast<float4*>(p + k) = make_float4(y[k], y[k + 1], y[k + 2], y[k + 3]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < G; ++k)
+                    if (k < n) p[k] = y[k];
+            }
+        }
+    }
+};
+
+// Pairwise sum of a compile-time-length array (fixed order).
+template <int N>
+__device__ __forceinline__ float pairwise_sum(const float* v)
+{
+    if constexpr (N == 1) {
+        return v[0];
+    } else {
+        return pairwise_sum<N / 2>(v) + pairwise_sum<N - N / 2>(v + N / 2);
+    }
+}
+
+// ------------------------------------------------------------ waits -----------
+// Bounded wait for a phase-complete flag.  Returns 0 when the flag is set, 1 when
+// the launch has an error or the wait ran out (then DC_ERR_TIMEOUT is recorded).
+static __device__ __noinline__ int wait_ready(const uint32_t* flag, uint32_t* err, unsigned long long timeout_ns)
+{
+    if (ld_acquire_u32(flag)) return 0;
+    const unsigned long long t0 = globaltimer_ns();
+    const unsigned long long max_iter = timeout_ns / 16ull + 4096ull;
+    unsigned ns = 32;
+    for (unsigned long long it = 0;; ++it) {
+        if (ld_acquire_u32(flag)) return 0;
+        if (ld_relaxed_u32(err)) return 1;
+        if (globaltimer_ns() - t0 > timeout_ns || it > max_iter) {
+            atomicCAS(err, 0u, (uint32_t)DC_ERR_TIMEOUT);
+            return 1;
+        }
+        __nanosleep(ns);
+        if (ns < 1024) ns *= 2;
+    }
+}
+
+// ------------------------------------------------------------ shared memory ---
+struct SmemStats {
+    uint32_t hist[256];
+    long long wsum[kThreads / 32];
+    float wmin[kThreads / 32], wmax[kThreads / 32];
+    uint32_t scan[kThreads];
+};
+struct SmemApplyG {
+    float lut[260];
+};
+struct SmemBlockH {
+    unsigned long long h[kLocMaxBlocksX * DC_MAX_BINS];
+};
+struct SmemCdf {
+    unsigned long long v[(kCdfChunk + 2 * kMaxRadius) * DC_MAX_BINS];
+};
+struct SmemApplyL {
+    float tab[3 * (kLocMaxBlocksX + 2) * (DC_MAX_BINS + 1)];
+};
+
+template <int OPK>
+struct SmemBytes {
+    static constexpr size_t a = sizeof(SmemStats) > sizeof(SmemApplyG) ? sizeof(SmemStats) : sizeof(SmemApplyG);
+    static constexpr size_t b = sizeof(SmemBlockH) > sizeof(SmemCdf) ? sizeof(SmemBlockH) : sizeof(SmemCdf);
+    static constexpr size_t c = b > sizeof(SmemApplyL) ? b : sizeof(SmemApplyL);
+    static constexpr size_t value = OPK == OPK_LOCAL ? (a > c ? a : c) : a;
+};
+
+__device__ __forceinline__ DcImgCtrl* img_ctrl(DcCtrl* c, int i)
+{
+    return reinterpret_cast<DcImgCtrl*>(reinterpret_cast<uint8_t*>(c) + sizeof(DcCtrl)) + i;
+}
+
+// Normalised log luminance u for the HDR histogram forms.
+__device__ __forceinline__ float log_u(float L, float delta, float lmin, float inv_range)
+{
+    if (inv_range == 0.0f) return 0.5f;
+    const float u = (logf(L + delta) - lmin) * inv_range;
+    return fminf(fmaxf(u, 0.0f), 1.0f);
+}
+
+}  // namespace dc

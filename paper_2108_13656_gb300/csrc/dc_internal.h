@@ -1,0 +1,134 @@
+// Internal structures shared by the host side (dc_abi.cu) and the engine kernels.
+//
+// One launch of the engine processes a batch of images of one input sample type
+// for one operation.  Each operation is a short chain of passes ("phases") per
+// image; every phase is cut into tiles, and one global atomic counter hands tiles
+// to CTAs in a fixed order (the segment table).  A tile of phase p of image i only
+// waits for phase p-1 of image i, and every such tile comes earlier in the order,
+// so all tiles it waits for are already held by running CTAs: the schedule cannot
+// deadlock, whatever the number of resident CTAs.
+#pragma once
+
+#include <stdint.h>
+
+#include "../../include/decolor.h"
+
+namespace dc {
+
+constexpr int kMaxPhases = 4;
+constexpr int kCapSmall = 1;     // params capacity for single-image calls
+constexpr int kCapMid = 16;
+constexpr int kCapLarge = 256;   // largest batch per launch (kernel parameter space)
+constexpr int kLogFixedShift = 20;  // logsum unit is 2^-20
+
+// phase kinds
+enum PhaseKind : int32_t {
+    PK_DECOLOR = 0,   // L -> out
+    PK_STATS = 1,     // log statistics (+ 8-bit gray histogram) (+ L plane)
+    PK_LOGHIST = 2,   // HDR histogram of u (DC_HISTEQ)
+    PK_APPLY_G = 3,   // global curve -> out
+    PK_BLOCKH = 4,    // local: block histograms
+    PK_CDF = 5,       // local: window sums -> per-block cumulative tables
+    PK_APPLY_L = 6,   // local: bilinear blend of block curves -> out
+};
+
+// per-image flags
+enum : uint32_t {
+    IF_VEC = 1u,      // 16-byte aligned pointers and strides: vector path
+    IF_LPLANE = 2u,   // out is an f32 plane that holds L between phases
+};
+
+struct DcImage {                 // 80 bytes
+    const uint8_t* in;
+    uint8_t* out;
+    int64_t in_stride;           // bytes between (logical) rows
+    int64_t out_stride;
+    int32_t rows, cols;          // logical geometry of pixelwise phases
+    int32_t prow, pcol;          // physical geometry (local operator)
+    int32_t out_dt;
+    uint32_t flags;
+    int32_t tiles_x;             // tiles per tile row, pixelwise phases
+    int32_t tiles_x_loc;         // tiles per block row, local phases
+    int32_t Hb, Wb;              // local: blocks
+    int64_t ws_hist;             // byte offsets into the workspace (local)
+};
+
+struct DcSegment {               // 8 bytes
+    int32_t start;               // first global tile index of this segment
+    int16_t img;
+    int8_t phase;                // index into the op's phase list
+    int8_t reverse;              // hand the tiles out last-first (L2 reuse)
+};
+
+// Per-image control block, cleared by the host before every launch.
+struct DcImgCtrl {
+    uint32_t done[kMaxPhases];
+    uint32_t ready[kMaxPhases];
+    unsigned long long logsum;   // two's complement, units of 2^-20
+    uint32_t lmax_ord;           // ordered-uint encoding of max ln(L+delta)
+    uint32_t lmin_nord;          // bitwise NOT of the ordered encoding of the min
+    float mu, lmin, lmax, exp_mu;
+    float inv_range;             // 1 / (lmax - lmin), 0 when lmax == lmin
+    uint32_t pad[7];
+    uint32_t hist[256];
+    float lut[260];              // LDR HISTEQ: y per gray code; HDR HISTEQ: cumulative edges
+};
+
+// Per-launch control block, cleared by the host before the launch.
+struct DcCtrl {
+    uint32_t next_tile;
+    uint32_t pad[63];
+    // followed by DcImgCtrl[n]
+};
+
+// Call-level header at the start of the workspace: the device-side error word.
+struct DcWsHeader {
+    uint32_t error;
+    uint32_t pad[63];
+};
+
+template <int CAP>
+struct DcBatch {
+    int32_t n_img, n_seg, total_tiles, n_phase;
+    int32_t phase_kind[kMaxPhases];
+    int32_t tile_rows, tile_cols;      // pixelwise phases
+    int32_t loc_tile_cols;             // local phases (tile height = block_s)
+    float beta_r, beta_k;
+    int32_t ldr;                       // 8-bit input
+    int32_t mode;                      // DC_SIGMOID / DC_HISTEQ
+    float gain_k, delta;
+    int32_t gain_is_one;
+    int32_t need_gray_hist;            // LDR: gray histogram wanted (HISTEQ or stats)
+    int32_t block_s, radius, bins;
+    float alpha;
+    uint32_t withhold_ready;
+    unsigned long long timeout_ns;
+    DcCtrl* ctrl;
+    uint32_t* err;                     // call-level error word (workspace header)
+    dc_global_stats* stats;            // nullable; indexed by img_stats_index
+    uint8_t* ws;
+    int32_t stats_index[CAP];
+    DcImage img[CAP];
+    DcSegment seg[CAP * kMaxPhases];
+};
+
+#ifdef __CUDACC__
+__host__ __device__
+#endif
+inline int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+
+// launcher entry points (one per input sample type), defined in dc_engine_*.cu
+struct LaunchShape {
+    int threads;
+    int grid;
+};
+
+// opk: 0 decolorize, 1 global, 2 local
+int launch_engine_u8(const void* batch, int cap, int opk, LaunchShape ls, void* stream);
+int launch_engine_f16(const void* batch, int cap, int opk, LaunchShape ls, void* stream);
+int launch_engine_f32(const void* batch, int cap, int opk, LaunchShape ls, void* stream);
+int occupancy_u8(int cap, int opk);
+int occupancy_f16(int cap, int opk);
+int occupancy_f32(int cap, int opk);
+
+}  // namespace dc

@@ -1,0 +1,148 @@
+"""Host-side checks of the C ABI that need no GPU.
+
+The shared library must load and export every entry point include/decolor.h
+declares; the ctypes mirrors must match the C struct sizes; argument validation and
+workspace sizing run entirely on the host, so they are exercised here (no kernel is
+launched by any of these calls: every call below fails validation or only sizes).
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "decolor.h")
+
+
+@pytest.fixture(scope="module")
+def abi():
+    from paper_2108_13656_gb300 import _abi, build_lib
+    build_lib.build()
+    _abi.load()
+    return _abi
+
+
+def _declared_symbols():
+    text = open(HEADER).read()
+    return re.findall(r"DC_API\s+[\w\s\*]+?\b(dc_\w+)\s*\(", text)
+
+
+def test_header_declares_the_three_calls():
+    syms = _declared_symbols()
+    for name in ("dc_decolorize", "dc_decolorize_tonemap_global", "dc_decolorize_tonemap_local",
+                 "dc_workspace_bytes", "dc_query_status", "dc_status_string"):
+        assert name in syms
+
+
+def test_library_exports_every_declared_symbol(abi):
+    lib = abi.load()
+    syms = _declared_symbols()
+    assert len(syms) >= 10
+    for name in syms:
+        assert hasattr(lib, name), name
+        assert name in abi._SIGS, "binding lacks " + name
+    assert lib.dc_version() == 100
+
+
+def test_struct_sizes(abi):
+    assert ctypes.sizeof(abi.dc_image_in) == 32
+    assert ctypes.sizeof(abi.dc_image_out) == 24
+    assert ctypes.sizeof(abi.dc_decolor_params) == 8
+    assert ctypes.sizeof(abi.dc_global_params) == 16
+    assert ctypes.sizeof(abi.dc_local_params) == 24
+    assert ctypes.sizeof(abi.dc_tuning) == 16
+    assert abi.STATS_BYTES == 1056
+
+
+def _img(w, h, dt=0, stride=None, ptr=1 << 20):
+    esz = {0: 1, 1: 2, 2: 4}.get(dt, 1)
+    d = None
+    from paper_2108_13656_gb300 import _abi
+    d = _abi.dc_image_in()
+    d.data = ptr
+    d.width, d.height = w, h
+    d.stride_bytes = stride if stride is not None else 3 * w * esz
+    d.dtype = dt
+    d.reserved = 0
+    return d
+
+
+def test_workspace_bytes_sizes(abi):
+    lib = abi.load()
+    ins = (abi.dc_image_in * 1)(_img(3840, 2160))
+    g = lib.dc_workspace_bytes(abi.DC_OP_GLOBAL, ins, 1, None)
+    assert 256 < g < 1 << 20
+    lp = abi.local_params()
+    loc = lib.dc_workspace_bytes(abi.DC_OP_LOCAL, ins, 1, ctypes.byref(lp))
+    Hb, Wb = (2160 + 31) // 32, 3840 // 32
+    assert loc >= g + Hb * Wb * 32 * 8 + Hb * Wb * 33 * 4
+    assert lib.dc_workspace_bytes(abi.DC_OP_LOCAL, ins, 1, None) == 0
+    assert lib.dc_workspace_bytes(7, ins, 1, None) == 0
+    many = (abi.dc_image_in * 300)(*[_img(64 + i, 32) for i in range(300)])
+    assert lib.dc_workspace_bytes(abi.DC_OP_GLOBAL, many, 300, None) > 0
+
+
+@pytest.mark.parametrize("bad", [
+    dict(width=0), dict(height=0), dict(dtype=9), dict(stride=10), dict(ptr=0),
+])
+def test_invalid_inputs_rejected(abi, bad):
+    lib = abi.load()
+    d = _img(16, 4, dt=bad.get("dtype", 0), stride=bad.get("stride"), ptr=bad.get("ptr", 1 << 20))
+    if "width" in bad:
+        d.width = bad["width"]
+    if "height" in bad:
+        d.height = bad["height"]
+    ins = (abi.dc_image_in * 1)(d)
+    assert lib.dc_workspace_bytes(abi.DC_OP_DECOLORIZE, ins, 1, None) == 0
+    out = (abi.dc_image_out * 1)(abi.dc_image_out(1 << 22, 16, 0, 0))
+    p = abi.dc_decolor_params(0.55, 0.8)
+    rc = lib.dc_decolorize(ins, out, 1, ctypes.byref(p), ctypes.c_void_p(1 << 12), 1 << 20, None)
+    assert rc in (abi.DC_ERR_INVALID_ARG, abi.DC_ERR_UNSUPPORTED_DTYPE)
+
+
+def test_invalid_params_and_workspace(abi):
+    lib = abi.load()
+    ins = (abi.dc_image_in * 1)(_img(16, 4))
+    out = (abi.dc_image_out * 1)(abi.dc_image_out(1 << 22, 16, 0, 0))
+    p = abi.dc_decolor_params(1.5, 0.8)
+    assert lib.dc_decolorize(ins, out, 1, ctypes.byref(p), ctypes.c_void_p(1 << 12), 1 << 20, None) == abi.DC_ERR_INVALID_ARG
+    p = abi.dc_decolor_params(0.55, 0.8)
+    # workspace: NULL, misaligned, too small
+    assert lib.dc_decolorize(ins, out, 1, ctypes.byref(p), None, 1 << 20, None) == abi.DC_ERR_WORKSPACE
+    assert lib.dc_decolorize(ins, out, 1, ctypes.byref(p), ctypes.c_void_p((1 << 12) + 8), 1 << 20, None) == abi.DC_ERR_WORKSPACE
+    assert lib.dc_decolorize(ins, out, 1, ctypes.byref(p), ctypes.c_void_p(1 << 12), 16, None) == abi.DC_ERR_WORKSPACE
+    g = abi.dc_global_params(5, 1.0, 1e-4, 0)
+    assert lib.dc_decolorize_tonemap_global(ins, out, 1, ctypes.byref(p), ctypes.byref(g), None,
+                                            ctypes.c_void_p(1 << 12), 1 << 20, None) == abi.DC_ERR_INVALID_ARG
+    g = abi.dc_global_params(0, 1.0, 0.0, 0)
+    assert lib.dc_decolorize_tonemap_global(ins, out, 1, ctypes.byref(p), ctypes.byref(g), None,
+                                            ctypes.c_void_p(1 << 12), 1 << 20, None) == abi.DC_ERR_INVALID_ARG
+    for lp in [abi.local_params(block_s=0), abi.local_params(bins=33), abi.local_params(radius_blocks=17),
+               abi.local_params(alpha=2.0)]:
+        assert lib.dc_decolorize_tonemap_local(ins, out, 1, ctypes.byref(p), ctypes.byref(lp),
+                                               ctypes.c_void_p(1 << 12), 1 << 20, None) == abi.DC_ERR_INVALID_ARG
+    # overlapping input and output
+    ov = (abi.dc_image_out * 1)(abi.dc_image_out(1 << 20, 16, 0, 0))
+    assert lib.dc_decolorize(ins, ov, 1, ctypes.byref(p), ctypes.c_void_p(1 << 12), 1 << 20, None) == abi.DC_ERR_INVALID_ARG
+    # batch limits
+    assert lib.dc_decolorize(ins, out, 0, ctypes.byref(p), ctypes.c_void_p(1 << 12), 1 << 20, None) == abi.DC_ERR_INVALID_ARG
+    assert lib.dc_decolorize(ins, out, 5000, ctypes.byref(p), ctypes.c_void_p(1 << 12), 1 << 20, None) == abi.DC_ERR_TOO_MANY
+
+
+def test_tuning_table_validation(abi):
+    orig = abi.get_tuning(abi.DC_OP_GLOBAL, abi.DC_U8)
+    with pytest.raises(abi.DcError):
+        abi.set_tuning(abi.DC_OP_GLOBAL, abi.DC_U8, 256, 1, 20)  # not a multiple of 16
+    with pytest.raises(abi.DcError):
+        abi.set_tuning(abi.DC_OP_GLOBAL, abi.DC_U8, 100, 1, 4096)
+    abi.set_tuning(abi.DC_OP_GLOBAL, abi.DC_U8, 256, 2, 8192, 4)
+    assert abi.get_tuning(abi.DC_OP_GLOBAL, abi.DC_U8) == (256, 2, 8192, 4)
+    abi.set_tuning(abi.DC_OP_GLOBAL, abi.DC_U8, *orig)
+    with pytest.raises(abi.DcError):
+        abi.set_wait_timeout_ns(10)
+
+
+def test_status_strings(abi):
+    assert abi.status_string(abi.DC_ERR_TIMEOUT).startswith("device-side")
+    assert abi.status_string(0) == "ok"

@@ -1,0 +1,113 @@
+"""Engine behaviour on the GPU: bounded dependency waits, launch-shape invariance,
+launch counts and CUDA-graph capture."""
+import numpy as np
+import pytest
+
+from _cmp import check_f32
+from _dev import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dc():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2108_13656_gb300 as m
+    m.load()
+    return m
+
+
+def test_wait_timeout_is_reported_and_recoverable(dc, oracle_mod):
+    """A dependency flag that is never published makes every dependent wait run out
+    after the (short) limit; the error comes back through dc_query_status and the
+    next call on the same workspace works."""
+    import torch
+    from paper_2108_13656_gb300 import synth
+    img = synth.s_ldr(256, 128, seed=1)
+    x = to_dev(img)
+    y = torch.zeros((128, 256), dtype=torch.float32, device="cuda")
+    ws = dc.Workspace()
+    dc.set_wait_timeout_ns(2_000_000)  # 2 ms
+    dc.debug_withhold_ready(True)
+    try:
+        dc.decolorize_tonemap_global(x, y, workspace=ws)
+        assert dc.query_status(ws) == 5  # DC_ERR_TIMEOUT
+    finally:
+        dc.debug_withhold_ready(False)
+        dc.set_wait_timeout_ns(2_000_000_000)
+    dc.decolorize_tonemap_global(x, y, workspace=ws)
+    assert dc.query_status(ws) == 0
+    y64, _ = oracle_mod.tonemap_global_plane(oracle_mod.decolorize(img), ldr=True)
+    check_f32(y.cpu().numpy(), y64, what="after timeout")
+
+
+@pytest.mark.parametrize("op", ["decolorize", "global", "histeq", "local"])
+@pytest.mark.parametrize("in_dt", [np.uint8, np.float32])
+def test_results_independent_of_launch_shape(dc, op, in_dt):
+    """Tile shape and CTAs per SM change neither the bits of the output nor the stats."""
+    import torch
+    from paper_2108_13656_gb300 import synth
+    img = synth.s_ldr(1000, 700, 3) if in_dt == np.uint8 else synth.s_hdr(1000, 700, 3)
+    x = to_dev(img)
+    dt_code = dc.DC_U8 if in_dt == np.uint8 else dc.DC_F32
+    op_code = {"decolorize": dc.DC_OP_DECOLORIZE, "global": dc.DC_OP_GLOBAL, "histeq": dc.DC_OP_GLOBAL,
+               "local": dc.DC_OP_LOCAL}[op]
+    orig = dc.get_tuning(op_code, dt_code)
+    results = []
+    try:
+        for (tr, tc, cps) in [(4, 4096, 0), (1, 16, 1), (7, 1040, 3), (64, 65536, 2), (2, 512, 0)]:
+            dc.set_tuning(op_code, dt_code, 256, tr, tc, cps)
+            y = torch.empty((700, 1000), dtype=torch.float32, device="cuda")
+            st = torch.zeros(dc.STATS_BYTES, dtype=torch.uint8, device="cuda")
+            if op == "decolorize":
+                dc.decolorize(x, y)
+            elif op == "local":
+                dc.decolorize_tonemap_local(x, y)
+            else:
+                dc.decolorize_tonemap_global(x, y, mode="sigmoid" if op == "global" else "histeq", stats=st)
+            torch.cuda.synchronize()
+            results.append((y.cpu(), st.cpu()))
+    finally:
+        dc.set_tuning(op_code, dt_code, *orig)
+    for y, st in results[1:]:
+        assert torch.equal(y, results[0][0])
+        assert torch.equal(st, results[0][1])
+
+
+def test_launch_counts(dc):
+    import torch
+    from paper_2108_13656_gb300 import synth
+    a = to_dev(synth.s_ldr(64, 32, 1))
+    b = to_dev(synth.s_ldr(32, 64, 2))
+    c = to_dev(synth.s_hdr(48, 16, 3))
+    outs = [torch.empty((32, 64), device="cuda"), torch.empty((64, 32), device="cuda"),
+            torch.empty((16, 48), device="cuda")]
+    dc.decolorize_tonemap_global([a, b], outs[:2])
+    assert dc.last_launch_count() == 1
+    dc.decolorize_tonemap_global([a, b, c], outs)
+    assert dc.last_launch_count() == 2  # one persistent launch per input sample type
+
+
+def test_cuda_graph_capture_matches_eager(dc):
+    import torch
+    from paper_2108_13656_gb300 import synth
+    imgs = [synth.s_ldr(640, 480, i) for i in range(4)]
+    xs = [to_dev(im) for im in imgs]
+    eager = [torch.empty((480, 640), dtype=torch.uint8, device="cuda") for _ in imgs]
+    outs = [torch.empty_like(e) for e in eager]
+    ws = dc.Workspace()
+    dc.decolorize_tonemap_global(xs, eager, workspace=ws)  # sizes the workspace
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            dc.decolorize_tonemap_global(xs, outs, workspace=ws)
+    torch.cuda.current_stream().wait_stream(s)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    for e, o in zip(eager, outs):
+        assert torch.equal(e, o)
