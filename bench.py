@@ -1,0 +1,373 @@
+#!/usr/bin/env python3
+"""Benchmark: decolorization (Eq. 1-6) fused with global and local tone mapping on GB300.
+
+Workload (one "step"): the 3840x2160 image in its two variants - 8-bit sRGB
+(S-LDR, seed 1) and FP32 linear HDR with log-normal luminance over 5 decades
+(S-HDR, mu = 0, sigma = 2.5, seed 2) - each through decolorize -> global
+centred-sigmoid tone map and decolorize -> local smoothed-LHE tone map, i.e. four
+C-ABI calls per step and every step of the hot path.  Inputs are synthetic and
+resident in HBM before timing; L2 is flushed (a 256 MiB write) before every timed
+call and each call is timed with CUDA events on its stream.
+
+Prints ONE JSON line (rank 0).  `value` is whole-job Gpix/s (output pixels of all
+four calls, all ranks) over device time; `e2e` repeats the step through the public
+API with pinned host buffers, host<->device copies inside the timed region.
+`--impl reference` times the FP64 CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+W, H = 3840, 2160
+NPIX = W * H
+METRIC = "Gpix/s and % of HBM roofline"
+L2_FLUSH_BYTES = 256 << 20
+OPS = [  # (name, input variant, operation, output dtype, algorithmic bytes per pixel)
+    ("u8_global", "u8", "global", "u8", 3 + 1),
+    ("f32_global", "f32", "global", "f32", 12 + 4),
+    ("u8_local", "u8", "local", "u8", 3 + 1),
+    ("f32_local", "f32", "local", "f32", 12 + 4),
+]
+WORKLOAD = ("3840x2160 8-bit sRGB (S-LDR seed 1) + FP32 linear HDR, 5 decades log-normal "
+            "(S-HDR mu=0 sigma=2.5 seed 2); each -> decolorize+global sigmoid TM and "
+            "decolorize+local smoothed-LHE TM (s=32, R=2, 32 bins)")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--busy-s", type=float, default=0.3, help="device-busy period while clock sampling starts")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def aggregate(local_ms: float, world: int, reduce_max) -> tuple[float, float]:
+    """Whole-job time = max over ranks; units = every rank's pixels (weak scaling)."""
+    t = reduce_max(local_ms)
+    return t, world * 4 * NPIX / (t * 1e-3) / 1e9
+
+
+def make_inputs():
+    from paper_2108_13656_gb300 import synth
+    ldr = synth.s_ldr(W, H, seed=1)
+    hdr = synth.s_hdr(W, H, seed=2, decades=5.0, sigma=2.5)
+    return {"u8": ldr, "f32": hdr}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": float(max(smax)) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2108_13656_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(op_name: str):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current kernels."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    v = d.get("per_launch_bytes", {}).get(op_name)
+    return float(v) if v is not None else None
+
+
+# ----------------------------------------------------------------- CPU oracle ----
+def oracle_step(imgs, rows: int):
+    """The FP64 oracle on a band of `rows` rows of each variant, all four operations."""
+    import oracle
+    n = 0
+    for name, var, op, _, _ in OPS:
+        img = imgs[var][:rows]
+        if op == "global":
+            oracle.tonemap_global(img)
+        else:
+            oracle.tonemap_local(img)
+        n += img.shape[0] * img.shape[1]
+    return n
+
+
+def cpu_baseline(imgs, budget_s: float = 12.0):
+    import oracle
+    oracle.build()
+    rows = 135  # 1/16 of the image per operation
+    t0 = time.perf_counter()
+    n = oracle_step(imgs, rows)
+    dt = time.perf_counter() - t0
+    reps = max(1, int(budget_s / max(dt, 1e-3)))
+    reps = min(reps, 16)
+    t0 = time.perf_counter()
+    tot = 0
+    for _ in range(reps):
+        tot += oracle_step(imgs, rows)
+    dt = time.perf_counter() - t0
+    return {"value": tot / dt / 1e9, "unit": "Gpix/s", "cores": 1, "kind": "oracle",
+            "sample": "%d repetitions of a %d-row band (%d px) of both 3840-wide variants through all "
+                      "four operations, FP64 C oracle, single thread" % (reps, rows, rows * W)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    imgs = make_inputs()
+    import oracle
+    oracle.build()
+    rows = 135
+    for _ in range(max(0, args.warmup)):
+        oracle_step(imgs, rows)
+    t0 = time.perf_counter()
+    n = 0
+    for _ in range(args.steps):
+        n += oracle_step(imgs, rows)
+    dt = time.perf_counter() - t0
+    val = n / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Gpix/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3 / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD + "; each step a %d-row band of each variant" % rows},
+            "cpu_baseline": {"value": val, "unit": "Gpix/s", "cores": 1, "kind": "oracle",
+                             "sample": "%d-row band (%d px) of both variants through all four operations "
+                                       "per step" % (rows, rows * W)},
+            "e2e": {"value": val, "unit": "Gpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# --------------------------------------------------------------------- native ----
+def run_native(args):
+    import torch
+    import paper_2108_13656_gb300 as dc
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dc.load()
+    imgs = make_inputs()
+    x = {k: torch.from_numpy(v).to(dev) for k, v in imgs.items()}
+    outs = {}
+    for name, var, op, odt, _ in OPS:
+        outs[name] = torch.empty((H, W), dtype=torch.uint8 if odt == "u8" else torch.float32, device=dev)
+    ws = dc.Workspace(device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    calls = {}
+    for name, var, op, _, _ in OPS:
+        if op == "global":
+            calls[name] = dc.PreparedCall("global", x[var], outs[name], mode="sigmoid", workspace=ws)
+        else:
+            calls[name] = dc.PreparedCall("local", x[var], outs[name], workspace=ws)
+
+    def call(name, var, op, out):
+        calls[name]()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    for _ in range(max(3, args.warmup)):
+        for name, var, op, _, _ in OPS:
+            call(name, var, op, outs[name])
+    torch.cuda.synchronize()
+    assert dc.query_status(ws) == 0
+    # keep the device busy while the samplers start
+    t_end = time.perf_counter() + args.busy_s
+    while time.perf_counter() < t_end:
+        for name, var, op, _, _ in OPS:
+            call(name, var, op, outs[name])
+        torch.cuda.synchronize()
+
+    K = args.steps
+    ev = {name: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+          for name, *_ in OPS}
+    launches = 0
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    torch.cuda._sleep(20_000_000)  # let the host queue run ahead of the device
+    for k in range(K):
+        for name, var, op, _, _ in OPS:
+            flush.fill_(k & 0xFF)  # evict L2 (256 MiB write), outside the timed pair
+            s, e = ev[name][k]
+            s.record(stream)
+            call(name, var, op, outs[name])
+            e.record(stream)
+            launches += dc.last_launch_count()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    op_ms = {name: float(np.mean([s.elapsed_time(e) for s, e in ev[name]])) for name, *_ in OPS}
+    step_ms = sum(op_ms.values())
+    assert dc.query_status(ws) == 0
+
+    def reduce_max(v):
+        if world == 1:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    t_max, gpix = aggregate(step_ms, world, reduce_max)
+
+    # end to end through the public API with pinned host buffers
+    hx = {k: torch.from_numpy(v).pin_memory() for k, v in imgs.items()}
+    hy = {name: torch.empty(outs[name].shape, dtype=outs[name].dtype).pin_memory() for name in outs}
+    h2d = sum(t.numel() * t.element_size() for t in hx.values())
+    d2h = sum(t.numel() * t.element_size() for t in hy.values())
+    E = max(3, args.e2e_steps)
+    for it in range(2 + E):
+        if it == 2:
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+        for k in x:
+            x[k].copy_(hx[k], non_blocking=True)
+        for name, var, op, _, _ in OPS:
+            call(name, var, op, outs[name])
+        for name in outs:
+            hy[name].copy_(outs[name], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / E
+    e2e_ms = reduce_max(e2e_ms)
+    e2e_val = world * 4 * NPIX / (e2e_ms * 1e-3) / 1e9
+
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        return 0
+
+    peak, peak_kind = measured_peak()
+    dom = max(op_ms, key=op_ms.get)
+    bpp = {name: b for name, _, _, _, b in OPS}[dom]
+    achieved = bpp * NPIX / (op_ms[dom] * 1e-3) / 1e9
+    traffic = ncu_traffic(dom)
+    per_op = {name: {"ms": op_ms[name],
+                     "GBps": {n: b for n, _, _, _, b in OPS}[name] * NPIX / (op_ms[name] * 1e-3) / 1e9,
+                     "frac_of_measured_hbm": {n: b for n, _, _, _, b in OPS}[name] * NPIX / (op_ms[name] * 1e-3) / 1e9 / peak}
+              for name in op_ms}
+    line = {
+        "metric": METRIC, "value": gpix, "unit": "Gpix/s", "n_gpus": world, "steps": K,
+        "warmup": max(3, args.warmup), "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "pixels_per_step": 4 * NPIX, "l2": "flushed (256 MiB write) before every timed call",
+                   "parallelism": "replicas" if world > 1 else "single GPU", "per_op": per_op},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": bpp * NPIX},
+        "e2e": {"value": e2e_val, "unit": "Gpix/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_ms},
+        "clocks": clk,
+        "gpu_launches": launches,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(imgs)
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_native(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -210,6 +210,18 @@ DC_API int dc_set_wait_timeout_ns(uint64_t ns);
  * timeout above).  Default 0. */
 DC_API int dc_debug_withhold_ready(int32_t on);
 
+/* Profiling switch for later calls (default 0).  When on, each launch records per
+ * image and phase the earliest tile start and latest tile end (globaltimer ns) and,
+ * summed over CTAs, the time spent waiting for earlier phases, for free stages, for
+ * tiles and for stage data.  Adds a few atomics per tile. */
+DC_API int dc_debug_profile(int32_t on);
+
+/* Synchronises `stream` and copies the profile of the last launch that used `ws`
+ * into out[]: 8 launch counters (dependency wait, stage wait, tile wait, data wait,
+ * tiles, kernel start, kernel end, reserved) followed, for each of the first n_img
+ * images of that launch, by 4 phase start and 4 phase end timestamps. */
+DC_API int dc_debug_read_profile(const void* ws, int32_t n_img, uint64_t* out, void* stream);
+
 /* Number of kernels the last successful call on this thread enqueued. */
 DC_API int dc_last_launch_count(void);
 

@@ -20,7 +20,9 @@ from ._abi import (  # noqa: F401
     DC_U8,
     STATS_BYTES,
     DcError,
+    PreparedCall,
     Workspace,
+    debug_profile,
     debug_withhold_ready,
     decolorize,
     decolorize_tonemap_global,
@@ -32,6 +34,7 @@ from ._abi import (  # noqa: F401
     local_params,
     parse_stats,
     query_status,
+    read_profile,
     set_tuning,
     set_wait_timeout_ns,
     status_string,

@@ -77,6 +77,8 @@ _SIGS = {
     "dc_get_tuning": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
     "dc_set_wait_timeout_ns": (ctypes.c_int, [ctypes.c_uint64]),
     "dc_debug_withhold_ready": (ctypes.c_int, [ctypes.c_int32]),
+    "dc_debug_profile": (ctypes.c_int, [ctypes.c_int32]),
+    "dc_debug_read_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "dc_last_launch_count": (ctypes.c_int, []),
     "dc_version": (ctypes.c_int, []),
 }
@@ -86,7 +88,8 @@ _lib_lock = threading.Lock()
 
 
 def library_path() -> str:
-    return build_lib.LIB
+    """The shared library the binding loads: $DC_LIBRARY if set, else the in-tree build."""
+    return os.environ.get("DC_LIBRARY") or build_lib.LIB
 
 
 def load(build_if_missing: bool = True):
@@ -95,7 +98,7 @@ def load(build_if_missing: bool = True):
     with _lib_lock:
         if _lib is not None:
             return _lib
-        path = build_lib.LIB
+        path = os.environ.get("DC_LIBRARY") or build_lib.LIB
         if not os.path.exists(path):
             if not build_if_missing:
                 raise RuntimeError("libdecolor.so is not built (run __graft_entry__.build())")
@@ -213,65 +216,95 @@ def _workspace(op, ins, n, lp, ws):
         dev = torch.cuda.current_device()
         ws = _default_ws.setdefault(dev, Workspace(device="cuda:%d" % dev))
     ptr, size = ws.get(need)
-    return ptr, size, ws
+    return ptr, size, ws.buf
 
 
 # ------------------------------------------------------------------ calls ----
+def local_params(block_s: int = 32, radius_blocks: int = 2, bins: int = 32, alpha: float = 1.0,
+                 delta: float = 1e-4) -> dc_local_params:
+    return dc_local_params(block_s, radius_blocks, bins, alpha, delta, 0)
+
+
+class PreparedCall:
+    """One ABI call with its descriptors, parameters and workspace resolved once.
+
+    op is "decolorize", "global" or "local"; calling the object enqueues the call on
+    `stream` (default: torch's current stream).  The tensors must stay alive and in
+    place for as long as the object is used.
+    """
+
+    def __init__(self, op: str, inputs, outputs, beta_r: float = BETA_R, beta_k: float = BETA_K,
+                 mode="sigmoid", gain_k: float = 1.0, delta: float = 1e-4, stats=None, block_s: int = 32,
+                 radius_blocks: int = 2, bins: int = 32, alpha: float = 1.0, workspace=None):
+        self.lib = load()
+        self.inputs, self.outputs = _as_list(inputs), _as_list(outputs)
+        self.n = len(self.inputs)
+        self.ins, self.outs = _arrays(self.inputs, self.outputs)
+        self.p = dc_decolor_params(beta_r, beta_k)
+        self.op = op
+        self.stats = stats
+        self.lp = None
+        if op == "decolorize":
+            code = DC_OP_DECOLORIZE
+        elif op == "global":
+            code = DC_OP_GLOBAL
+            m = {"sigmoid": DC_SIGMOID, "histeq": DC_HISTEQ}.get(mode, mode)
+            self.g = dc_global_params(int(m), gain_k, delta, 0)
+            self.sp = None
+            if stats is not None:
+                if not stats.is_cuda or stats.numel() * stats.element_size() < STATS_BYTES * self.n:
+                    raise ValueError("stats buffer must be a CUDA tensor of n * STATS_BYTES bytes")
+                self.sp = ctypes.c_void_p(stats.data_ptr())
+        elif op == "local":
+            code = DC_OP_LOCAL
+            self.lp = local_params(block_s, radius_blocks, bins, alpha, delta)
+        else:
+            raise ValueError("unknown op %r" % op)
+        # keep the buffer itself: a later, larger request may replace the Workspace's buffer
+        self.ws_ptr, self.ws_size, self.ws_buf = _workspace(code, self.ins, self.n, self.lp, workspace)
+        self._ws = ctypes.c_void_p(self.ws_ptr)
+
+    def __call__(self, stream=None):
+        st = _stream_handle(stream)
+        if self.op == "decolorize":
+            rc = self.lib.dc_decolorize(self.ins, self.outs, self.n, ctypes.byref(self.p), self._ws,
+                                        self.ws_size, st)
+            name = "dc_decolorize"
+        elif self.op == "global":
+            rc = self.lib.dc_decolorize_tonemap_global(self.ins, self.outs, self.n, ctypes.byref(self.p),
+                                                       ctypes.byref(self.g), self.sp, self._ws, self.ws_size, st)
+            name = "dc_decolorize_tonemap_global"
+        else:
+            rc = self.lib.dc_decolorize_tonemap_local(self.ins, self.outs, self.n, ctypes.byref(self.p),
+                                                      ctypes.byref(self.lp), self._ws, self.ws_size, st)
+            name = "dc_decolorize_tonemap_local"
+        if rc != DC_OK:
+            raise DcError(rc, name)
+        return self.outputs
+
+
 def decolorize(inputs, outputs, beta_r: float = BETA_R, beta_k: float = BETA_K, workspace=None,
                stream=None):
     """Eq. 1-6 over a (ragged) batch: outputs[i] = L(inputs[i])."""
-    inputs, outputs = _as_list(inputs), _as_list(outputs)
-    ins, outs = _arrays(inputs, outputs)
-    p = dc_decolor_params(beta_r, beta_k)
-    ptr, size, _ = _workspace(DC_OP_DECOLORIZE, ins, len(inputs), None, workspace)
-    rc = load().dc_decolorize(ins, outs, len(inputs), ctypes.byref(p), ctypes.c_void_p(ptr), size,
-                              _stream_handle(stream))
-    if rc != DC_OK:
-        raise DcError(rc, "dc_decolorize")
-    return outputs
+    return PreparedCall("decolorize", inputs, outputs, beta_r=beta_r, beta_k=beta_k,
+                        workspace=workspace)(stream)
 
 
 def decolorize_tonemap_global(inputs, outputs, mode: str | int = "sigmoid", gain_k: float = 1.0,
                               delta: float = 1e-4, stats=None, beta_r: float = BETA_R,
                               beta_k: float = BETA_K, workspace=None, stream=None):
     """Eq. 1-6 then the global curve; `stats` is None or a uint8 CUDA tensor of n*STATS_BYTES."""
-    inputs, outputs = _as_list(inputs), _as_list(outputs)
-    ins, outs = _arrays(inputs, outputs)
-    m = {"sigmoid": DC_SIGMOID, "histeq": DC_HISTEQ}.get(mode, mode)
-    p = dc_decolor_params(beta_r, beta_k)
-    g = dc_global_params(int(m), gain_k, delta, 0)
-    sp = None
-    if stats is not None:
-        if stats.numel() * stats.element_size() < STATS_BYTES * len(inputs) or not stats.is_cuda:
-            raise ValueError("stats buffer too small")
-        sp = ctypes.c_void_p(stats.data_ptr())
-    ptr, size, _ = _workspace(DC_OP_GLOBAL, ins, len(inputs), None, workspace)
-    rc = load().dc_decolorize_tonemap_global(ins, outs, len(inputs), ctypes.byref(p), ctypes.byref(g), sp,
-                                             ctypes.c_void_p(ptr), size, _stream_handle(stream))
-    if rc != DC_OK:
-        raise DcError(rc, "dc_decolorize_tonemap_global")
-    return outputs
-
-
-def local_params(block_s: int = 32, radius_blocks: int = 2, bins: int = 32, alpha: float = 1.0,
-                 delta: float = 1e-4) -> dc_local_params:
-    return dc_local_params(block_s, radius_blocks, bins, alpha, delta, 0)
+    return PreparedCall("global", inputs, outputs, beta_r=beta_r, beta_k=beta_k, mode=mode, gain_k=gain_k,
+                        delta=delta, stats=stats, workspace=workspace)(stream)
 
 
 def decolorize_tonemap_local(inputs, outputs, block_s: int = 32, radius_blocks: int = 2, bins: int = 32,
                              alpha: float = 1.0, delta: float = 1e-4, beta_r: float = BETA_R,
                              beta_k: float = BETA_K, workspace=None, stream=None):
     """Eq. 1-6 then smoothed local-histogram equalisation."""
-    inputs, outputs = _as_list(inputs), _as_list(outputs)
-    ins, outs = _arrays(inputs, outputs)
-    p = dc_decolor_params(beta_r, beta_k)
-    lp = local_params(block_s, radius_blocks, bins, alpha, delta)
-    ptr, size, _ = _workspace(DC_OP_LOCAL, ins, len(inputs), lp, workspace)
-    rc = load().dc_decolorize_tonemap_local(ins, outs, len(inputs), ctypes.byref(p), ctypes.byref(lp),
-                                            ctypes.c_void_p(ptr), size, _stream_handle(stream))
-    if rc != DC_OK:
-        raise DcError(rc, "dc_decolorize_tonemap_local")
-    return outputs
+    return PreparedCall("local", inputs, outputs, beta_r=beta_r, beta_k=beta_k, block_s=block_s,
+                        radius_blocks=radius_blocks, bins=bins, alpha=alpha, delta=delta,
+                        workspace=workspace)(stream)
 
 
 def workspace_bytes(op: int, inputs, lparams: dc_local_params | None = None) -> int:
@@ -312,6 +345,27 @@ def set_wait_timeout_ns(ns: int):
 
 def debug_withhold_ready(on: bool):
     load().dc_debug_withhold_ready(1 if on else 0)
+
+
+def debug_profile(on: bool):
+    load().dc_debug_profile(1 if on else 0)
+
+
+def read_profile(workspace, n_img: int = 1, stream=None) -> dict:
+    """Profile of the last launch on `workspace` (a Workspace or a PreparedCall)."""
+    buf = workspace.ws_buf if hasattr(workspace, "ws_buf") else workspace.buf
+    out = (ctypes.c_uint64 * (8 + n_img * 8))()
+    rc = load().dc_debug_read_profile(ctypes.c_void_p(buf.data_ptr()), n_img, out, _stream_handle(stream))
+    if rc != DC_OK:
+        raise DcError(rc, "dc_debug_read_profile")
+    v = list(out)
+    res = {"dep_wait_ns": v[0], "stage_wait_ns": v[1], "tile_wait_ns": v[2], "data_wait_ns": v[3],
+           "tiles": v[4], "kernel_ns": v[6] - v[5], "images": []}
+    for i in range(n_img):
+        st = v[8 + i * 8: 12 + i * 8]
+        en = v[12 + i * 8: 16 + i * 8]
+        res["images"].append([(s - v[5], e - v[5]) if s else None for s, e in zip(st, en)])
+    return res
 
 
 def last_launch_count() -> int:

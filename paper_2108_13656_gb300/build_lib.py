@@ -41,18 +41,22 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None) -> str:
-    """Compile and link libdecolor.so; returns its path.  Raises on compiler errors."""
+def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | None = None,
+          lib_path: str | None = None, obj_dir: str | None = None) -> str:
+    """Compile and link libdecolor.so (or `lib_path`); returns its path.  Raises on
+    compiler errors.  `extra_flags` go to every nvcc compile (e.g. -D options)."""
+    lib = lib_path or LIB
+    objdir = obj_dir or OBJDIR
     with _lock:
-        if not force and up_to_date():
+        if not force and lib_path is None and up_to_date():
             return LIB
         nvcc = nvcc_path()
-        os.makedirs(OBJDIR, exist_ok=True)
+        os.makedirs(objdir, exist_ok=True)
         flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden",
                         "-I", os.path.join(ROOT, "include")] + list(extra_flags or [])
         procs = []
         for src in SOURCES:
-            obj = os.path.join(OBJDIR, src.replace(".cu", ".o"))
+            obj = os.path.join(objdir, src.replace(".cu", ".o"))
             cmd = [nvcc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
             procs.append((cmd, obj, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
         objs, errors = [], []
@@ -65,14 +69,14 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
             objs.append(obj)
         if errors:
             raise RuntimeError("nvcc failed:\n" + "\n".join(errors))
-        tmp = LIB + ".tmp%d" % os.getpid()
+        tmp = lib + ".tmp%d" % os.getpid()
         link = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + objs + [
             "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
         res = subprocess.run(link, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
         if res.returncode != 0:
             raise RuntimeError("link failed:\n" + " ".join(link) + "\n" + res.stdout.decode(errors="replace"))
-        os.replace(tmp, LIB)
-        return LIB
+        os.replace(tmp, lib)
+        return lib
 
 
 if __name__ == "__main__":

@@ -19,7 +19,8 @@ constexpr int kOpkDecolor = 0, kOpkGlobal = 1, kOpkLocal = 2;
 constexpr int64_t kHeaderBytes = 256;
 constexpr int64_t kMaxPixels = int64_t(1) << 28;
 constexpr int kMaxLocalSide = 1 << 16;
-constexpr int kLocMaxBlocksX = 64;
+constexpr int kLocMaxBlocksX = 32;
+constexpr int kCdfChunk = 16;
 
 std::mutex g_mu;
 dc_tuning g_tune[3][3] = {
@@ -29,6 +30,7 @@ dc_tuning g_tune[3][3] = {
 };
 unsigned long long g_timeout_ns = 2000000000ull;
 int g_withhold = 0;
+int g_profile = 0;
 thread_local int g_last_launches = 0;
 
 int esz(int dt) { return dt == DC_U8 ? 1 : (dt == DC_F16 ? 2 : 4); }
@@ -154,7 +156,11 @@ void make_geometry(const dc_image_in& in, const dc_image_out& out, const OpArgs&
     bool vec = al16(in.data) && al16(out.data);
     if (im.rows > 1) vec = vec && (in.stride_bytes % 16 == 0) && (out.stride_bytes % 16 == 0);
     im.flags = vec ? IF_VEC : 0u;
-    if (op.opk != kOpkDecolor && in.dtype != DC_U8 && out.dtype == DC_F32) im.flags |= IF_LPLANE;
+    if (op.opk != kOpkDecolor && in.dtype != DC_U8 && out.dtype == DC_F32) {
+        im.flags |= IF_LPLANE;
+        // the local operator and HDR histogram equalisation only need ln(L + delta)
+        if (op.opk == kOpkLocal || (op.opk == kOpkGlobal && op.g->mode == DC_HISTEQ)) im.flags |= IF_PLANE_LOG;
+    }
     im.tiles_x = (im.cols + tile_cols - 1) / tile_cols;
     const int tiles_y = (im.rows + tile_rows - 1) / tile_rows;
     g.local_bytes = 0;
@@ -170,7 +176,7 @@ void make_geometry(const dc_image_in& in, const dc_image_out& out, const OpArgs&
     (void)tu;
     for (int p = 0; p < n_phase; ++p) {
         if (op.opk == kOpkLocal)
-            g.tiles[p] = kinds[p] == PK_CDF ? im.Hb : im.Hb * im.tiles_x_loc;
+            g.tiles[p] = kinds[p] == PK_CDF ? im.Hb * ((im.Wb + kCdfChunk - 1) / kCdfChunk) : im.Hb * im.tiles_x_loc;
         else
             g.tiles[p] = tiles_y * im.tiles_x;
     }
@@ -204,6 +210,7 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
         std::lock_guard<std::mutex> lk(g_mu);
         b->timeout_ns = g_timeout_ns;
         b->withhold_ready = g_withhold ? 1u : 0u;
+        b->profile = g_profile ? 1u : 0u;
     }
     if (op.opk == kOpkGlobal) {
         b->mode = op.g->mode;
@@ -214,6 +221,9 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
         b->stats = op.stats;
     } else if (op.opk == kOpkLocal) {
         b->block_s = op.l->block_s;
+        // ceil(2^32 / s) for s >= 2 (2^32 itself does not fit: s = 1 is flagged by 0)
+        b->s_magic = op.l->block_s == 1 ? 0u
+                     : (uint32_t)(((uint64_t(1) << 32) + (uint64_t)op.l->block_s - 1) / (uint64_t)op.l->block_s);
         b->radius = op.l->radius_blocks;
         b->bins = op.l->bins;
         b->alpha = op.l->alpha;
@@ -495,6 +505,35 @@ DC_API int dc_debug_withhold_ready(int32_t on)
 {
     std::lock_guard<std::mutex> lk(g_mu);
     g_withhold = on ? 1 : 0;
+    return DC_OK;
+}
+
+DC_API int dc_debug_profile(int32_t on)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_profile = on ? 1 : 0;
+    return DC_OK;
+}
+
+DC_API int dc_debug_read_profile(const void* ws, int32_t n_img, uint64_t* out, void* stream)
+{
+    if (!ws || !out || n_img < 0 || n_img > kCapLarge) return DC_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return DC_ERR_CUDA;
+    const uint8_t* ctrl = static_cast<const uint8_t*>(ws) + kHeaderBytes;
+    DcCtrl c;
+    if (cudaMemcpy(&c, ctrl, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess) return DC_ERR_CUDA;
+    for (int i = 0; i < PROF_SLOTS; ++i) out[i] = c.prof[i];
+    out[PROF_KSTART_NOT] = ~out[PROF_KSTART_NOT];
+    for (int i = 0; i < n_img; ++i) {
+        DcImgCtrl ic;
+        if (cudaMemcpy(&ic, ctrl + sizeof(DcCtrl) + (size_t)i * sizeof(DcImgCtrl), sizeof(ic),
+                       cudaMemcpyDeviceToHost) != cudaSuccess)
+            return DC_ERR_CUDA;
+        for (int p = 0; p < kMaxPhases; ++p) {
+            out[PROF_SLOTS + i * 2 * kMaxPhases + p] = ic.t_start_not[p] ? ~ic.t_start_not[p] : 0ull;
+            out[PROF_SLOTS + i * 2 * kMaxPhases + kMaxPhases + p] = ic.t_end[p];
+        }
+    }
     return DC_OK;
 }
 

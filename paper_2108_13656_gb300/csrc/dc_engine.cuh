@@ -20,8 +20,8 @@
 namespace dc {
 
 constexpr int kThreads = 256;
-constexpr int kLocMaxBlocksX = 64;    // max blocks per local tile row
-constexpr int kCdfChunk = 64;         // block columns per CDF sub-pass
+constexpr int kLocMaxBlocksX = 32;    // max blocks per local tile row
+constexpr int kCdfChunk = 16;         // block columns per CDF tile
 constexpr int kMaxRadius = 16;
 
 template <int IN_DT> struct InT;
@@ -97,6 +97,24 @@ __device__ __forceinline__ unsigned long long globaltimer_ns()
     return t;
 }
 
+// ------------------------------------------------------- fast binary32 math --
+// Hardware approximations (PTX sqrt.approx / rcp.approx, and the lg2/ex2 based
+// intrinsics); their errors are a few ulp, far inside the 2e-6 parity tolerance.
+__device__ __forceinline__ float sqrt_fast(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float rcp_fast(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ln_fast(float x) { return __logf(x); }
+__device__ __forceinline__ float exp_fast(float x) { return __expf(x); }
+
 // ------------------------------------------------------------- Eq. 1-6 -------
 struct Beta {
     float bR, one_m_bR, bk, one_m_bk;
@@ -106,32 +124,39 @@ struct Beta {
 __device__ __forceinline__ float luminance_f32(float R, float G, float B, const Beta& be)
 {
     const float S = R + G + B;
-    const float L_WHITE = sqrtf(fmaf(R, R, fmaf(G, G, B * B)) * (1.0f / 3.0f));  // Eq. 1
-    const float L_B = B;                                                       // Eq. 2
-    const float L_GR = sqrtf(fmaf(be.bR, R * R, be.one_m_bR * (G * G)));        // Eq. 3
-    const float inv = 1.0f / S;
+    const float L_WHITE = sqrt_fast(fmaf(R, R, fmaf(G, G, B * B)) * (1.0f / 3.0f));  // Eq. 1
+    const float L_B = B;                                                           // Eq. 2
+    const float L_GR = sqrt_fast(fmaf(be.bR, R * R, be.one_m_bR * (G * G)));        // Eq. 3
+    const float inv = rcp_fast(S);
     const float r = R * inv, b = B * inv;
-    const float L_WARM = fmaf(r, L_GR - L_WHITE, L_WHITE);                      // Eq. 4
-    const float L_COOL = fmaf(b, L_WHITE - L_B, L_B);                           // Eq. 5
-    const float L = sqrtf(fmaf(be.bk, L_WARM * L_WARM, be.one_m_bk * (L_COOL * L_COOL)));  // Eq. 6
+    const float L_WARM = fmaf(r, L_GR - L_WHITE, L_WHITE);                          // Eq. 4
+    const float L_COOL = fmaf(b, L_WHITE - L_B, L_B);                               // Eq. 5
+    const float L = sqrt_fast(fmaf(be.bk, L_WARM * L_WARM, be.one_m_bk * (L_COOL * L_COOL)));  // Eq. 6
     return S > 0.0f ? L : 0.0f;
 }
 
-// Linear samples of arbitrary magnitude: Eq. 1-6 are 1-homogeneous, so scale the
-// pixel by a power of two into a safe range first (exact), then scale back.
+// Linear samples of arbitrary magnitude: Eq. 1-6 are 1-homogeneous, so a pixel
+// whose squares leave the binary32 range is scaled by a power of two first (exact)
+// and the result scaled back.
+static __device__ __noinline__ float luminance_rescaled(float R, float G, float B, const Beta& be)
+{
+    const float m = fmaxf(R, fmaxf(G, B));
+    int e;
+    frexpf(m, &e);
+    const float s = ldexpf(1.0f, -e);
+    return ldexpf(luminance_f32(R * s, G * s, B * s, be), e);
+}
+
 __device__ __forceinline__ float luminance_hdr(float R, float G, float B, const Beta& be)
 {
     R = fmaxf(R, 0.0f);
     G = fmaxf(G, 0.0f);
     B = fmaxf(B, 0.0f);
-    const float m = fmaxf(R, fmaxf(G, B));
-    if (m > 0x1p60f || (m < 0x1p-60f && m > 0.0f)) {
-        int e;
-        frexpf(m, &e);
-        const float s = ldexpf(1.0f, -e);
-        return ldexpf(luminance_f32(R * s, G * s, B * s, be), e);
-    }
-    return luminance_f32(R, G, B, be);
+    const float L = luminance_f32(R, G, B, be);
+    // samples beyond about 2^63 overflow the squares (inf or NaN); samples below
+    // about 2^-63 flush them (0 for a non-black pixel): both take the scaled path
+    if (!(L <= 3.0e38f) || (L == 0.0f && R + G + B > 0.0f)) return luminance_rescaled(R, G, B, be);
+    return L;
 }
 
 // 8-bit code of y in [0,1]: floor(255 y + 1/2), clamped.
@@ -164,60 +189,62 @@ struct GroupIO {
     static constexpr int G = InT<IN_DT>::G;
     static constexpr int ESZ = InT<IN_DT>::ESZ;
 
-    // Luminance in [0,1] units (8-bit codes / 255; linear values as they are)
-    // of the n pixels starting at (r, c).  vec: full 16-byte aligned group.
+    // Luminance in [0,1] units (8-bit codes / 255; linear values as they are) of a
+    // full group given as its 48 raw bytes (twelve 32-bit words).
+    __device__ static __forceinline__ void decode(const uint32_t (&w)[12], const Beta& be, float (&Lv)[G])
+    {
+        if constexpr (IN_DT == DC_U8) {
+#pragma unroll
+            for (int k = 0; k < G; ++k)
+                Lv[k] = luminance_f32(u8_at(w, 3 * k), u8_at(w, 3 * k + 1), u8_at(w, 3 * k + 2), be) *
+                        (1.0f / 255.0f);
+        } else if constexpr (IN_DT == DC_F16) {
+            float f[24];
+#pragma unroll
+            for (int k = 0; k < 12; ++k) {
+                __half2 h;
+                memcpy(&h, &w[k], 4);
+                float2 v = __half22float2(h);
+                f[2 * k] = v.x;
+                f[2 * k + 1] = v.y;
+            }
+#pragma unroll
+            for (int k = 0; k < G; ++k) Lv[k] = luminance_hdr(f[3 * k], f[3 * k + 1], f[3 * k + 2], be);
+        } else {
+#pragma unroll
+            for (int k = 0; k < G; ++k)
+                Lv[k] = luminance_hdr(__uint_as_float(w[3 * k]), __uint_as_float(w[3 * k + 1]),
+                                      __uint_as_float(w[3 * k + 2]), be);
+        }
+    }
+
+    // Luminance of the n pixels starting at (r, c) read straight from global memory.
+    // vec: full 16-byte aligned group.
     __device__ static void luminance(const DcImage& im, int r, int c, int n, bool vec,
                                      const Beta& be, float (&Lv)[G])
     {
         const uint8_t* p = im.in + (int64_t)r * im.in_stride + (int64_t)c * 3 * ESZ;
         if (vec) {
-            uint4 a = ld_stream16(p), b = ld_stream16(p + 16), d = ld_stream16(p + 32);
-            if constexpr (IN_DT == DC_U8) {
-                const uint32_t w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, d.x, d.y, d.z, d.w};
-#pragma unroll
-                for (int k = 0; k < G; ++k)
-                    Lv[k] = luminance_f32(u8_at(w, 3 * k), u8_at(w, 3 * k + 1), u8_at(w, 3 * k + 2), be) *
-                            (1.0f / 255.0f);
-            } else if constexpr (IN_DT == DC_F16) {
-                const uint32_t w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, d.x, d.y, d.z, d.w};
-                float f[24];
-#pragma unroll
-                for (int k = 0; k < 12; ++k) {
-                    __half2 h;
-                    memcpy(&h, &w[k], 4);
-                    float2 v = __half22float2(h);
-                    f[2 * k] = v.x;
-                    f[2 * k + 1] = v.y;
-                }
-#pragma unroll
-                for (int k = 0; k < G; ++k) Lv[k] = luminance_hdr(f[3 * k], f[3 * k + 1], f[3 * k + 2], be);
-            } else {
-                const float f[12] = {__uint_as_float(a.x), __uint_as_float(a.y), __uint_as_float(a.z),
-                                     __uint_as_float(a.w), __uint_as_float(b.x), __uint_as_float(b.y),
-                                     __uint_as_float(b.z), __uint_as_float(b.w), __uint_as_float(d.x),
-                                     __uint_as_float(d.y), __uint_as_float(d.z), __uint_as_float(d.w)};
-#pragma unroll
-                for (int k = 0; k < G; ++k) Lv[k] = luminance_hdr(f[3 * k], f[3 * k + 1], f[3 * k + 2], be);
-            }
+            const uint4 a = ld_stream16(p), b = ld_stream16(p + 16), d = ld_stream16(p + 32);
+            const uint32_t w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, d.x, d.y, d.z, d.w};
+            decode(w, be, Lv);
         } else {
 #pragma unroll
-            for (int k = 0; k < G; ++k) {
-                if (k < n) {
-                    const uint8_t* q = p + k * 3 * ESZ;
-                    if constexpr (IN_DT == DC_U8) {
-                        Lv[k] = luminance_f32((float)__ldg(q), (float)__ldg(q + 1), (float)__ldg(q + 2), be) *
-                                (1.0f / 255.0f);
-                    } else if constexpr (IN_DT == DC_F16) {
-                        const __half* h = reinterpret_cast<const __half*>(q);
-                        Lv[k] = luminance_hdr(__half2float(h[0]), __half2float(h[1]), __half2float(h[2]), be);
-                    } else {
-                        const float* f = reinterpret_cast<const float*>(q);
-                        Lv[k] = luminance_hdr(__ldg(f), __ldg(f + 1), __ldg(f + 2), be);
-                    }
-                } else {
-                    Lv[k] = 0.0f;
-                }
-            }
+            for (int k = 0; k < G; ++k) Lv[k] = (k < n) ? scalar_luminance(p + k * 3 * ESZ, be) : 0.0f;
+        }
+    }
+
+    // One pixel through the scalar path (ragged tails and unaligned images).
+    __device__ static __noinline__ float scalar_luminance(const uint8_t* q, const Beta& be)
+    {
+        if constexpr (IN_DT == DC_U8) {
+            return luminance_f32((float)__ldg(q), (float)__ldg(q + 1), (float)__ldg(q + 2), be) * (1.0f / 255.0f);
+        } else if constexpr (IN_DT == DC_F16) {
+            const __half* h = reinterpret_cast<const __half*>(q);
+            return luminance_hdr(__half2float(h[0]), __half2float(h[1]), __half2float(h[2]), be);
+        } else {
+            const float* f = reinterpret_cast<const float*>(q);
+            return luminance_hdr(__ldg(f), __ldg(f + 1), __ldg(f + 2), be);
         }
     }
 
@@ -313,23 +340,30 @@ __device__ __forceinline__ float pairwise_sum(const float* v)
 }
 
 // ------------------------------------------------------------ waits -----------
-// Bounded wait for a phase-complete flag.  Returns 0 when the flag is set, 1 when
-// the launch has an error or the wait ran out (then DC_ERR_TIMEOUT is recorded).
-static __device__ __noinline__ int wait_ready(const uint32_t* flag, uint32_t* err, unsigned long long timeout_ns)
+__device__ __forceinline__ void red_release_add(uint32_t* p, uint32_t v)
 {
-    if (ld_acquire_u32(flag)) return 0;
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded wait until *count >= target (the tiles of a phase all published).  Returns
+// 0 on success, 1 when the launch has an error or the wait ran out (then
+// DC_ERR_TIMEOUT is recorded in *err).
+static __device__ __noinline__ int wait_count(const uint32_t* count, uint32_t target, uint32_t* err,
+                                              unsigned long long timeout_ns)
+{
+    if (ld_acquire_u32(count) >= target) return 0;
     const unsigned long long t0 = globaltimer_ns();
     const unsigned long long max_iter = timeout_ns / 16ull + 4096ull;
     unsigned ns = 32;
     for (unsigned long long it = 0;; ++it) {
-        if (ld_acquire_u32(flag)) return 0;
+        if (ld_acquire_u32(count) >= target) return 0;
         if (ld_relaxed_u32(err)) return 1;
         if (globaltimer_ns() - t0 > timeout_ns || it > max_iter) {
             atomicCAS(err, 0u, (uint32_t)DC_ERR_TIMEOUT);
             return 1;
         }
         __nanosleep(ns);
-        if (ns < 1024) ns *= 2;
+        if (ns < 512) ns *= 2;
     }
 }
 
@@ -366,12 +400,13 @@ __device__ __forceinline__ DcImgCtrl* img_ctrl(DcCtrl* c, int i)
     return reinterpret_cast<DcImgCtrl*>(reinterpret_cast<uint8_t*>(c) + sizeof(DcCtrl)) + i;
 }
 
-// Normalised log luminance u for the HDR histogram forms.
-__device__ __forceinline__ float log_u(float L, float delta, float lmin, float inv_range)
+// Normalised log luminance u in [0,1] for the HDR histogram forms, from a plane
+// value that is either L or already ln(L + delta).
+__device__ __forceinline__ float log_u(float val, bool is_log, float delta, float lmin, float inv_range)
 {
     if (inv_range == 0.0f) return 0.5f;
-    const float u = (logf(L + delta) - lmin) * inv_range;
-    return fminf(fmaxf(u, 0.0f), 1.0f);
+    const float v = is_log ? val : ln_fast(val + delta);
+    return fminf(fmaxf((v - lmin) * inv_range, 0.0f), 1.0f);
 }
 
 }  // namespace dc

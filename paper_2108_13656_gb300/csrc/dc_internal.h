@@ -36,6 +36,7 @@ enum PhaseKind : int32_t {
 enum : uint32_t {
     IF_VEC = 1u,      // 16-byte aligned pointers and strides: vector path
     IF_LPLANE = 2u,   // out is an f32 plane that holds L between phases
+    IF_PLANE_LOG = 4u,  // ... and it holds ln(L + delta) instead of L
 };
 
 struct DcImage {                 // 80 bytes
@@ -60,24 +61,42 @@ struct DcSegment {               // 8 bytes
     int8_t reverse;              // hand the tiles out last-first (L2 reuse)
 };
 
-// Per-image control block, cleared by the host before every launch.
+// Per-image control block, cleared by the host before every launch.  Tiles publish
+// their completion by incrementing done[phase] with release semantics; a tile of the
+// next phase waits (acquire) until the count reaches the phase's tile count and then
+// derives what it needs (mu, lmin, lmax, cumulative tables) from the integer
+// accumulators itself, so no tile has to finalise a phase.
 struct DcImgCtrl {
     uint32_t done[kMaxPhases];
-    uint32_t ready[kMaxPhases];
     unsigned long long logsum;   // two's complement, units of 2^-20
     uint32_t lmax_ord;           // ordered-uint encoding of max ln(L+delta)
     uint32_t lmin_nord;          // bitwise NOT of the ordered encoding of the min
-    float mu, lmin, lmax, exp_mu;
-    float inv_range;             // 1 / (lmax - lmin), 0 when lmax == lmin
-    uint32_t pad[7];
+    uint32_t pad[2];
+    // profiling (only when enabled): per phase, NOT of the earliest tile start and
+    // the latest tile end, in globaltimer nanoseconds
+    unsigned long long t_start_not[kMaxPhases];
+    unsigned long long t_end[kMaxPhases];
     uint32_t hist[256];
-    float lut[260];              // LDR HISTEQ: y per gray code; HDR HISTEQ: cumulative edges
+};
+
+// Profile counters of one launch (only when enabled), summed over CTAs, ns.
+enum ProfSlot {
+    PROF_DEP_WAIT = 0,    // producer: waiting for earlier phases
+    PROF_EMPTY_WAIT = 1,  // producer: waiting for a free stage
+    PROF_TILE_WAIT = 2,   // consumers: waiting for the next tile message
+    PROF_DATA_WAIT = 3,   // consumers: waiting for stage data
+    PROF_TILES = 4,       // tiles processed
+    PROF_KSTART_NOT = 5,  // NOT of the earliest CTA start
+    PROF_KEND = 6,        // latest CTA end
+    PROF_SLOTS = 8
 };
 
 // Per-launch control block, cleared by the host before the launch.
 struct DcCtrl {
     uint32_t next_tile;
-    uint32_t pad[63];
+    uint32_t pad[15];
+    unsigned long long prof[PROF_SLOTS];
+    uint32_t pad2[32];
     // followed by DcImgCtrl[n]
 };
 
@@ -100,8 +119,10 @@ struct DcBatch {
     int32_t gain_is_one;
     int32_t need_gray_hist;            // LDR: gray histogram wanted (HISTEQ or stats)
     int32_t block_s, radius, bins;
+    uint32_t s_magic;                  // ceil(2^32 / block_s), 0 for block_s = 1: exact division of offsets < 2^16
     float alpha;
     uint32_t withhold_ready;
+    uint32_t profile;                  // record phase timestamps and wait counters
     unsigned long long timeout_ns;
     DcCtrl* ctrl;
     uint32_t* err;                     // call-level error word (workspace header)
