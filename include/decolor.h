@@ -145,7 +145,7 @@ typedef struct {
     float logmax;         /* max of ln(L + delta) */
     float reserved0;
     int64_t logsum_fixed; /* exact sum over pixels of ln(L + delta) in units of 2^-20,
-                             each 16/8/4-pixel vector group rounded once */
+                             each 8-pixel (u8, f16) or 4-pixel (f32) group rounded once */
     int64_t npix;         /* width * height */
     uint32_t hist[256];   /* LDR: 8-bit gray-code histogram (always filled);
                              HDR: the DC_HISTEQ u-bin histogram (zeros in DC_SIGMOID) */

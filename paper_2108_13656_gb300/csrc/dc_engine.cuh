@@ -25,51 +25,38 @@ constexpr int kCdfChunk = 16;         // block columns per CDF tile
 constexpr int kMaxRadius = 16;
 
 template <int IN_DT> struct InT;
-template <> struct InT<DC_U8> { static constexpr int G = 16; static constexpr int ESZ = 1; };
+template <> struct InT<DC_U8> { static constexpr int G = 8; static constexpr int ESZ = 1; };
 template <> struct InT<DC_F16> { static constexpr int G = 8; static constexpr int ESZ = 2; };
 template <> struct InT<DC_F32> { static constexpr int G = 4; static constexpr int ESZ = 4; };
 
 enum OpKind { OPK_DECOLOR = 0, OPK_GLOBAL = 1, OPK_LOCAL = 2 };
 
 // ------------------------------------------------------------ memory access ---
+// Input pixels: read-only for the whole launch, so the loads may be scheduled
+// freely (not volatile); no L1 allocation, normal L2 caching.
 __device__ __forceinline__ uint4 ld_stream16(const void* p)
 {
     uint4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p));
+    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p));
     return v;
 }
 
-__device__ __forceinline__ float4 ld_cg_f4(const float* p)
+__device__ __forceinline__ uint2 ld_stream8(const void* p)
 {
-    float4 v;
-    asm volatile("ld.global.cg.v4.f32 {%0,%1,%2,%3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "l"(p));
+    uint2 v;
+    asm("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
     return v;
 }
 
-__device__ __forceinline__ float ld_cg_f(const float* p)
-{
-    float v;
-    asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(p));
-    return v;
-}
-
-__device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long* p)
-{
-    unsigned long long v;
-    asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p));
-    return v;
-}
-
-__device__ __forceinline__ uint32_t ld_cg_u32(const uint32_t* p)
-{
-    uint32_t v;
-    asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p));
-    return v;
-}
+// Data other CTAs of the same launch wrote (the L plane, histograms, tables):
+// L2 only, never a stale L1 line.  Ordinary loads to the compiler, so independent
+// ones are issued back to back.
+__device__ __forceinline__ float4 ld_cg_f4(const float* p) { return __ldcg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float ld_cg_f(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long* p) { return __ldcg(p); }
+__device__ __forceinline__ uint32_t ld_cg_u32(const uint32_t* p) { return __ldcg(p); }
 
 __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p)
 {
@@ -218,6 +205,22 @@ struct GroupIO {
         }
     }
 
+    // The raw bytes of a full, aligned group: 24 (u8, three 8-byte loads) or 48
+    // (f16, f32, three 16-byte loads).
+    __device__ static __forceinline__ void load_raw(const DcImage& im, int r, int c, uint32_t (&w)[12])
+    {
+        const uint8_t* p = im.in + (int64_t)r * im.in_stride + (int64_t)c * 3 * ESZ;
+        if constexpr (IN_DT == DC_U8) {
+            const uint2 a = ld_stream8(p), b = ld_stream8(p + 8), d = ld_stream8(p + 16);
+            w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y; w[4] = d.x; w[5] = d.y;
+        } else {
+            const uint4 a = ld_stream16(p), b = ld_stream16(p + 16), d = ld_stream16(p + 32);
+            w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+            w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+            w[8] = d.x; w[9] = d.y; w[10] = d.z; w[11] = d.w;
+        }
+    }
+
     // Luminance of the n pixels starting at (r, c) read straight from global memory.
     // vec: full 16-byte aligned group.
     __device__ static void luminance(const DcImage& im, int r, int c, int n, bool vec,
@@ -225,8 +228,8 @@ struct GroupIO {
     {
         const uint8_t* p = im.in + (int64_t)r * im.in_stride + (int64_t)c * 3 * ESZ;
         if (vec) {
-            const uint4 a = ld_stream16(p), b = ld_stream16(p + 16), d = ld_stream16(p + 32);
-            const uint32_t w[12] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, d.x, d.y, d.z, d.w};
+            uint32_t w[12];
+            load_raw(im, r, c, w);
             decode(w, be, Lv);
         } else {
 #pragma unroll

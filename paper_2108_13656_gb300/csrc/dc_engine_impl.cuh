@@ -1,13 +1,34 @@
-// Engine kernel body: tile queue, producer warp (TMA streaming), consumer warps
-// (per-phase tile work).  Included by one translation unit per input sample type.
+// Engine kernel body: tile queue with phase dependencies, and the per-phase tile
+// work.  Included by one translation unit per input sample type.
 #pragma once
 
-#include "dc_pipe.cuh"
+#include "dc_engine.cuh"
 
 namespace dc {
 
 struct TileRect {
     int r0, r1, c0, c1;
+};
+
+// Values a tile derives from an image's finished statistics pass.
+struct Derived {
+    float mu, exp_mu, lmin, lmax, inv_range;
+};
+
+// What thread 0 hands the CTA for the next tile (tile < 0: no more work).
+struct TileMsg {
+    int tile, lt, img, p;
+    Derived d;
+};
+
+__device__ __forceinline__ void cta_sync() { __syncthreads(); }
+
+// Groups a thread loads before computing any of them (memory-level parallelism):
+// the light plane-reading phases keep 64 bytes in flight per thread; the
+// compute-heavy RGB phases rely on the number of warps instead.
+template <int IN_DT, bool PLANE>
+struct Unroll {
+    static constexpr int value = PLANE ? (InT<IN_DT>::G == 4 ? 4 : 2) : 1;
 };
 
 // ------------------------------------------------------------ tile geometry ---
@@ -28,7 +49,7 @@ __device__ __forceinline__ int phase_tiles(const DcBatch<CAP>& P, const DcImage&
 }
 
 // Rectangle of tile lt of a phase; for the local operator also its block row I
-// (and, for the CDF phase, its first block column J0 in tr.c0).
+// (for the CDF phase, tr.c0..tr.c1 are block columns).
 template <int OPK, int CAP>
 __device__ __forceinline__ TileRect tile_rect(const DcBatch<CAP>& P, const DcImage& im, int kind, int lt, int& I)
 {
@@ -66,50 +87,6 @@ __device__ __forceinline__ bool from_plane(const DcImage& im, int kind)
     return (im.flags & IF_LPLANE) != 0 && kind != PK_STATS && kind != PK_DECOLOR;
 }
 
-// ----------------------------------------------------------------- producer ---
-// Streams the tile's full groups into the stage ring, in the chunk order the
-// consumers use.  Returns false when a wait ran out.
-template <int IN_DT, int CAP>
-__device__ bool produce_tile(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps, Ring& data, const DcImage& im,
-                             const TileRect& t, bool plane)
-{
-    using PS = PipeSmem<IN_DT>;
-    constexpr int G = InT<IN_DT>::G, ESZ = InT<IN_DT>::ESZ, SG = PS::kGroups;
-    const ChunkGeo g = chunk_geo<SG>(t.r0, t.r1, t.c0, t.c1, G, (im.flags & IF_VEC) != 0);
-    if (g.nchunks == 0) return true;
-    const int bpp = plane ? 4 : 3 * ESZ;
-    const int bpg = G * bpp;
-    const uint8_t* base = (plane ? im.out : im.in) + (int64_t)t.c0 * bpp;
-    const int64_t stride = plane ? im.out_stride : im.in_stride;
-    if (plane) fence_proxy_async_global();
-    ChunkCursor<SG> cur;
-    cur.start(g, t.r0);
-    for (int k = 0; k < g.nchunks; ++k) {
-        if (!mbar_test_wait(&ps.empty[data.idx], data.parity ^ 1u)) {
-            const unsigned long long t0 = P.profile ? globaltimer_ns() : 0ull;
-            if (!mbar_wait_slow(&ps.empty[data.idx], data.parity ^ 1u, P.err, P.timeout_ns)) return false;
-            if (P.profile) atomicAdd(&P.ctrl->prof[PROF_EMPTY_WAIT], globaltimer_ns() - t0);
-        }
-        unsigned char* dst = ps.stage[data.idx];
-        unsigned long long* full = &ps.full[data.idx];
-        if (g.ngv <= SG) {
-            const int rows = min(g.rpc, t.r1 - cur.row);
-            const uint32_t row_bytes = (uint32_t)(g.ngv * bpg);
-            mbar_arrive_expect_tx(full, row_bytes * (uint32_t)rows);
-            const uint8_t* src = base + (int64_t)cur.row * stride;
-            for (int j = 0; j < rows; ++j, src += stride) tma_load_1d(dst + ((j << g.lg) * bpg), src, row_bytes, full);
-        } else {
-            const int ng = min(SG, g.ngv - cur.g0);
-            const uint32_t bytes = (uint32_t)(ng * bpg);
-            mbar_arrive_expect_tx(full, bytes);
-            tma_load_1d(dst, base + (int64_t)cur.row * stride + (int64_t)cur.g0 * bpg, bytes, full);
-        }
-        cur.next(g);
-        data.advance(PS::kStages);
-    }
-    return true;
-}
-
 // mu, lmin, lmax from the exact integer accumulators of a finished stats pass.
 __device__ __forceinline__ Derived derive(const DcImgCtrl* ic, long long N)
 {
@@ -124,152 +101,69 @@ __device__ __forceinline__ Derived derive(const DcImgCtrl* ic, long long N)
     return d;
 }
 
-// One lane of the producer warp: pulls tiles from the queue (one ahead), waits
-// for the phases a tile depends on, hands the tile to the consumers and streams
-// its pixels.
-template <int IN_DT, int OPK, int CAP>
-__device__ void producer_loop(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps)
+// ------------------------------------------------------------- group walk ---
+// Visit every group of a tile: f(r, c, n, vec, v) with the group's source values
+// v (the luminance from RGB, or the plane values).  Groups start at columns that
+// are multiples of G from the row start, whatever the tile shape.  Threads form a
+// TXT x (256/TXT) grid, TXT the smallest power of two covering a row's groups, so
+// the mapping needs no integer division; each thread issues the loads of U groups
+// before computing any of them.
+template <int IN_DT, bool PLANE, class F>
+__device__ __forceinline__ void walk_tile(const DcImage& im, const TileRect& t, const Beta& be, F&& f)
 {
-    Ring data{0u, 0u}, tring{0u, 0u};
-    int next = (int)atomicAdd(&P.ctrl->next_tile, 1u);
-    int sg_i = 0;
-    // image whose phases [0, ready_p) are known complete, with its derived values
-    int ready_img = -1, ready_p = 0;
-    Derived ready_d = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-    for (;;) {
-        TileMsg m;
-        m.tile = -1;
-        int kind = PK_CDF;
-        const int tile = next;
-        if (tile < P.total_tiles && ld_relaxed_u32(P.err) == 0) {
-            next = (int)atomicAdd(&P.ctrl->next_tile, 1u);  // overlaps this tile
-            while (sg_i + 1 < P.n_seg && P.seg[sg_i + 1].start <= tile) ++sg_i;
-            const DcSegment sg = P.seg[sg_i];
-            const int nt = (sg_i + 1 < P.n_seg ? P.seg[sg_i + 1].start : P.total_tiles) - sg.start;
-            int lt = tile - sg.start;
-            if (sg.reverse) lt = nt - 1 - lt;
-            const int img = sg.img, p = sg.phase;
-            const DcImage& im = P.img[img];
-            DcImgCtrl* ic = img_ctrl(P.ctrl, img);
-            bool ok = true;
-            const int known = img == ready_img ? ready_p : 0;
-            if (p > known) {
-                // every earlier phase of this image must have published all its tiles
-                const unsigned long long t0 = P.profile ? globaltimer_ns() : 0ull;
-                for (int q = p - 1; q >= known && ok; --q)
-                    ok = wait_count(&ic->done[q], (uint32_t)phase_tiles<OPK>(P, im, P.phase_kind[q]), P.err,
-                                    P.timeout_ns) == 0;
-                if (P.profile) atomicAdd(&P.ctrl->prof[PROF_DEP_WAIT], globaltimer_ns() - t0);
-                if (ok) {
-                    if (img != ready_img && P.phase_kind[0] == PK_STATS)
-                        ready_d = derive(ic, (long long)im.prow * (long long)im.pcol);
-                    ready_img = img;
-                    ready_p = p;
+    constexpr int G = InT<IN_DT>::G, U = Unroll<IN_DT, PLANE>::value;
+    const int gpr = (t.c1 - t.c0 + G - 1) / G;
+    const int lg = gpr >= kThreads ? 8 : 32 - __clz(gpr - 1);
+    const int txt = 1 << lg;
+    const int tx = threadIdx.x & (txt - 1);
+    const int rpi = kThreads >> lg;
+    const bool vec_img = (im.flags & IF_VEC) != 0;
+    for (int r = t.r0 + (threadIdx.x >> lg); r < t.r1; r += rpi) {
+        for (int g = tx; g < gpr; g += U * txt) {
+            int c[U], n[U];
+            bool vec[U];
+            float v[U][G];
+            uint32_t w[U][PLANE ? 1 : 12];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int gu = g + u * txt;
+                c[u] = t.c0 + gu * G;
+                n[u] = gu < gpr ? min(G, t.c1 - c[u]) : 0;
+                vec[u] = vec_img && n[u] == G;
+                if (n[u] > 0) {
+                    if constexpr (PLANE) {
+                        GroupIO<IN_DT>::from_plane(im, r, c[u], n[u], vec[u], v[u]);
+                    } else {
+                        if (vec[u])
+                            GroupIO<IN_DT>::load_raw(im, r, c[u], w[u]);
+                        else
+                            GroupIO<IN_DT>::luminance(im, r, c[u], n[u], false, be, v[u]);
+                    }
                 }
             }
-            if (ok) {
-                m.tile = tile;
-                m.lt = lt;
-                m.img = img;
-                m.p = p;
-                m.d = ready_d;
-                kind = P.phase_kind[p];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                if (n[u] > 0) {
+                    if constexpr (!PLANE) {
+                        if (vec[u]) GroupIO<IN_DT>::decode(w[u], be, v[u]);
+                    }
+                    f(r, c[u], n[u], vec[u], v[u]);
+                }
             }
-        }
-        if (!mbar_wait(&ps.tempty[tring.idx], tring.parity ^ 1u, P.err, P.timeout_ns)) return;
-        ps.msg[tring.idx] = m;
-        mbar_arrive(&ps.tfull[tring.idx]);
-        tring.advance(kTileRing);
-        if (m.tile < 0) return;
-        if (kind != PK_CDF) {
-            const DcImage& im = P.img[m.img];
-            int I;
-            const TileRect tr = tile_rect<OPK>(P, im, kind, m.lt, I);
-            if (!produce_tile<IN_DT>(P, ps, data, im, tr, from_plane(im, kind))) return;
         }
     }
 }
 
-// ---------------------------------------------------------------- consumers ---
-// Visit every group of a tile: full groups from the stage ring, then the scalar
-// remainder (ragged row ends, or every group of an unaligned image) from global
-// memory.  f(r, c, n, vec, v) gets the group's source values v: the luminance
-// (from RGB) or the plane values.
-template <int IN_DT, int CAP, class F>
-__device__ __forceinline__ void consume_tile(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps, Ring& data,
-                                             const DcImage& im, const TileRect& t, bool plane, const Beta& be, F&& f)
+template <int IN_DT, class F>
+__device__ __forceinline__ void consume_tile(const DcImage& im, const TileRect& t, bool plane, const Beta& be, F&& f)
 {
-    using PS = PipeSmem<IN_DT>;
-    constexpr int G = InT<IN_DT>::G, SG = PS::kGroups, GPT = PS::kGPT;
-    const bool vec_img = (im.flags & IF_VEC) != 0;
-    const ChunkGeo g = chunk_geo<SG>(t.r0, t.r1, t.c0, t.c1, G, vec_img);
-    const int tid = threadIdx.x;
-    ChunkCursor<SG> cur;
-    cur.start(g, t.r0);
-    for (int k = 0; k < g.nchunks; ++k) {
-        bool ok = mbar_test_wait(&ps.full[data.idx], data.parity);
-        if (!ok) {
-            const unsigned long long t0 = (P.profile && tid == 0) ? globaltimer_ns() : 0ull;
-            ok = mbar_wait_slow(&ps.full[data.idx], data.parity, P.err, P.timeout_ns);
-            if (P.profile && tid == 0) atomicAdd(&P.ctrl->prof[PROF_DATA_WAIT], globaltimer_ns() - t0);
-        }
-        int r[GPT], c[GPT];
-        bool valid[GPT];
-        float v[GPT][G];
-        uint32_t w[GPT][12];
-#pragma unroll
-        for (int i = 0; i < GPT; ++i) {
-            const int sidx = tid + i * kThreads;
-            valid[i] = cur.slot(g, t.r1, t.c0, G, sidx, r[i], c[i]) && ok;
-            if (valid[i]) {
-                if (plane) {
-                    const float4* q = reinterpret_cast<const float4*>(ps.stage[data.idx] + sidx * (4 * G));
-#pragma unroll
-                    for (int j = 0; j < G / 4; ++j) {
-                        const float4 x = q[j];
-                        v[i][4 * j] = x.x;
-                        v[i][4 * j + 1] = x.y;
-                        v[i][4 * j + 2] = x.z;
-                        v[i][4 * j + 3] = x.w;
-                    }
-                } else {
-                    const uint4* q = reinterpret_cast<const uint4*>(ps.stage[data.idx] + sidx * 48);
-                    const uint4 a = q[0], b = q[1], d = q[2];
-                    w[i][0] = a.x; w[i][1] = a.y; w[i][2] = a.z; w[i][3] = a.w;
-                    w[i][4] = b.x; w[i][5] = b.y; w[i][6] = b.z; w[i][7] = b.w;
-                    w[i][8] = d.x; w[i][9] = d.y; w[i][10] = d.z; w[i][11] = d.w;
-                }
-            }
-        }
-        __syncwarp();
-        if ((tid & 31) == 0) mbar_arrive(&ps.empty[data.idx]);
-        data.advance(PS::kStages);
-        cur.next(g);
-#pragma unroll
-        for (int i = 0; i < GPT; ++i) {
-            if (valid[i]) {
-                if (!plane) GroupIO<IN_DT>::decode(w[i], be, v[i]);
-                f(r[i], c[i], G, true, v[i]);
-            }
-        }
-    }
-    const int c_rem = t.c0 + g.ngv * G;
-    if (c_rem < t.c1) {
-        // scalar remainder, rows spread over threads, groups at multiples of G
-        const int gpr = (t.c1 - c_rem + G - 1) / G;
-        const int nslots = (t.r1 - t.r0) * gpr;
-        for (int s = tid; s < nslots; s += kThreads) {
-            const int rr = s / gpr;
-            const int r = t.r0 + rr;
-            const int c = c_rem + (s - rr * gpr) * G;
-            const int n = min(G, t.c1 - c);
-            float v[G];
-            if (plane)
-                GroupIO<IN_DT>::from_plane(im, r, c, n, false, v);
-            else
-                GroupIO<IN_DT>::luminance(im, r, c, n, false, be, v);
-            f(r, c, n, false, v);
-        }
+    if constexpr (IN_DT == DC_U8) {
+        walk_tile<IN_DT, false>(im, t, be, f);  // 8-bit images never keep a plane
+    } else {
+        if (plane)
+            walk_tile<IN_DT, true>(im, t, be, f);
+        else
+            walk_tile<IN_DT, false>(im, t, be, f);
     }
 }
 
@@ -303,16 +197,16 @@ __device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t* scratc
         if (lane >= o) v += u;
     }
     if (lane == 31) scratch[warp] = v;
-    consumer_sync();
+    cta_sync();
     uint32_t off = 0;
     for (int w = 0; w < warp; ++w) off += scratch[w];
-    consumer_sync();
+    cta_sync();
     return v + off;
 }
 
 // ------------------------------------------------------------- phase: stats --
 template <int IN_DT, int CAP>
-__device__ void tile_stats(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps, Ring& data, const DcImage& im, DcImgCtrl* ic,
+__device__ void tile_stats(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* ic,
                            const TileRect& t, const Beta& be, unsigned char* smem)
 {
     constexpr int G = InT<IN_DT>::G;
@@ -322,12 +216,12 @@ __device__ void tile_stats(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps, Ring& dat
     const bool plane_log = (im.flags & IF_PLANE_LOG) != 0;
     if (want_hist) {
         for (int b = threadIdx.x; b < 256; b += kThreads) S.hist[b] = 0;
-        consumer_sync();
+        cta_sync();
     }
     long long acc = 0;
     float vmin = INFINITY, vmax = -INFINITY;
     const float delta = P.delta;
-    consume_tile<IN_DT>(P, ps, data, im, t, false, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+    consume_tile<IN_DT>(im, t, false, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
         float v[G];
 #pragma unroll
         for (int k = 0; k < G; ++k) {
@@ -352,11 +246,11 @@ __device__ void tile_stats(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps, Ring& dat
         S.wmin[warp] = vmin;
         S.wmax[warp] = vmax;
     }
-    consumer_sync();
+    cta_sync();
     if (threadIdx.x == 0) {
         long long s = 0;
         float mn = INFINITY, mx = -INFINITY;
-        for (int w = 0; w < kConsumerWarps; ++w) {
+        for (int w = 0; w < (kThreads / 32); ++w) {
             s += S.wsum[w];
             mn = fminf(mn, S.wmin[w]);
             mx = fmaxf(mx, S.wmax[w]);
@@ -375,7 +269,7 @@ __device__ void tile_stats(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps, Ring& dat
 
 // ---------------------------------------------------------- phase: log hist --
 template <int IN_DT, int CAP>
-__device__ void tile_loghist(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps, Ring& data, const DcImage& im, DcImgCtrl* ic,
+__device__ void tile_loghist(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* ic,
                              const TileRect& t, const Beta& be, const Derived& d, unsigned char* smem)
 {
     constexpr int G = InT<IN_DT>::G;
@@ -384,8 +278,8 @@ __device__ void tile_loghist(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps, Ring& d
     const bool plane = from_plane(im, PK_LOGHIST);
     const bool is_log = (im.flags & IF_PLANE_LOG) != 0;
     const float delta = P.delta;
-    consumer_sync();
-    consume_tile<IN_DT>(P, ps, data, im, t, plane, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+    cta_sync();
+    consume_tile<IN_DT>(im, t, plane, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
 #pragma unroll
         for (int k = 0; k < G; ++k)
             if (k < n) {
@@ -393,7 +287,7 @@ __device__ void tile_loghist(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps, Ring& d
                 atomicAdd(&S.hist[min((int)(256.0f * u), 255)], 1u);
             }
     });
-    consumer_sync();
+    cta_sync();
     for (int b = threadIdx.x; b < 256; b += kThreads)
         if (S.hist[b]) atomicAdd(&ic->hist[b], S.hist[b]);
 }
@@ -418,7 +312,7 @@ __device__ void write_stats(const DcBatch<CAP>& P, const DcImage& im, const DcIm
 
 // ------------------------------------------------------- phase: global apply --
 template <int IN_DT, int CAP>
-__device__ void tile_apply_global(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps, Ring& data, const DcImage& im,
+__device__ void tile_apply_global(const DcBatch<CAP>& P, const DcImage& im,
                                   DcImgCtrl* ic, const TileRect& t, const Beta& be, const Derived& d,
                                   unsigned char* smem)
 {
@@ -430,7 +324,7 @@ __device__ void tile_apply_global(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps, Ri
     if (P.mode == DC_SIGMOID) {
         const float mu = d.mu, exp_mu = d.exp_mu, k = P.gain_k;
         const bool one = P.gain_is_one != 0;
-        consume_tile<IN_DT>(P, ps, data, im, t, plane, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+        consume_tile<IN_DT>(im, t, plane, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
 #pragma unroll
             for (int j = 0; j < G; ++j) {
                 const float x = Lv[j] + delta;
@@ -452,9 +346,9 @@ __device__ void tile_apply_global(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps, Ri
             S.lut[threadIdx.x] = __uint2float_rn(cum - h) * invN;  // edge b: count(bins < b) / N
             if (threadIdx.x == 0) S.lut[256] = 1.0f;
         }
-        consumer_sync();
+        cta_sync();
         const bool ldr = P.ldr != 0;
-        consume_tile<IN_DT>(P, ps, data, im, t, plane, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+        consume_tile<IN_DT>(im, t, plane, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
 #pragma unroll
             for (int j = 0; j < G; ++j) {
                 if (ldr) {
@@ -473,7 +367,7 @@ __device__ void tile_apply_global(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps, Ri
 
 // ---------------------------------------------------- phase: local histograms --
 template <int IN_DT, int CAP>
-__device__ void tile_blockh(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps, Ring& data, const DcImage& im,
+__device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im,
                             const TileRect& t, int I, const Beta& be, const Derived& d, unsigned char* smem)
 {
     constexpr int G = InT<IN_DT>::G;
@@ -487,8 +381,8 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps, Ring& da
     const bool ldr = P.ldr != 0;
     const float delta = P.delta, Bf = (float)B;
     const uint32_t magic = P.s_magic;
-    consumer_sync();
-    consume_tile<IN_DT>(P, ps, data, im, t, plane, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+    cta_sync();
+    consume_tile<IN_DT>(im, t, plane, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
         int cur = -1;
         unsigned long long acc = 0ull;
 #pragma unroll
@@ -524,7 +418,7 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps, Ring& da
         }
         if (cur >= 0) atomicAdd(&S.h[cur], acc);
     });
-    consumer_sync();
+    cta_sync();
     // unpack: bin j holds count_j * 2^24 - F_j + F_{j-1}
     const unsigned long long mask = (1ull << kCountShift) - 1ull;
     unsigned long long* H = reinterpret_cast<unsigned long long*>(P.ws + im.ws_hist);
@@ -558,9 +452,9 @@ __device__ void tile_cdf(const DcBatch<CAP>& P, const DcImage& im, int I, const 
         for (int I2 = i0; I2 <= i1; ++I2) v += ld_cg_u64(&H[((size_t)I2 * Wb + jj) * B + j]);
         S.v[k] = v;
     }
-    consumer_sync();
+    cta_sync();
     const int nout = t.c1 - t.c0;
-    for (int o = warp; o < nout; o += kConsumerWarps) {
+    for (int o = warp; o < nout; o += (kThreads / 32)) {
         const int J = J0 + o;
         unsigned long long w = 0ull;
         if (lane < B) {
@@ -582,7 +476,7 @@ __device__ void tile_cdf(const DcBatch<CAP>& P, const DcImage& im, int I, const 
 
 // ------------------------------------------------------- phase: local apply --
 template <int IN_DT, int CAP>
-__device__ void tile_apply_local(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps, Ring& data, const DcImage& im,
+__device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im,
                                  const TileRect& t, int I, const Beta& be, const Derived& d, unsigned char* smem)
 {
     constexpr int G = InT<IN_DT>::G;
@@ -604,8 +498,8 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps, Rin
     const bool is_log = plane && (im.flags & IF_PLANE_LOG) != 0;
     const bool ldr = P.ldr != 0;
     const float delta = P.delta, Bf = (float)B, inv_s = 1.0f / (float)s, alpha = P.alpha;
-    consumer_sync();
-    consume_tile<IN_DT>(P, ps, data, im, t, plane, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+    cta_sync();
+    consume_tile<IN_DT>(im, t, plane, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
         const float fy = fmaf((float)r + 0.5f, inv_s, -0.5f);
         const float fly = floorf(fy);
         const float wy = fy - fly;
@@ -645,130 +539,167 @@ struct PhaseSmem {
     static constexpr size_t value = OPK == OPK_GLOBAL ? sizeof(SmemApplyG) + sizeof(SmemStats) : SmemBytes<OPK>::value;
 };
 
-template <int IN_DT, int OPK>
-constexpr size_t engine_smem_bytes()
-{
-    return sizeof(PipeSmem<IN_DT>) + PhaseSmem<OPK>::value + 64;
-}
+#ifndef DC_MIN_CTAS
+#define DC_MIN_CTAS 4
+#endif
+
+// Thread 0 of a CTA: the next tile from the queue (fetched one ahead), after the
+// phases it depends on have published all their tiles.  Per image it remembers
+// which phases are known complete and the values derived from the stats pass.
+// Finished tiles are counted locally and published with one release when the CTA
+// moves to another (image, phase), before it blocks on any wait, and at exit, so
+// a CTA never waits while holding unpublished completions.
+template <int OPK, int CAP>
+struct TileSource {
+    int next, sg_i, ready_img, ready_p;
+    Derived ready_d;
+    int pend_img, pend_p;
+    uint32_t pend_n;
+
+    __device__ void init(const DcBatch<CAP>& P)
+    {
+        next = (int)atomicAdd(&P.ctrl->next_tile, 1u);
+        sg_i = 0;
+        ready_img = -1;
+        ready_p = 0;
+        ready_d = Derived{0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        pend_img = -1;
+        pend_p = 0;
+        pend_n = 0u;
+    }
+
+    // Called after a CTA barrier that follows the counted tiles' last writes.
+    __device__ void flush(const DcBatch<CAP>& P)
+    {
+        if (pend_n) {
+            if (!(P.withhold_ready && pend_p == 0))
+                red_release_add(&img_ctrl(P.ctrl, pend_img)->done[pend_p], pend_n);
+            pend_n = 0u;
+        }
+    }
+
+    __device__ void finished(int img, int p)
+    {
+        pend_img = img;
+        pend_p = p;
+        ++pend_n;
+    }
+
+    __device__ TileMsg fetch(const DcBatch<CAP>& P)
+    {
+        TileMsg m;
+        m.tile = -1;
+        const int tile = next;
+        if (tile >= P.total_tiles) {
+            flush(P);
+            return m;
+        }
+        next = (int)atomicAdd(&P.ctrl->next_tile, 1u);  // overlaps this tile's work
+        while (sg_i + 1 < P.n_seg && P.seg[sg_i + 1].start <= tile) ++sg_i;
+        const DcSegment sg = P.seg[sg_i];
+        const int nt = (sg_i + 1 < P.n_seg ? P.seg[sg_i + 1].start : P.total_tiles) - sg.start;
+        int lt = tile - sg.start;
+        if (sg.reverse) lt = nt - 1 - lt;
+        const int img = sg.img, p = sg.phase;
+        if (img != pend_img || p != pend_p) flush(P);
+        const int known = img == ready_img ? ready_p : 0;
+        if (p > known) {
+            flush(P);
+            const DcImage& im = P.img[img];
+            DcImgCtrl* ic = img_ctrl(P.ctrl, img);
+            const unsigned long long t0 = P.profile ? globaltimer_ns() : 0ull;
+            bool ok = true;
+            // every earlier phase of this image must have published all its tiles
+            for (int q = p - 1; q >= known && ok; --q)
+                ok = wait_count(&ic->done[q], (uint32_t)phase_tiles<OPK>(P, im, P.phase_kind[q]), P.err,
+                                P.timeout_ns) == 0;
+            if (P.profile) atomicAdd(&P.ctrl->prof[PROF_DEP_WAIT], globaltimer_ns() - t0);
+            if (!ok) return m;
+            if (img != ready_img && P.phase_kind[0] == PK_STATS)
+                ready_d = derive(ic, (long long)im.prow * (long long)im.pcol);
+            ready_img = img;
+            ready_p = p;
+        }
+        m.tile = tile;
+        m.lt = lt;
+        m.img = img;
+        m.p = p;
+        m.d = ready_d;
+        return m;
+    }
+};
 
 template <int IN_DT, int OPK, int CAP>
-__device__ void consumer_loop(const DcBatch<CAP>& P, PipeSmem<IN_DT>& ps, unsigned char* smem, int* s_abort)
+__global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) engine_kernel(const __grid_constant__ DcBatch<CAP> P)
 {
+    __shared__ __align__(16) unsigned char smem[PhaseSmem<OPK>::value];
+    __shared__ TileMsg s_msg;
+    __shared__ TileSource<OPK, CAP> s_src;  // thread 0's scheduler state, kept out of registers
     const Beta be = {P.beta_r, 1.0f - P.beta_r, P.beta_k, 1.0f - P.beta_k};
-    Ring data{0u, 0u}, tring{0u, 0u};
+    if (threadIdx.x == 0) {
+        if (P.profile) atomicMax(&P.ctrl->prof[PROF_KSTART_NOT], ~globaltimer_ns());
+        s_src.init(P);
+    }
     for (;;) {
-        if (threadIdx.x == 0) {
-            const unsigned long long t0 = P.profile ? globaltimer_ns() : 0ull;
-            *s_abort = mbar_wait(&ps.tfull[tring.idx], tring.parity, P.err, P.timeout_ns) ? 0 : 1;
-            if (P.profile) atomicAdd(&P.ctrl->prof[PROF_TILE_WAIT], globaltimer_ns() - t0);
-        }
-        consumer_sync();
-        if (*s_abort) return;
-        const TileMsg m = ps.msg[tring.idx];
-        __syncwarp();
-        if ((threadIdx.x & 31) == 0) mbar_arrive(&ps.tempty[tring.idx]);
-        tring.advance(kTileRing);
-        if (m.tile < 0) return;
+        if (threadIdx.x == 0) s_msg = s_src.fetch(P);
+        cta_sync();
+        const TileMsg& m = s_msg;
+        if (m.tile < 0) break;
         const int img = m.img, p = m.p, kind = P.phase_kind[p];
-        const DcImage im = P.img[img];  // one copy per tile, not per group
+        const DcImage& im = P.img[img];
         DcImgCtrl* ic = img_ctrl(P.ctrl, img);
         int I;
         const TileRect tr = tile_rect<OPK>(P, im, kind, m.lt, I);
         if (P.profile && threadIdx.x == 0) atomicMax(&ic->t_start_not[p], ~globaltimer_ns());
         if constexpr (OPK == OPK_DECOLOR) {
             constexpr int G = InT<IN_DT>::G;
-            consume_tile<IN_DT>(P, ps, data, im, tr, false, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+            consume_tile<IN_DT>(im, tr, false, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) {
                 GroupIO<IN_DT>::store(im, r, c, n, vec, Lv);
             });
         } else if constexpr (OPK == OPK_GLOBAL) {
             if (kind == PK_STATS) {
-                tile_stats<IN_DT>(P, ps, data, im, ic, tr, be, smem);
+                tile_stats<IN_DT>(P, im, ic, tr, be, smem);
             } else if (kind == PK_LOGHIST) {
-                tile_loghist<IN_DT>(P, ps, data, im, ic, tr, be, m.d, smem);
+                tile_loghist<IN_DT>(P, im, ic, tr, be, m.d, smem);
             } else {
                 if (P.stats && m.lt == 0) write_stats(P, im, ic, img, m.d);
-                tile_apply_global<IN_DT>(P, ps, data, im, ic, tr, be, m.d, smem);
+                tile_apply_global<IN_DT>(P, im, ic, tr, be, m.d, smem);
             }
         } else {
             if (kind == PK_STATS)
-                tile_stats<IN_DT>(P, ps, data, im, ic, tr, be, smem);
+                tile_stats<IN_DT>(P, im, ic, tr, be, smem);
             else if (kind == PK_BLOCKH)
-                tile_blockh<IN_DT>(P, ps, data, im, tr, I, be, m.d, smem);
+                tile_blockh<IN_DT>(P, im, tr, I, be, m.d, smem);
             else if (kind == PK_CDF)
                 tile_cdf(P, im, I, tr, smem);
             else
-                tile_apply_local<IN_DT>(P, ps, data, im, tr, I, be, m.d, smem);
+                tile_apply_local<IN_DT>(P, im, tr, I, be, m.d, smem);
         }
-        consumer_sync();
+        cta_sync();
         if (threadIdx.x == 0) {
             if (P.profile) {
                 atomicMax(&ic->t_end[p], globaltimer_ns());
                 atomicAdd(&P.ctrl->prof[PROF_TILES], 1ull);
             }
-            if (!(P.withhold_ready && p == 0)) red_release_add(&ic->done[p], 1u);
+            s_src.finished(img, p);
         }
     }
-}
-
-template <int IN_DT, int OPK, int CAP>
-#ifndef DC_MIN_CTAS
-#define DC_MIN_CTAS 2
-#endif
-__global__ void __launch_bounds__(kBlockThreads, DC_MIN_CTAS) engine_kernel(const __grid_constant__ DcBatch<CAP> P)
-{
-    extern __shared__ __align__(128) unsigned char dsmem[];
-    PipeSmem<IN_DT>& ps = *reinterpret_cast<PipeSmem<IN_DT>*>(dsmem);
-    unsigned char* phase_smem = dsmem + sizeof(PipeSmem<IN_DT>);
-    int* s_abort = reinterpret_cast<int*>(phase_smem + PhaseSmem<OPK>::value);
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < PipeSmem<IN_DT>::kStages; ++i) {
-            mbar_init(&ps.full[i], 1);
-            mbar_init(&ps.empty[i], kConsumerWarps);
-        }
-        for (int i = 0; i < kTileRing; ++i) {
-            mbar_init(&ps.tfull[i], 1);
-            mbar_init(&ps.tempty[i], kConsumerWarps);
-        }
-        fence_mbarrier_init();
-    }
-    if (P.profile && threadIdx.x == 0) atomicMax(&P.ctrl->prof[PROF_KSTART_NOT], ~globaltimer_ns());
-    __syncthreads();
-    if (threadIdx.x >= kThreads) {
-        if (threadIdx.x == kThreads) producer_loop<IN_DT, OPK>(P, ps);
-        return;
-    }
-    consumer_loop<IN_DT, OPK>(P, ps, phase_smem, s_abort);
     if (P.profile && threadIdx.x == 0) atomicMax(&P.ctrl->prof[PROF_KEND], globaltimer_ns());
 }
 
 template <int IN_DT, int OPK, int CAP>
 int launch_one(const void* batch, LaunchShape ls, void* stream)
 {
-    static unsigned long long attr_set = 0ull;  // one bit per device
-    constexpr size_t smem = engine_smem_bytes<IN_DT, OPK>();
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return DC_ERR_CUDA;
-    const unsigned long long bit = 1ull << (dev & 63);
-    if (!(__atomic_load_n(&attr_set, __ATOMIC_ACQUIRE) & bit)) {
-        if (cudaFuncSetAttribute(engine_kernel<IN_DT, OPK, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem) != cudaSuccess)
-            return DC_ERR_CUDA;
-        __atomic_fetch_or(&attr_set, bit, __ATOMIC_RELEASE);
-    }
     const DcBatch<CAP>& b = *reinterpret_cast<const DcBatch<CAP>*>(batch);
-    engine_kernel<IN_DT, OPK, CAP><<<ls.grid, kBlockThreads, smem, (cudaStream_t)stream>>>(b);
+    engine_kernel<IN_DT, OPK, CAP><<<ls.grid, kThreads, 0, (cudaStream_t)stream>>>(b);
     return cudaGetLastError() == cudaSuccess ? DC_OK : DC_ERR_CUDA;
 }
 
 template <int IN_DT, int OPK, int CAP>
 int occupancy_one()
 {
-    constexpr size_t smem = engine_smem_bytes<IN_DT, OPK>();
-    if (cudaFuncSetAttribute(engine_kernel<IN_DT, OPK, CAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
-        return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, engine_kernel<IN_DT, OPK, CAP>, kBlockThreads, smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, engine_kernel<IN_DT, OPK, CAP>, kThreads, 0) !=
         cudaSuccess)
         return 0;
     return nb;
