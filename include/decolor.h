@@ -6,8 +6,8 @@
  * "A color temperature-based high-speed decolorization: an empirical approach for
  * tone mapping applications" (arXiv 2108.13656), Sec. II-B, and fuses it with the
  * global tone curve of Sec. III-B-1 and the smoothed local-histogram-equalisation
- * tone mapping of Sec. III-B-2.  Every call is one persistent CUDA launch over a
- * (possibly ragged) batch of images.
+ * tone mapping of Sec. III-B-2.  Every pass of a call is one persistent CUDA launch
+ * over a (possibly ragged) batch of images of one input sample type.
  *
  * Conventions shared by every entry point
  *  - Images are interleaved RGB (R, G, B per pixel, no padding between pixels),
@@ -27,9 +27,9 @@
  *    not overlap output.  Two calls that share a workspace must be ordered (same
  *    stream or an event between them).
  *  - Return value: DC_OK or a DC_ERR_* code; nothing is enqueued when a call
- *    returns an error.  Errors found on the device while the launch runs (a
- *    dependency wait that ran out of time) are recorded in the workspace and read
- *    with dc_query_status.
+ *    returns an error.  A call is a short chain of passes (one persistent kernel
+ *    each, chained with programmatic dependent launch on `stream`); no kernel ever
+ *    waits for another CTA, so a call cannot hang on the device.
  *  - Vector path: when an image's data pointers and row strides are 16-byte
  *    aligned, pixels move in 16-byte vectors; otherwise the image takes a scalar
  *    path with the same results.
@@ -58,7 +58,7 @@ extern "C" {
 #define DC_ERR_UNSUPPORTED_DTYPE 2 /* a dtype is not DC_U8 / DC_F16 / DC_F32 */
 #define DC_ERR_WORKSPACE 3         /* ws is NULL, misaligned (256 B) or smaller than needed */
 #define DC_ERR_CUDA 4              /* a CUDA runtime call failed (launch, memset, attribute) */
-#define DC_ERR_TIMEOUT 5           /* device side: a dependency wait ran past its limit */
+#define DC_ERR_TIMEOUT 5           /* reserved: a device-side wait ran past its limit */
 #define DC_ERR_TOO_MANY 6          /* more than DC_MAX_BATCH images */
 
 /* ---- sample types ---- */
@@ -127,7 +127,7 @@ typedef struct {
  * nearest block curves (nominal block centres, clamped at the border) evaluated at
  * its own u, then y = alpha * F + (1 - alpha) * u.
  * Defaults: block_s = 32, radius_blocks = 2, bins = 32, alpha = 1, delta = 1e-4.
- * Limits: 1 <= block_s <= 256, 0 <= radius_blocks <= 16, 2 <= bins <= DC_MAX_BINS,
+ * Limits: 1 <= block_s <= 64, 0 <= radius_blocks <= 16, 2 <= bins <= DC_MAX_BINS,
  * alpha in [0, 1]. */
 typedef struct {
     int32_t block_s;
@@ -187,9 +187,9 @@ DC_API int dc_decolorize_tonemap_local(const dc_image_in* in, const dc_image_out
 DC_API size_t dc_workspace_bytes(int32_t op, const dc_image_in* in, int32_t n,
                                  const void* op_params);
 
-/* Synchronises `stream`, then reads the device-side error word that the last call
- * using workspace `ws` left there: DC_OK or DC_ERR_TIMEOUT.  Returns DC_ERR_CUDA if
- * the copy fails. */
+/* Synchronises `stream`, then reads the device-side error word of workspace `ws`
+ * (reserved for device-detected errors; the current kernels never wait on each
+ * other and report DC_OK).  Returns DC_ERR_CUDA if the copy fails. */
 DC_API int dc_query_status(const void* ws, void* stream);
 
 /* Static English description of a status code. */
@@ -199,16 +199,6 @@ DC_API const char* dc_status_string(int status);
  * used by the autotuner.  Returns DC_ERR_INVALID_ARG for values out of range. */
 DC_API int dc_set_tuning(int32_t op, int32_t in_dtype, const dc_tuning* t);
 DC_API int dc_get_tuning(int32_t op, int32_t in_dtype, dc_tuning* t);
-
-/* Upper limit, in nanoseconds, of every device-side dependency wait in later calls
- * (default 2e9).  A wait that runs past it records DC_ERR_TIMEOUT and the launch
- * drains without writing further output.  Values below 1000 are rejected. */
-DC_API int dc_set_wait_timeout_ns(uint64_t ns);
-
-/* Test hook for the timeout path: when nonzero, later calls never publish the
- * completion of their first pass, so every dependent wait runs out (bounded by the
- * timeout above).  Default 0. */
-DC_API int dc_debug_withhold_ready(int32_t on);
 
 /* Profiling switch for later calls (default 0).  When on, each launch records per
  * image and phase the earliest tile start and latest tile end (globaltimer ns) and,

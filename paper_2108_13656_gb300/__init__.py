@@ -23,7 +23,6 @@ from ._abi import (  # noqa: F401
     PreparedCall,
     Workspace,
     debug_profile,
-    debug_withhold_ready,
     decolorize,
     decolorize_tonemap_global,
     decolorize_tonemap_local,
@@ -36,7 +35,6 @@ from ._abi import (  # noqa: F401
     query_status,
     read_profile,
     set_tuning,
-    set_wait_timeout_ns,
     status_string,
     workspace_bytes,
 )

@@ -75,8 +75,6 @@ _SIGS = {
     "dc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "dc_set_tuning": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
     "dc_get_tuning": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
-    "dc_set_wait_timeout_ns": (ctypes.c_int, [ctypes.c_uint64]),
-    "dc_debug_withhold_ready": (ctypes.c_int, [ctypes.c_int32]),
     "dc_debug_profile": (ctypes.c_int, [ctypes.c_int32]),
     "dc_debug_read_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "dc_last_launch_count": (ctypes.c_int, []),
@@ -335,16 +333,6 @@ def get_tuning(op: int, in_dtype: int) -> tuple[int, int, int, int]:
     if rc != DC_OK:
         raise DcError(rc, "dc_get_tuning")
     return (t.threads, t.tile_rows, t.tile_cols, t.ctas_per_sm)
-
-
-def set_wait_timeout_ns(ns: int):
-    rc = load().dc_set_wait_timeout_ns(int(ns))
-    if rc != DC_OK:
-        raise DcError(rc, "dc_set_wait_timeout_ns")
-
-
-def debug_withhold_ready(on: bool):
-    load().dc_debug_withhold_ready(1 if on else 0)
 
 
 def debug_profile(on: bool):

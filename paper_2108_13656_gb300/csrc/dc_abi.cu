@@ -28,10 +28,9 @@ dc_tuning g_tune[3][3] = {
     {{256, 4, 4096, 0}, {256, 4, 4096, 0}, {256, 4, 4096, 0}},
     {{256, 32, 256, 0}, {256, 32, 256, 0}, {256, 32, 256, 0}},
 };
-unsigned long long g_timeout_ns = 2000000000ull;
-int g_withhold = 0;
 int g_profile = 0;
 thread_local int g_last_launches = 0;
+thread_local int g_call_launches = 0;
 
 int esz(int dt) { return dt == DC_U8 ? 1 : (dt == DC_F16 ? 2 : 4); }
 bool dt_ok(int dt) { return dt == DC_U8 || dt == DC_F16 || dt == DC_F32; }
@@ -75,7 +74,7 @@ int validate_params(const dc_decolor_params* p, const OpArgs& op)
     } else if (op.opk == kOpkLocal) {
         const dc_local_params* l = op.l;
         if (!l || l->reserved != 0) return DC_ERR_INVALID_ARG;
-        if (l->block_s < 1 || l->block_s > 256 || l->radius_blocks < 0 || l->radius_blocks > 16) return DC_ERR_INVALID_ARG;
+        if (l->block_s < 1 || l->block_s > 64 || l->radius_blocks < 0 || l->radius_blocks > 16) return DC_ERR_INVALID_ARG;
         if (l->bins < 2 || l->bins > DC_MAX_BINS || !finite_in(l->alpha, 0.f, 1.f)) return DC_ERR_INVALID_ARG;
         if (!std::isfinite(l->delta) || !(l->delta > 0.f)) return DC_ERR_INVALID_ARG;
     }
@@ -205,11 +204,8 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
     b->beta_r = p->beta_r;
     b->beta_k = p->beta_k;
     b->ldr = ldr ? 1 : 0;
-    b->withhold_ready = 0;
     {
         std::lock_guard<std::mutex> lk(g_mu);
-        b->timeout_ns = g_timeout_ns;
-        b->withhold_ready = g_withhold ? 1u : 0u;
         b->profile = g_profile ? 1u : 0u;
     }
     if (op.opk == kOpkGlobal) {
@@ -242,40 +238,30 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
         b->stats_index[k] = idx[k];
     }
     *need = std::max(*need, off);
-    // segment table: wave w holds (image w - p, phase p), phases ascending
-    bool rev[kMaxPhases];
+    // per pass: first tile of each image; passes that re-read what the previous
+    // pixel pass read hand their tiles out last-first
     {
         bool dir = false;
         for (int ph = 0; ph < b->n_phase; ++ph) {
             if (b->phase_kind[ph] == PK_CDF) {
-                rev[ph] = false;
+                b->reverse[ph] = 0;
             } else {
-                rev[ph] = dir;
+                b->reverse[ph] = dir ? 1 : 0;
                 dir = !dir;
             }
+            int64_t total = 0;
+            for (int i = 0; i < n; ++i) {
+                b->seg_start[ph][i] = (int32_t)total;
+                total += geo[i].tiles[ph];
+                if (total > INT32_MAX / 2) {
+                    delete b;
+                    return DC_ERR_INVALID_ARG;
+                }
+            }
+            b->seg_start[ph][n] = (int32_t)total;
         }
-    }
-    int64_t total = 0;
-    int nseg = 0;
-    for (int w = 0; w < n + b->n_phase - 1; ++w) {
-        for (int ph = 0; ph < b->n_phase; ++ph) {
-            const int i = w - ph;
-            if (i < 0 || i >= n) continue;
-            DcSegment& sg = b->seg[nseg++];
-            sg.start = (int32_t)total;
-            sg.img = (int16_t)i;
-            sg.phase = (int8_t)ph;
-            sg.reverse = rev[ph] ? 1 : 0;
-            total += geo[i].tiles[ph];
-        }
-    }
-    if (total <= 0 || total > INT32_MAX - 65536) {
-        delete b;
-        return DC_ERR_INVALID_ARG;
     }
     b->n_img = n;
-    b->n_seg = nseg;
-    b->total_tiles = (int32_t)total;
     if (!launch) {
         delete b;
         return DC_OK;
@@ -295,19 +281,24 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
         delete b;
         return DC_ERR_CUDA;
     }
-    int occ = in_dt == DC_U8 ? occupancy_u8(CAP, op.opk) : (in_dt == DC_F16 ? occupancy_f16(CAP, op.opk) : occupancy_f32(CAP, op.opk));
-    if (occ <= 0) occ = 1;
-    const int per_sm = tu.ctas_per_sm > 0 ? std::min(tu.ctas_per_sm, occ) : occ;
-    LaunchShape ls;
-    ls.threads = 256;
-    ls.grid = (int)std::min<int64_t>(total, (int64_t)per_sm * nsm);
-    int rc;
-    if (in_dt == DC_U8)
-        rc = launch_engine_u8(b, CAP, op.opk, ls, stream);
-    else if (in_dt == DC_F16)
-        rc = launch_engine_f16(b, CAP, op.opk, ls, stream);
-    else
-        rc = launch_engine_f32(b, CAP, op.opk, ls, stream);
+    int rc = DC_OK;
+    for (int ph = 0; ph < b->n_phase && rc == DC_OK; ++ph) {
+        const int kind = b->phase_kind[ph];
+        int occ = in_dt == DC_U8 ? occupancy_u8(CAP, op.opk, kind)
+                                 : (in_dt == DC_F16 ? occupancy_f16(CAP, op.opk, kind) : occupancy_f32(CAP, op.opk, kind));
+        if (occ <= 0) occ = 1;
+        const int per_sm = tu.ctas_per_sm > 0 ? std::min(tu.ctas_per_sm, occ) : occ;
+        LaunchShape ls;
+        ls.threads = 256;
+        ls.grid = (int)std::min<int64_t>(b->seg_start[ph][n], (int64_t)per_sm * nsm);
+        if (in_dt == DC_U8)
+            rc = launch_engine_u8(b, CAP, op.opk, kind, ph, ls, stream);
+        else if (in_dt == DC_F16)
+            rc = launch_engine_f16(b, CAP, op.opk, kind, ph, ls, stream);
+        else
+            rc = launch_engine_f32(b, CAP, op.opk, kind, ph, ls, stream);
+        if (rc == DC_OK) ++g_call_launches;
+    }
     delete b;
     return rc;
 }
@@ -379,7 +370,7 @@ int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_deco
         return DC_OK;
     }
     if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < (size_t)need) return DC_ERR_WORKSPACE;
-    int launches = 0;
+    g_call_launches = 0;
     bool first = true;
     for (const LaunchPlan& pl : plans) {
         const int cnt = (int)pl.idx.size();
@@ -394,9 +385,8 @@ int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_deco
             r2 = build_and_launch<kCapLarge>(in, out, pl.idx, p, op, w, first, &dummy, stream, true);
         if (r2 != DC_OK) return r2;
         first = false;
-        ++launches;
     }
-    g_last_launches = launches;
+    g_last_launches = g_call_launches;
     return DC_OK;
 }
 
@@ -490,21 +480,6 @@ DC_API int dc_get_tuning(int32_t op, int32_t in_dtype, dc_tuning* t)
     if (op < DC_OP_DECOLORIZE || op > DC_OP_LOCAL || !dt_ok(in_dtype) || !t) return DC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_mu);
     *t = g_tune[op][in_dtype];
-    return DC_OK;
-}
-
-DC_API int dc_set_wait_timeout_ns(uint64_t ns)
-{
-    if (ns < 1000) return DC_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lk(g_mu);
-    g_timeout_ns = ns;
-    return DC_OK;
-}
-
-DC_API int dc_debug_withhold_ready(int32_t on)
-{
-    std::lock_guard<std::mutex> lk(g_mu);
-    g_withhold = on ? 1 : 0;
     return DC_OK;
 }
 

@@ -342,34 +342,6 @@ __device__ __forceinline__ float pairwise_sum(const float* v)
     }
 }
 
-// ------------------------------------------------------------ waits -----------
-__device__ __forceinline__ void red_release_add(uint32_t* p, uint32_t v)
-{
-    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Bounded wait until *count >= target (the tiles of a phase all published).  Returns
-// 0 on success, 1 when the launch has an error or the wait ran out (then
-// DC_ERR_TIMEOUT is recorded in *err).
-static __device__ __noinline__ int wait_count(const uint32_t* count, uint32_t target, uint32_t* err,
-                                              unsigned long long timeout_ns)
-{
-    if (ld_acquire_u32(count) >= target) return 0;
-    const unsigned long long t0 = globaltimer_ns();
-    const unsigned long long max_iter = timeout_ns / 16ull + 4096ull;
-    unsigned ns = 32;
-    for (unsigned long long it = 0;; ++it) {
-        if (ld_acquire_u32(count) >= target) return 0;
-        if (ld_relaxed_u32(err)) return 1;
-        if (globaltimer_ns() - t0 > timeout_ns || it > max_iter) {
-            atomicCAS(err, 0u, (uint32_t)DC_ERR_TIMEOUT);
-            return 1;
-        }
-        __nanosleep(ns);
-        if (ns < 512) ns *= 2;
-    }
-}
-
 // ------------------------------------------------------------ shared memory ---
 struct SmemStats {
     uint32_t hist[256];
@@ -381,13 +353,14 @@ struct SmemApplyG {
     float lut[260];
 };
 struct SmemBlockH {
-    unsigned long long h[kLocMaxBlocksX * DC_MAX_BINS];
+    uint32_t cnt[kLocMaxBlocksX * DC_MAX_BINS];  // pixels whose lower tent bin is j
+    uint32_t fs[kLocMaxBlocksX * DC_MAX_BINS];   // their upper-bin fractions, units of 2^-20
 };
 struct SmemCdf {
     unsigned long long v[(kCdfChunk + 2 * kMaxRadius) * DC_MAX_BINS];
 };
 struct SmemApplyL {
-    float tab[3 * (kLocMaxBlocksX + 2) * (DC_MAX_BINS + 1)];
+    float2 tab[3 * (kLocMaxBlocksX + 2) * (DC_MAX_BINS + 1)];  // per block and bin: (F at bin start, slope)
 };
 
 template <int OPK>

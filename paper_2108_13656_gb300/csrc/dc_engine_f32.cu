@@ -1,16 +1,16 @@
-// Engine kernels for DC_F32 input (all operations, all batch capacities).
+// Pass kernels for DC_F32 input (all operations and pass kinds, all batch capacities).
 #include "dc_engine_impl.cuh"
 
 namespace dc {
 
-int launch_engine_f32(const void* batch, int cap, int opk, LaunchShape ls, void* stream)
+int launch_engine_f32(const void* batch, int cap, int opk, int kind, int ph, LaunchShape ls, void* stream)
 {
-    return launch_dispatch<DC_F32>(batch, cap, opk, ls, stream);
+    return launch_dispatch<DC_F32>(batch, cap, opk, kind, ph, ls, stream);
 }
 
-int occupancy_f32(int cap, int opk)
+int occupancy_f32(int cap, int opk, int kind)
 {
-    return occupancy_dispatch<DC_F32>(cap, opk);
+    return occupancy_dispatch<DC_F32>(cap, opk, kind);
 }
 
 }  // namespace dc

@@ -1,5 +1,6 @@
-// Engine kernel body: tile queue with phase dependencies, and the per-phase tile
-// work.  Included by one translation unit per input sample type.
+// Pass kernels: one persistent kernel per pass kind, each covering that pass's
+// tiles for every image of the batch.  Included by one translation unit per input
+// sample type.
 #pragma once
 
 #include "dc_engine.cuh"
@@ -13,12 +14,6 @@ struct TileRect {
 // Values a tile derives from an image's finished statistics pass.
 struct Derived {
     float mu, exp_mu, lmin, lmax, inv_range;
-};
-
-// What thread 0 hands the CTA for the next tile (tile < 0: no more work).
-struct TileMsg {
-    int tile, lt, img, p;
-    Derived d;
 };
 
 __device__ __forceinline__ void cta_sync() { __syncthreads(); }
@@ -109,6 +104,27 @@ __device__ __forceinline__ Derived derive(const DcImgCtrl* ic, long long N)
 // the mapping needs no integer division; each thread issues the loads of U groups
 // before computing any of them.
 template <int IN_DT, bool PLANE, class F>
+__device__ __forceinline__ void walk_group(const DcImage& im, const Beta& be, F&& f, int r, int c, int n, bool vec,
+                                           float (&v)[InT<IN_DT>::G], uint32_t (&w)[PLANE ? 1 : 12], bool load)
+{
+    if (load) {
+        if constexpr (PLANE) {
+            GroupIO<IN_DT>::from_plane(im, r, c, n, vec, v);
+        } else {
+            if (vec)
+                GroupIO<IN_DT>::load_raw(im, r, c, w);
+            else
+                GroupIO<IN_DT>::luminance(im, r, c, n, false, be, v);
+        }
+    } else {
+        if constexpr (!PLANE) {
+            if (vec) GroupIO<IN_DT>::decode(w, be, v);
+        }
+        f(r, c, n, vec, v);
+    }
+}
+
+template <int IN_DT, bool PLANE, class F>
 __device__ __forceinline__ void walk_tile(const DcImage& im, const TileRect& t, const Beta& be, F&& f)
 {
     constexpr int G = InT<IN_DT>::G, U = Unroll<IN_DT, PLANE>::value;
@@ -118,38 +134,42 @@ __device__ __forceinline__ void walk_tile(const DcImage& im, const TileRect& t, 
     const int tx = threadIdx.x & (txt - 1);
     const int rpi = kThreads >> lg;
     const bool vec_img = (im.flags & IF_VEC) != 0;
-    for (int r = t.r0 + (threadIdx.x >> lg); r < t.r1; r += rpi) {
-        for (int g = tx; g < gpr; g += U * txt) {
-            int c[U], n[U];
-            bool vec[U];
-            float v[U][G];
-            uint32_t w[U][PLANE ? 1 : 12];
+    int c[U], n[U], rr[U];
+    bool vec[U];
+    float v[U][G];
+    uint32_t w[U][PLANE ? 1 : 12];
+    if (gpr >= kThreads) {
+        // long rows: the U groups of an iteration lie along the row
+        for (int r = t.r0; r < t.r1; ++r) {
+            for (int g = tx; g < gpr; g += U * kThreads) {
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const int gu = g + u * kThreads;
+                    c[u] = t.c0 + gu * G;
+                    n[u] = gu < gpr ? min(G, t.c1 - c[u]) : 0;
+                    vec[u] = vec_img && n[u] == G;
+                    if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, r, c[u], n[u], vec[u], v[u], w[u], true);
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u)
+                    if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, r, c[u], n[u], vec[u], v[u], w[u], false);
+            }
+        }
+    } else {
+        // short rows: one group per thread per row, the U groups lie in U rows
+        const int cc = t.c0 + tx * G;
+        const int nn = tx < gpr ? min(G, t.c1 - cc) : 0;
+        const bool vv = vec_img && nn == G;
+        for (int r = t.r0 + (threadIdx.x >> lg); r < t.r1; r += U * rpi) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int gu = g + u * txt;
-                c[u] = t.c0 + gu * G;
-                n[u] = gu < gpr ? min(G, t.c1 - c[u]) : 0;
-                vec[u] = vec_img && n[u] == G;
-                if (n[u] > 0) {
-                    if constexpr (PLANE) {
-                        GroupIO<IN_DT>::from_plane(im, r, c[u], n[u], vec[u], v[u]);
-                    } else {
-                        if (vec[u])
-                            GroupIO<IN_DT>::load_raw(im, r, c[u], w[u]);
-                        else
-                            GroupIO<IN_DT>::luminance(im, r, c[u], n[u], false, be, v[u]);
-                    }
-                }
+                rr[u] = r + u * rpi;
+                n[u] = rr[u] < t.r1 ? nn : 0;
+                if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, rr[u], cc, n[u], vv, v[u], w[u], true);
             }
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                if (n[u] > 0) {
-                    if constexpr (!PLANE) {
-                        if (vec[u]) GroupIO<IN_DT>::decode(w[u], be, v[u]);
-                    }
-                    f(r, c[u], n[u], vec[u], v[u]);
-                }
-            }
+            for (int u = 0; u < U; ++u)
+                if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, rr[u], cc, n[u], vv, v[u], w[u], false);
         }
     }
 }
@@ -366,68 +386,73 @@ __device__ void tile_apply_global(const DcBatch<CAP>& P, const DcImage& im,
 }
 
 // ---------------------------------------------------- phase: local histograms --
+// Tent binning: x = B u - 1/2 in 2^-20 fixed point, clamped to [0, (B-1) 2^20];
+// j = x >> 20 takes 1 - f, bin j+1 takes f.  Per block and bin the tile counts the
+// pixels with lower bin j and sums their f (two native 32-bit shared atomics per
+// run of equal keys; exact for blocks up to 64 x 64).  Bin j's mass is then
+// count_j 2^20 - F_j + F_{j-1}, stored as a 64-bit integer in units of 2^-20.
 template <int IN_DT, int CAP>
-__device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im,
-                            const TileRect& t, int I, const Beta& be, const Derived& d, unsigned char* smem)
+__device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const TileRect& t, int I,
+                            const Beta& be, const Derived& d, unsigned char* smem)
 {
     constexpr int G = InT<IN_DT>::G;
-    constexpr int kCountShift = 42;
     SmemBlockH& S = *reinterpret_cast<SmemBlockH*>(smem);
     const int s = P.block_s, B = P.bins;
     const int nbx = (t.c1 - t.c0 + s - 1) / s;
-    for (int k = threadIdx.x; k < nbx * B; k += kThreads) S.h[k] = 0ull;
+    for (int k = threadIdx.x; k < nbx * B; k += kThreads) {
+        S.cnt[k] = 0u;
+        S.fs[k] = 0u;
+    }
     const bool plane = from_plane(im, PK_BLOCKH);
     const bool is_log = plane && (im.flags & IF_PLANE_LOG) != 0;
     const bool ldr = P.ldr != 0;
-    const float delta = P.delta, Bf = (float)B;
+    const float delta = P.delta, scale = (float)B * 1048576.0f;
+    const int xmax = (B - 1) << 20;
     const uint32_t magic = P.s_magic;
+    const bool group_in_block = magic != 0u && s % G == 0;  // a G-pixel group never straddles blocks
     cta_sync();
     consume_tile<IN_DT>(im, t, plane, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+        const int blk0 = group_in_block ? (int)__umulhi((uint32_t)(c - t.c0), magic) : 0;
         int cur = -1;
-        unsigned long long acc = 0ull;
+        uint32_t rc = 0u, rf = 0u;
 #pragma unroll
         for (int k = 0; k < G; ++k) {
             if (k < n) {
                 const float u = ldr ? fminf(fmaxf(Lv[k], 0.0f), 1.0f) : log_u(Lv[k], is_log, delta, d.lmin, d.inv_range);
-                // tent binning onto bin centres (j + 1/2)/B
-                const float x = fmaf(Bf, u, -0.5f);
-                int j;
-                float f;
-                if (x <= 0.0f) {
-                    j = 0;
-                    f = 0.0f;
-                } else if (x >= Bf - 1.0f) {
-                    j = B - 1;
-                    f = 0.0f;
-                } else {
-                    j = (int)x;
-                    f = x - (float)j;
+                const int x = min(max(__float2int_rn(fmaf(u, scale, -524288.0f)), 0), xmax);
+                int blk = blk0;
+                if (!group_in_block) {
+                    const uint32_t off = (uint32_t)(c + k - t.c0);
+                    blk = magic ? (int)__umulhi(off, magic) : (int)off;
                 }
-                const uint32_t off = (uint32_t)(c + k - t.c0);
-                const int blk = magic ? (int)__umulhi(off, magic) : (int)off;
-                const int key = blk * B + j;
-                const unsigned long long val = (1ull << kCountShift) | (unsigned long long)__float2uint_rn(f * 16777216.0f);
+                const int key = blk * B + (x >> 20);
+                const uint32_t f = (uint32_t)x & 0xFFFFFu;
                 if (key == cur) {
-                    acc += val;
+                    ++rc;
+                    rf += f;
                 } else {
-                    if (cur >= 0) atomicAdd(&S.h[cur], acc);
+                    if (cur >= 0) {
+                        atomicAdd(&S.cnt[cur], rc);
+                        atomicAdd(&S.fs[cur], rf);
+                    }
                     cur = key;
-                    acc = val;
+                    rc = 1u;
+                    rf = f;
                 }
             }
         }
-        if (cur >= 0) atomicAdd(&S.h[cur], acc);
+        if (cur >= 0) {
+            atomicAdd(&S.cnt[cur], rc);
+            atomicAdd(&S.fs[cur], rf);
+        }
     });
     cta_sync();
-    // unpack: bin j holds count_j * 2^24 - F_j + F_{j-1}
-    const unsigned long long mask = (1ull << kCountShift) - 1ull;
     unsigned long long* H = reinterpret_cast<unsigned long long*>(P.ws + im.ws_hist);
     const int J0 = t.c0 / s;
     for (int k = threadIdx.x; k < nbx * B; k += kThreads) {
         const int blk = k / B, j = k - blk * B;
-        const unsigned long long v = S.h[k];
-        const unsigned long long Fprev = j > 0 ? (S.h[k - 1] & mask) : 0ull;
-        const unsigned long long h = ((v >> kCountShift) << 24) - (v & mask) + Fprev;
+        const unsigned long long fprev = j > 0 ? S.fs[k - 1] : 0u;
+        const unsigned long long h = ((unsigned long long)S.cnt[k] << 20) - S.fs[k] + fprev;
         H[((size_t)I * im.Wb + (J0 + blk)) * B + j] = h;
     }
 }
@@ -475,9 +500,13 @@ __device__ void tile_cdf(const DcBatch<CAP>& P, const DcImage& im, int I, const 
 }
 
 // ------------------------------------------------------- phase: local apply --
+// The tile's block row and its neighbours' cumulative tables are staged as
+// (F at the start of bin j, F(j+1) - F(j)) pairs, so each of the four block curves
+// costs one 64-bit shared load and one FMA.  When block_s is a power of two and a
+// multiple of 2G, the bilinear column pair and weight step are fixed per group.
 template <int IN_DT, int CAP>
-__device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im,
-                                 const TileRect& t, int I, const Beta& be, const Derived& d, unsigned char* smem)
+__device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const TileRect& t, int I,
+                                 const Beta& be, const Derived& d, unsigned char* smem)
 {
     constexpr int G = InT<IN_DT>::G;
     SmemApplyL& S = *reinterpret_cast<SmemApplyL*>(smem);
@@ -485,43 +514,55 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im,
     const int nbx = (t.c1 - t.c0 + s - 1) / s;
     const int J0 = t.c0 / s;
     const int W2 = nbx + 2, B1 = B + 1;
+    // slots B+1 pairs apart: the same bin of neighbouring blocks falls in other banks
+    const int SB = B + 1;
     const float* E = reinterpret_cast<const float*>(P.ws + im.ws_hist + align_up((int64_t)Hb * Wb * B * 8, 256));
-    for (int k = threadIdx.x; k < 3 * W2 * B1; k += kThreads) {
-        const int sr = k / (W2 * B1);
-        const int rem = k - sr * W2 * B1;
-        const int sc = rem / B1, j = rem - sc * B1;
+    for (int k = threadIdx.x; k < 3 * W2 * B; k += kThreads) {
+        const int slot = k / B, j = k - slot * B;
+        const int sr = slot / W2, sc = slot - sr * W2;
         const int I2 = min(max(I - 1 + sr, 0), Hb - 1);
         const int J2 = min(max(J0 - 1 + sc, 0), Wb - 1);
-        S.tab[k] = ld_cg_f(&E[((size_t)I2 * Wb + J2) * B1 + j]);
+        const float* e = E + ((size_t)I2 * Wb + J2) * B1 + j;
+        const float e0 = ld_cg_f(e), e1 = ld_cg_f(e + 1);
+        S.tab[slot * SB + j] = make_float2(e0, e1 - e0);
     }
     const bool plane = from_plane(im, PK_APPLY_L);
     const bool is_log = plane && (im.flags & IF_PLANE_LOG) != 0;
     const bool ldr = P.ldr != 0;
     const float delta = P.delta, Bf = (float)B, inv_s = 1.0f / (float)s, alpha = P.alpha;
+    const bool group_cols = (s & (s - 1)) == 0 && s % (2 * G) == 0;
     cta_sync();
     consume_tile<IN_DT>(im, t, plane, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
         const float fy = fmaf((float)r + 0.5f, inv_s, -0.5f);
         const float fly = floorf(fy);
         const float wy = fy - fly;
-        const int sr0 = (int)fly - (I - 1);
-        const float* row0 = S.tab + sr0 * W2 * B1;
-        const float* row1 = row0 + W2 * B1;
+        const float2* row0 = S.tab + ((int)fly - (I - 1)) * W2 * SB;
+        const float2* row1 = row0 + W2 * SB;
+        const float fx0 = fmaf((float)c + 0.5f, inv_s, -0.5f);
+        const float flx0 = floorf(fx0);
+        const int sc0g = (int)flx0 - (J0 - 1);
+        const float wx0 = fx0 - flx0;
 #pragma unroll
         for (int k = 0; k < G; ++k) {
             const float u = ldr ? fminf(fmaxf(Lv[k], 0.0f), 1.0f) : log_u(Lv[k], is_log, delta, d.lmin, d.inv_range);
-            const float fx = fmaf((float)(c + k) + 0.5f, inv_s, -0.5f);
-            const float flx = floorf(fx);
-            const float wx = fx - flx;
-            const int sc0 = (int)flx - (J0 - 1);
+            int sc0;
+            float wx;
+            if (group_cols) {
+                sc0 = sc0g;
+                wx = fmaf((float)k, inv_s, wx0);
+            } else {
+                const float fx = fmaf((float)(c + k) + 0.5f, inv_s, -0.5f);
+                const float flx = floorf(fx);
+                wx = fx - flx;
+                sc0 = (int)flx - (J0 - 1);
+            }
             const float Bu = Bf * u;
             const int j = min((int)Bu, B - 1);
             const float tt = Bu - (float)j;
-            const float* a0 = row0 + sc0 * B1 + j;
-            const float* a1 = row1 + sc0 * B1 + j;
-            const float f00 = fmaf(tt, a0[1] - a0[0], a0[0]);
-            const float f01 = fmaf(tt, a0[B1 + 1] - a0[B1], a0[B1]);
-            const float f10 = fmaf(tt, a1[1] - a1[0], a1[0]);
-            const float f11 = fmaf(tt, a1[B1 + 1] - a1[B1], a1[B1]);
+            const float2 a = row0[sc0 * SB + j], b = row0[(sc0 + 1) * SB + j];
+            const float2 cc = row1[sc0 * SB + j], dd = row1[(sc0 + 1) * SB + j];
+            const float f00 = fmaf(tt, a.y, a.x), f01 = fmaf(tt, b.y, b.x);
+            const float f10 = fmaf(tt, cc.y, cc.x), f11 = fmaf(tt, dd.y, dd.x);
             const float top = fmaf(wx, f01 - f00, f00);
             const float bot = fmaf(wx, f11 - f10, f10);
             const float F = fmaf(wy, bot - top, top);
@@ -534,209 +575,144 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im,
 // ------------------------------------------------------------ the engine -----
 static_assert(kThreads == 256, "per-bin work uses one consumer thread per histogram bin");
 
-template <int OPK>
-struct PhaseSmem {
-    static constexpr size_t value = OPK == OPK_GLOBAL ? sizeof(SmemApplyG) + sizeof(SmemStats) : SmemBytes<OPK>::value;
+template <int KIND>
+struct PassSmem {
+    static constexpr size_t value = KIND == PK_STATS || KIND == PK_LOGHIST ? sizeof(SmemStats)
+                                    : KIND == PK_APPLY_G                   ? sizeof(SmemApplyG) + sizeof(SmemStats)
+                                    : KIND == PK_BLOCKH                    ? sizeof(SmemBlockH)
+                                    : KIND == PK_CDF                       ? sizeof(SmemCdf)
+                                    : KIND == PK_APPLY_L                   ? sizeof(SmemApplyL)
+                                                                           : 16;
 };
 
 #ifndef DC_MIN_CTAS
 #define DC_MIN_CTAS 4
 #endif
 
-// Thread 0 of a CTA: the next tile from the queue (fetched one ahead), after the
-// phases it depends on have published all their tiles.  Per image it remembers
-// which phases are known complete and the values derived from the stats pass.
-// Finished tiles are counted locally and published with one release when the CTA
-// moves to another (image, phase), before it blocks on any wait, and at exit, so
-// a CTA never waits while holding unpublished completions.
-template <int OPK, int CAP>
-struct TileSource {
-    int next, sg_i, ready_img, ready_p;
-    Derived ready_d;
-    int pend_img, pend_p;
-    uint32_t pend_n;
-
-    __device__ void init(const DcBatch<CAP>& P)
-    {
-        next = (int)atomicAdd(&P.ctrl->next_tile, 1u);
-        sg_i = 0;
-        ready_img = -1;
-        ready_p = 0;
-        ready_d = Derived{0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        pend_img = -1;
-        pend_p = 0;
-        pend_n = 0u;
-    }
-
-    // Called after a CTA barrier that follows the counted tiles' last writes.
-    __device__ void flush(const DcBatch<CAP>& P)
-    {
-        if (pend_n) {
-            if (!(P.withhold_ready && pend_p == 0))
-                red_release_add(&img_ctrl(P.ctrl, pend_img)->done[pend_p], pend_n);
-            pend_n = 0u;
-        }
-    }
-
-    __device__ void finished(int img, int p)
-    {
-        pend_img = img;
-        pend_p = p;
-        ++pend_n;
-    }
-
-    __device__ TileMsg fetch(const DcBatch<CAP>& P)
-    {
-        TileMsg m;
-        m.tile = -1;
-        const int tile = next;
-        if (tile >= P.total_tiles) {
-            flush(P);
-            return m;
-        }
-        next = (int)atomicAdd(&P.ctrl->next_tile, 1u);  // overlaps this tile's work
-        while (sg_i + 1 < P.n_seg && P.seg[sg_i + 1].start <= tile) ++sg_i;
-        const DcSegment sg = P.seg[sg_i];
-        const int nt = (sg_i + 1 < P.n_seg ? P.seg[sg_i + 1].start : P.total_tiles) - sg.start;
-        int lt = tile - sg.start;
-        if (sg.reverse) lt = nt - 1 - lt;
-        const int img = sg.img, p = sg.phase;
-        if (img != pend_img || p != pend_p) flush(P);
-        const int known = img == ready_img ? ready_p : 0;
-        if (p > known) {
-            flush(P);
-            const DcImage& im = P.img[img];
-            DcImgCtrl* ic = img_ctrl(P.ctrl, img);
-            const unsigned long long t0 = P.profile ? globaltimer_ns() : 0ull;
-            bool ok = true;
-            // every earlier phase of this image must have published all its tiles
-            for (int q = p - 1; q >= known && ok; --q)
-                ok = wait_count(&ic->done[q], (uint32_t)phase_tiles<OPK>(P, im, P.phase_kind[q]), P.err,
-                                P.timeout_ns) == 0;
-            if (P.profile) atomicAdd(&P.ctrl->prof[PROF_DEP_WAIT], globaltimer_ns() - t0);
-            if (!ok) return m;
-            if (img != ready_img && P.phase_kind[0] == PK_STATS)
-                ready_d = derive(ic, (long long)im.prow * (long long)im.pcol);
-            ready_img = img;
-            ready_p = p;
-        }
-        m.tile = tile;
-        m.lt = lt;
-        m.img = img;
-        m.p = p;
-        m.d = ready_d;
-        return m;
-    }
-};
-
-template <int IN_DT, int OPK, int CAP>
-__global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) engine_kernel(const __grid_constant__ DcBatch<CAP> P)
+// One pass over all tiles of pass `ph` (kind KIND) of every image in the batch.
+// CTAs take tiles round-robin (last-first when the pass re-reads what the previous
+// pass just read, so the most recently touched data is still in L2).
+template <int IN_DT, int OPK, int KIND, int CAP>
+__global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __grid_constant__ DcBatch<CAP> P, int ph)
 {
-    __shared__ __align__(16) unsigned char smem[PhaseSmem<OPK>::value];
-    __shared__ TileMsg s_msg;
-    __shared__ TileSource<OPK, CAP> s_src;  // thread 0's scheduler state, kept out of registers
+    __shared__ __align__(16) unsigned char smem[PassSmem<KIND>::value];
+    __shared__ Derived s_d;
     const Beta be = {P.beta_r, 1.0f - P.beta_r, P.beta_k, 1.0f - P.beta_k};
-    if (threadIdx.x == 0) {
-        if (P.profile) atomicMax(&P.ctrl->prof[PROF_KSTART_NOT], ~globaltimer_ns());
-        s_src.init(P);
-    }
-    for (;;) {
-        if (threadIdx.x == 0) s_msg = s_src.fetch(P);
-        cta_sync();
-        const TileMsg& m = s_msg;
-        if (m.tile < 0) break;
-        const int img = m.img, p = m.p, kind = P.phase_kind[p];
+    const int total = P.seg_start[ph][P.n_img];
+    const bool rev = P.reverse[ph] != 0;
+    // derived values of the stats pass are needed by every later pass that
+    // normalises log luminance or applies the sigmoid
+    const bool need_d = KIND != PK_STATS && KIND != PK_CDF && KIND != PK_DECOLOR && P.phase_kind[0] == PK_STATS;
+    // programmatic dependent launch: let the next pass start launching its CTAs as
+    // ours retire, and wait here until the previous pass has completed and its
+    // memory is visible
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (P.profile && threadIdx.x == 0) atomicMax(&P.ctrl->prof[PROF_KSTART_NOT], ~globaltimer_ns());
+    int cached = -1;
+    for (int t = blockIdx.x; t < total; t += gridDim.x) {
+        const int tt = rev ? total - 1 - t : t;
+        int lo = 0, hi = P.n_img - 1;  // image: last one whose first tile is <= tt
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (P.seg_start[ph][mid] <= tt) lo = mid; else hi = mid - 1;
+        }
+        const int img = lo, lt = tt - P.seg_start[ph][img];
         const DcImage& im = P.img[img];
         DcImgCtrl* ic = img_ctrl(P.ctrl, img);
+        if (need_d && img != cached) {
+            if (threadIdx.x == 0) s_d = derive(ic, (long long)im.prow * (long long)im.pcol);
+            cta_sync();
+            cached = img;
+        }
+        if (P.profile && threadIdx.x == 0) atomicMax(&ic->t_start_not[ph], ~globaltimer_ns());
         int I;
-        const TileRect tr = tile_rect<OPK>(P, im, kind, m.lt, I);
-        if (P.profile && threadIdx.x == 0) atomicMax(&ic->t_start_not[p], ~globaltimer_ns());
-        if constexpr (OPK == OPK_DECOLOR) {
+        const TileRect tr = tile_rect<OPK>(P, im, KIND, lt, I);
+        if constexpr (KIND == PK_DECOLOR) {
             constexpr int G = InT<IN_DT>::G;
             consume_tile<IN_DT>(im, tr, false, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) {
                 GroupIO<IN_DT>::store(im, r, c, n, vec, Lv);
             });
-        } else if constexpr (OPK == OPK_GLOBAL) {
-            if (kind == PK_STATS) {
-                tile_stats<IN_DT>(P, im, ic, tr, be, smem);
-            } else if (kind == PK_LOGHIST) {
-                tile_loghist<IN_DT>(P, im, ic, tr, be, m.d, smem);
-            } else {
-                if (P.stats && m.lt == 0) write_stats(P, im, ic, img, m.d);
-                tile_apply_global<IN_DT>(P, im, ic, tr, be, m.d, smem);
-            }
+        } else if constexpr (KIND == PK_STATS) {
+            tile_stats<IN_DT>(P, im, ic, tr, be, smem);
+        } else if constexpr (KIND == PK_LOGHIST) {
+            tile_loghist<IN_DT>(P, im, ic, tr, be, s_d, smem);
+        } else if constexpr (KIND == PK_APPLY_G) {
+            if (P.stats && lt == 0) write_stats(P, im, ic, img, s_d);
+            tile_apply_global<IN_DT>(P, im, ic, tr, be, s_d, smem);
+        } else if constexpr (KIND == PK_BLOCKH) {
+            tile_blockh<IN_DT>(P, im, tr, I, be, s_d, smem);
+        } else if constexpr (KIND == PK_CDF) {
+            tile_cdf(P, im, I, tr, smem);
         } else {
-            if (kind == PK_STATS)
-                tile_stats<IN_DT>(P, im, ic, tr, be, smem);
-            else if (kind == PK_BLOCKH)
-                tile_blockh<IN_DT>(P, im, tr, I, be, m.d, smem);
-            else if (kind == PK_CDF)
-                tile_cdf(P, im, I, tr, smem);
-            else
-                tile_apply_local<IN_DT>(P, im, tr, I, be, m.d, smem);
+            tile_apply_local<IN_DT>(P, im, tr, I, be, s_d, smem);
         }
-        cta_sync();
-        if (threadIdx.x == 0) {
-            if (P.profile) {
-                atomicMax(&ic->t_end[p], globaltimer_ns());
-                atomicAdd(&P.ctrl->prof[PROF_TILES], 1ull);
-            }
-            s_src.finished(img, p);
+        cta_sync();  // shared memory is reused by the next tile
+        if (P.profile && threadIdx.x == 0) {
+            atomicMax(&ic->t_end[ph], globaltimer_ns());
+            atomicAdd(&P.ctrl->prof[PROF_TILES], 1ull);
         }
     }
     if (P.profile && threadIdx.x == 0) atomicMax(&P.ctrl->prof[PROF_KEND], globaltimer_ns());
 }
 
-template <int IN_DT, int OPK, int CAP>
-int launch_one(const void* batch, LaunchShape ls, void* stream)
+template <int IN_DT, int OPK, int KIND, int CAP>
+int launch_one(const void* batch, int ph, LaunchShape ls, void* stream)
 {
     const DcBatch<CAP>& b = *reinterpret_cast<const DcBatch<CAP>*>(batch);
-    engine_kernel<IN_DT, OPK, CAP><<<ls.grid, kThreads, 0, (cudaStream_t)stream>>>(b);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ls.grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = (cudaStream_t)stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = ph > 0 ? 1 : 0;  // the first pass follows the memset
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, pass_kernel<IN_DT, OPK, KIND, CAP>, b, ph) != cudaSuccess) return DC_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? DC_OK : DC_ERR_CUDA;
 }
 
-template <int IN_DT, int OPK, int CAP>
+template <int IN_DT, int OPK, int KIND, int CAP>
 int occupancy_one()
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, engine_kernel<IN_DT, OPK, CAP>, kThreads, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<IN_DT, OPK, KIND, CAP>, kThreads, 0) !=
         cudaSuccess)
         return 0;
     return nb;
 }
 
+// Valid (operation, pass kind) pairs, expanded for every batch capacity.
+#define DC_FOR_EACH_PASS(X)                                                                                     \
+    X(OPK_DECOLOR, PK_DECOLOR) X(OPK_GLOBAL, PK_STATS) X(OPK_GLOBAL, PK_LOGHIST) X(OPK_GLOBAL, PK_APPLY_G)      \
+        X(OPK_LOCAL, PK_STATS) X(OPK_LOCAL, PK_BLOCKH) X(OPK_LOCAL, PK_CDF) X(OPK_LOCAL, PK_APPLY_L)
+
 template <int IN_DT>
-int launch_dispatch(const void* batch, int cap, int opk, LaunchShape ls, void* stream)
+int launch_dispatch(const void* batch, int cap, int opk, int kind, int ph, LaunchShape ls, void* stream)
 {
-#define DC_CASE(OP, C) \
-    if (opk == OP && cap == C) return launch_one<IN_DT, OP, C>(batch, ls, stream);
-    DC_CASE(OPK_DECOLOR, kCapSmall)
-    DC_CASE(OPK_DECOLOR, kCapMid)
-    DC_CASE(OPK_DECOLOR, kCapLarge)
-    DC_CASE(OPK_GLOBAL, kCapSmall)
-    DC_CASE(OPK_GLOBAL, kCapMid)
-    DC_CASE(OPK_GLOBAL, kCapLarge)
-    DC_CASE(OPK_LOCAL, kCapSmall)
-    DC_CASE(OPK_LOCAL, kCapMid)
-    DC_CASE(OPK_LOCAL, kCapLarge)
+#define DC_CASE(OP, K)                                                                      \
+    if (opk == OP && kind == K) {                                                          \
+        if (cap == kCapSmall) return launch_one<IN_DT, OP, K, kCapSmall>(batch, ph, ls, stream); \
+        if (cap == kCapMid) return launch_one<IN_DT, OP, K, kCapMid>(batch, ph, ls, stream);     \
+        if (cap == kCapLarge) return launch_one<IN_DT, OP, K, kCapLarge>(batch, ph, ls, stream); \
+    }
+    DC_FOR_EACH_PASS(DC_CASE)
 #undef DC_CASE
     return DC_ERR_INVALID_ARG;
 }
 
 template <int IN_DT>
-int occupancy_dispatch(int cap, int opk)
+int occupancy_dispatch(int cap, int opk, int kind)
 {
-#define DC_CASE(OP, C) \
-    if (opk == OP && cap == C) return occupancy_one<IN_DT, OP, C>();
-    DC_CASE(OPK_DECOLOR, kCapSmall)
-    DC_CASE(OPK_DECOLOR, kCapMid)
-    DC_CASE(OPK_DECOLOR, kCapLarge)
-    DC_CASE(OPK_GLOBAL, kCapSmall)
-    DC_CASE(OPK_GLOBAL, kCapMid)
-    DC_CASE(OPK_GLOBAL, kCapLarge)
-    DC_CASE(OPK_LOCAL, kCapSmall)
-    DC_CASE(OPK_LOCAL, kCapMid)
-    DC_CASE(OPK_LOCAL, kCapLarge)
+#define DC_CASE(OP, K)                                                          \
+    if (opk == OP && kind == K) {                                              \
+        if (cap == kCapSmall) return occupancy_one<IN_DT, OP, K, kCapSmall>(); \
+        if (cap == kCapMid) return occupancy_one<IN_DT, OP, K, kCapMid>();     \
+        if (cap == kCapLarge) return occupancy_one<IN_DT, OP, K, kCapLarge>(); \
+    }
+    DC_FOR_EACH_PASS(DC_CASE)
 #undef DC_CASE
     return 0;
 }

@@ -1,16 +1,16 @@
-// Engine kernels for DC_U8 input (all operations, all batch capacities).
+// Pass kernels for DC_U8 input (all operations and pass kinds, all batch capacities).
 #include "dc_engine_impl.cuh"
 
 namespace dc {
 
-int launch_engine_u8(const void* batch, int cap, int opk, LaunchShape ls, void* stream)
+int launch_engine_u8(const void* batch, int cap, int opk, int kind, int ph, LaunchShape ls, void* stream)
 {
-    return launch_dispatch<DC_U8>(batch, cap, opk, ls, stream);
+    return launch_dispatch<DC_U8>(batch, cap, opk, kind, ph, ls, stream);
 }
 
-int occupancy_u8(int cap, int opk)
+int occupancy_u8(int cap, int opk, int kind)
 {
-    return occupancy_dispatch<DC_U8>(cap, opk);
+    return occupancy_dispatch<DC_U8>(cap, opk, kind);
 }
 
 }  // namespace dc

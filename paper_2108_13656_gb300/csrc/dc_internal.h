@@ -1,12 +1,10 @@
 // Internal structures shared by the host side (dc_abi.cu) and the engine kernels.
 //
-// One launch of the engine processes a batch of images of one input sample type
-// for one operation.  Each operation is a short chain of passes ("phases") per
-// image; every phase is cut into tiles, and one global atomic counter hands tiles
-// to CTAs in a fixed order (the segment table).  A tile of phase p of image i only
-// waits for phase p-1 of image i, and every such tile comes earlier in the order,
-// so all tiles it waits for are already held by running CTAs: the schedule cannot
-// deadlock, whatever the number of resident CTAs.
+// A call runs each image through a short chain of passes ("phases": statistics,
+// histograms, tone curve ...).  Every pass is one persistent kernel launch over
+// the tiles of that pass for all images of the batch; passes follow each other
+// on the caller's stream, so a pass sees everything the previous one wrote and no
+// kernel ever waits for another CTA.
 #pragma once
 
 #include <stdint.h>
@@ -52,13 +50,6 @@ struct DcImage {                 // 80 bytes
     int32_t tiles_x_loc;         // tiles per block row, local phases
     int32_t Hb, Wb;              // local: blocks
     int64_t ws_hist;             // byte offsets into the workspace (local)
-};
-
-struct DcSegment {               // 8 bytes
-    int32_t start;               // first global tile index of this segment
-    int16_t img;
-    int8_t phase;                // index into the op's phase list
-    int8_t reverse;              // hand the tiles out last-first (L2 reuse)
 };
 
 // Per-image control block, cleared by the host before every launch.  Tiles publish
@@ -108,7 +99,7 @@ struct DcWsHeader {
 
 template <int CAP>
 struct DcBatch {
-    int32_t n_img, n_seg, total_tiles, n_phase;
+    int32_t n_img, n_phase;
     int32_t phase_kind[kMaxPhases];
     int32_t tile_rows, tile_cols;      // pixelwise phases
     int32_t loc_tile_cols;             // local phases (tile height = block_s)
@@ -121,16 +112,15 @@ struct DcBatch {
     int32_t block_s, radius, bins;
     uint32_t s_magic;                  // ceil(2^32 / block_s), 0 for block_s = 1: exact division of offsets < 2^16
     float alpha;
-    uint32_t withhold_ready;
-    uint32_t profile;                  // record phase timestamps and wait counters
-    unsigned long long timeout_ns;
+    uint32_t profile;                  // record phase timestamps
     DcCtrl* ctrl;
     uint32_t* err;                     // call-level error word (workspace header)
     dc_global_stats* stats;            // nullable; indexed by img_stats_index
     uint8_t* ws;
     int32_t stats_index[CAP];
     DcImage img[CAP];
-    DcSegment seg[CAP * kMaxPhases];
+    int32_t reverse[kMaxPhases];         // hand a pass's tiles out last-first (L2 reuse)
+    int32_t seg_start[kMaxPhases][CAP + 1];  // first tile of each image, per pass
 };
 
 #ifdef __CUDACC__
@@ -144,12 +134,12 @@ struct LaunchShape {
     int grid;
 };
 
-// opk: 0 decolorize, 1 global, 2 local
-int launch_engine_u8(const void* batch, int cap, int opk, LaunchShape ls, void* stream);
-int launch_engine_f16(const void* batch, int cap, int opk, LaunchShape ls, void* stream);
-int launch_engine_f32(const void* batch, int cap, int opk, LaunchShape ls, void* stream);
-int occupancy_u8(int cap, int opk);
-int occupancy_f16(int cap, int opk);
-int occupancy_f32(int cap, int opk);
+// opk: 0 decolorize, 1 global, 2 local; kind: PhaseKind; ph: index of the pass
+int launch_engine_u8(const void* batch, int cap, int opk, int kind, int ph, LaunchShape ls, void* stream);
+int launch_engine_f16(const void* batch, int cap, int opk, int kind, int ph, LaunchShape ls, void* stream);
+int launch_engine_f32(const void* batch, int cap, int opk, int kind, int ph, LaunchShape ls, void* stream);
+int occupancy_u8(int cap, int opk, int kind);
+int occupancy_f16(int cap, int opk, int kind);
+int occupancy_f32(int cap, int opk, int kind);
 
 }  // namespace dc
