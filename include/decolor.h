@@ -180,6 +180,22 @@ DC_API int dc_decolorize_tonemap_local(const dc_image_in* in, const dc_image_out
                                        const dc_local_params* lparams, void* ws, size_t ws_bytes,
                                        void* stream);
 
+/* Global tone mapping for callers that cannot allocate device memory (no
+ * counterpart in the paper; it is a deployment convenience).  Same arguments and
+ * results as dc_decolorize_tonemap_global, without a workspace: the scratch is a
+ * fixed DC_NOALLOC_SCRATCH_BYTES array in the library's device memory, held by
+ * every GPU that loads the library until the process exits.  The call allocates
+ * nothing; it returns DC_ERR_WORKSPACE when the batch needs more scratch than
+ * that (about 1.1 KiB per image).  The first call on a device looks up the
+ * array's address with that device current; make that first call before any
+ * stream capture.  Every call reuses the same array, so calls whose executions
+ * overlap on the GPU (other streams, other threads) race: order them. */
+#define DC_NOALLOC_SCRATCH_BYTES 65536
+DC_API int dc_decolorize_tonemap_global_noalloc(const dc_image_in* in, const dc_image_out* out, int32_t n,
+                                                const dc_decolor_params* params,
+                                                const dc_global_params* gparams, dc_global_stats* stats,
+                                                void* stream);
+
 /* Workspace bytes a call of `op` (DC_OP_*) needs for these inputs; op_params is
  * NULL (DC_OP_DECOLORIZE, DC_OP_GLOBAL) or a dc_local_params* (DC_OP_LOCAL).
  * Returns 0 when the arguments are invalid.  The workspace must be 256-byte

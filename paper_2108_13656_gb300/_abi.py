@@ -70,6 +70,9 @@ _SIGS = {
     "dc_decolorize_tonemap_local": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                    ctypes.c_size_t, ctypes.c_void_p]),
+    "dc_decolorize_tonemap_global_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                                            ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                                            ctypes.c_void_p]),
     "dc_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "dc_query_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "dc_status_string": (ctypes.c_char_p, [ctypes.c_int]),

@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJDIR = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdecolor.so")
-SOURCES = ["dc_engine_u8.cu", "dc_engine_f16.cu", "dc_engine_f32.cu", "dc_abi.cu"]
+SOURCES = ["dc_engine_u8.cu", "dc_engine_f16.cu", "dc_engine_f32.cu", "dc_abi.cu", "dc_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 _lock = threading.Lock()
 
