@@ -152,8 +152,9 @@ typedef struct {
 } dc_global_stats;
 
 /* Kernel launch shape used for one (operation, input sample type): threads per CTA
- * (128, 256 or 512), tile rows and columns (columns a multiple of 16; for the local
- * operator the tile is block_s rows high and columns are rounded up to a multiple of
+ * (256), tile rows and columns (columns a multiple of 16, or 0 to size tiles per
+ * call so that they split evenly over the CTAs - the default except for the local
+ * operator, whose tile is block_s rows high with columns rounded to a multiple of
  * block_s) and resident CTAs per SM (0 = as many as fit).  None of these change
  * results: every reduction in the library is exact integer arithmetic. */
 typedef struct {

@@ -23,11 +23,13 @@ constexpr int kLocMaxBlocksX = 32;
 constexpr int kCdfChunk = 16;
 
 std::mutex g_mu;
+// tile_cols 0: sized per launch so the pass's tiles split evenly over the CTAs
 dc_tuning g_tune[3][3] = {
-    {{256, 4, 4096, 0}, {256, 4, 4096, 0}, {256, 4, 4096, 0}},
-    {{256, 4, 4096, 0}, {256, 4, 4096, 0}, {256, 4, 4096, 0}},
+    {{256, 1, 0, 0}, {256, 1, 0, 0}, {256, 1, 0, 0}},
+    {{256, 1, 0, 0}, {256, 1, 0, 0}, {256, 1, 0, 0}},
     {{256, 32, 256, 0}, {256, 32, 256, 0}, {256, 32, 256, 0}},
 };
+constexpr int kAutoCtasPerSm = 4;  // resident CTAs of a pass kernel (launch bounds)
 int g_profile = 0;
 thread_local int g_last_launches = 0;
 thread_local int g_call_launches = 0;
@@ -199,8 +201,20 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
     std::memset(b, 0, sizeof(DcBatch<CAP>));
     b->n_phase = phase_list(op, ldr, b->phase_kind);
     b->tile_rows = std::max(1, tu.tile_rows);
-    b->tile_cols = std::max(16, (tu.tile_cols + 15) / 16 * 16);
-    b->loc_tile_cols = op.opk == kOpkLocal ? local_tile_cols(op.l->block_s, tu.tile_cols) : 0;
+    if (tu.tile_cols > 0) {
+        b->tile_cols = std::max(16, (tu.tile_cols + 15) / 16 * 16);
+    } else {
+        // automatic: one tile per CTA for a single image, about four for a batch
+        int64_t px = 0;
+        for (int k = 0; k < n; ++k) px += (int64_t)in[idx[k]].width * in[idx[k]].height;
+        int nsm = 152, dev = 0;
+        if (launch && cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t ctas = (int64_t)nsm * (tu.ctas_per_sm > 0 ? tu.ctas_per_sm : kAutoCtasPerSm) * (n == 1 ? 1 : 4);
+        const int64_t want = (px + ctas - 1) / ctas;
+        b->tile_cols = (int)std::min<int64_t>(1 << 20, std::max<int64_t>(1024, (want + 15) / 16 * 16));
+        b->tile_rows = 1;
+    }
+    b->loc_tile_cols = op.opk == kOpkLocal ? local_tile_cols(op.l->block_s, tu.tile_cols > 0 ? tu.tile_cols : 256) : 0;
     b->beta_r = p->beta_r;
     b->beta_k = p->beta_k;
     b->ldr = ldr ? 1 : 0;
@@ -467,8 +481,9 @@ DC_API int dc_set_tuning(int32_t op, int32_t in_dtype, const dc_tuning* t)
 {
     if (op < DC_OP_DECOLORIZE || op > DC_OP_LOCAL || !dt_ok(in_dtype) || !t) return DC_ERR_INVALID_ARG;
     if (t->threads != 256) return DC_ERR_INVALID_ARG;
-    if (t->tile_rows < 1 || t->tile_rows > 4096 || t->tile_cols < 16 || t->tile_cols > (1 << 20) || (t->tile_cols % 16) != 0)
+    if (t->tile_rows < 1 || t->tile_rows > 4096 || t->tile_cols < 0 || t->tile_cols > (1 << 20) || (t->tile_cols % 16) != 0)
         return DC_ERR_INVALID_ARG;
+    if (op == DC_OP_LOCAL && t->tile_cols == 0) return DC_ERR_INVALID_ARG;
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return DC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_mu);
     g_tune[op][in_dtype] = *t;

@@ -43,6 +43,37 @@ __device__ __forceinline__ uint4 ld_stream16(const void* p)
     return v;
 }
 
+// L2 eviction-priority policies (createpolicy): input that is read once can leave
+// L2 first, so that a plane written for the next pass stays resident.
+__device__ __forceinline__ unsigned long long policy_evict_first()
+{
+    unsigned long long pol;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ unsigned long long policy_evict_last()
+{
+    unsigned long long pol;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ uint4 ld_stream16_hint(const void* p, unsigned long long pol)
+{
+    uint4 v;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+        : "l"(p), "l"(pol));
+    return v;
+}
+
+__device__ __forceinline__ void st_f4_hint(float* p, float4 v, unsigned long long pol)
+{
+    asm volatile("st.global.L2::cache_hint.v4.f32 [%0], {%1,%2,%3,%4}, %5;" ::"l"(p), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w), "l"(pol)
+                 : "memory");
+}
+
 __device__ __forceinline__ uint2 ld_stream8(const void* p)
 {
     uint2 v;
@@ -207,12 +238,20 @@ struct GroupIO {
 
     // The raw bytes of a full, aligned group: 24 (u8, three 8-byte loads) or 48
     // (f16, f32, three 16-byte loads).
+    // With a plane kept for later passes (f16/f32 input), the input is read only
+    // once, so it is loaded with an evict-first L2 policy.
     __device__ static __forceinline__ void load_raw(const DcImage& im, int r, int c, uint32_t (&w)[12])
     {
         const uint8_t* p = im.in + (int64_t)r * im.in_stride + (int64_t)c * 3 * ESZ;
         if constexpr (IN_DT == DC_U8) {
             const uint2 a = ld_stream8(p), b = ld_stream8(p + 8), d = ld_stream8(p + 16);
             w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y; w[4] = d.x; w[5] = d.y;
+        } else if (im.flags & IF_LPLANE) {
+            const unsigned long long pol = policy_evict_first();
+            const uint4 a = ld_stream16_hint(p, pol), b = ld_stream16_hint(p + 16, pol), d = ld_stream16_hint(p + 32, pol);
+            w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
+            w[4] = b.x; w[5] = b.y; w[6] = b.z; w[7] = b.w;
+            w[8] = d.x; w[9] = d.y; w[10] = d.z; w[11] = d.w;
         } else {
             const uint4 a = ld_stream16(p), b = ld_stream16(p + 16), d = ld_stream16(p + 32);
             w[0] = a.x; w[1] = a.y; w[2] = a.z; w[3] = a.w;
@@ -267,6 +306,22 @@ struct GroupIO {
         } else {
 #pragma unroll
             for (int k = 0; k < G; ++k) Lv[k] = (k < n) ? ld_cg_f(p + k) : 0.0f;
+        }
+    }
+
+    // The f32 plane a stats pass keeps for the next passes (evict-last in L2).
+    __device__ static __forceinline__ void store_plane(const DcImage& im, int r, int c, int n, bool vec,
+                                                       const float (&y)[G])
+    {
+        float* p = reinterpret_cast<float*>(im.out + (int64_t)r * im.out_stride) + c;
+        if (vec) {
+            const unsigned long long pol = policy_evict_last();
+#pragma unroll
+            for (int k = 0; k < G; k += 4) st_f4_hint(p + k, make_float4(y[k], y[k + 1], y[k + 2], y[k + 3]), pol);
+        } else {
+#pragma unroll
+            for (int k = 0; k < G; ++k)
+                if (k < n) p[k] = y[k];
         }
     }
 

@@ -254,7 +254,7 @@ __device__ void tile_stats(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* 
                 v[k] = 0.0f;
             }
         }
-        if (plane_out) GroupIO<IN_DT>::store(im, r, c, n, vec, plane_log ? v : Lv);
+        if (plane_out) GroupIO<IN_DT>::store_plane(im, r, c, n, vec, plane_log ? v : Lv);
         acc += __float2ll_rn(pairwise_sum<G>(v) * (float)(1 << kLogFixedShift));
     });
     acc = warp_sum_ll(acc);
