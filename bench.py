@@ -142,11 +142,18 @@ def measured_peak():
 
 
 def kernel_source_hash() -> str:
+    """Hash of the CUDA/C++ sources with comments and whitespace removed: it changes
+    exactly when the code that was profiled changes."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2108_13656_gb300", "csrc")
     for fn in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, fn), "rb") as f:
-            h.update(fn.encode() + f.read())
+        with open(os.path.join(csrc, fn), encoding="utf-8") as f:
+            src = f.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        src = " ".join(src.split())
+        h.update(fn.encode() + b"\0" + src.encode())
     return h.hexdigest()[:16]
 
 

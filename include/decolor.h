@@ -108,7 +108,10 @@ typedef struct {
  *              gray code floor(255 L + 1/2);
  *              HDR: u = (ln(L+delta) - lmin) / (lmax - lmin) (1/2 when lmax = lmin),
  *              256 bins over u, y = piecewise-linear cumulative histogram at u.
- * Defaults: gain_k = 1, delta = 1e-4.  gain_k >= 0, delta > 0 and finite. */
+ *              The HDR u uses ln(L + delta) in 2^-24 fixed point (exact integer
+ *              min, max and bin arithmetic, absolute error about 1e-7).
+ * Defaults: gain_k = 1, delta = 1e-4.  gain_k >= 0; delta finite and at least
+ * FLT_MIN (a normal binary32 number). */
 typedef struct {
     int32_t mode;
     float gain_k;
@@ -126,9 +129,10 @@ typedef struct {
  * spread uniformly over the bin; a pixel's value is the bilinear blend of the four
  * nearest block curves (nominal block centres, clamped at the border) evaluated at
  * its own u, then y = alpha * F + (1 - alpha) * u.
+ * HDR u is computed from ln(L + delta) in 2^-24 fixed point as in DC_HISTEQ.
  * Defaults: block_s = 32, radius_blocks = 2, bins = 32, alpha = 1, delta = 1e-4.
  * Limits: 1 <= block_s <= 64, 0 <= radius_blocks <= 16, 2 <= bins <= DC_MAX_BINS,
- * alpha in [0, 1]. */
+ * alpha in [0, 1], delta finite and at least FLT_MIN. */
 typedef struct {
     int32_t block_s;
     int32_t radius_blocks;
@@ -144,8 +148,10 @@ typedef struct {
     float logmin;         /* min of ln(L + delta) */
     float logmax;         /* max of ln(L + delta) */
     float reserved0;
-    int64_t logsum_fixed; /* exact sum over pixels of ln(L + delta) in units of 2^-20,
-                             each 8-pixel (u8, f16) or 4-pixel (f32) group rounded once */
+    int64_t logsum_fixed; /* exact sum over pixels of ln(L + delta) in units of 2^-24:
+                             DC_SIGMOID and 8-bit input round each 8-pixel (u8, f16) or
+                             4-pixel (f32) group's sum once; HDR DC_HISTEQ sums every
+                             pixel's fixed-point logarithm */
     int64_t npix;         /* width * height */
     uint32_t hist[256];   /* LDR: 8-bit gray-code histogram (always filled);
                              HDR: the DC_HISTEQ u-bin histogram (zeros in DC_SIGMOID) */

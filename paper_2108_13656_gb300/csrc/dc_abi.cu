@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cfloat>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -72,13 +73,13 @@ int validate_params(const dc_decolor_params* p, const OpArgs& op)
     if (op.opk == kOpkGlobal) {
         const dc_global_params* g = op.g;
         if (!g || (g->mode != DC_SIGMOID && g->mode != DC_HISTEQ) || g->reserved != 0) return DC_ERR_INVALID_ARG;
-        if (!finite_in(g->gain_k, 0.f, 1e6f) || !std::isfinite(g->delta) || !(g->delta > 0.f)) return DC_ERR_INVALID_ARG;
+        if (!finite_in(g->gain_k, 0.f, 1e6f) || !std::isfinite(g->delta) || !(g->delta >= FLT_MIN)) return DC_ERR_INVALID_ARG;
     } else if (op.opk == kOpkLocal) {
         const dc_local_params* l = op.l;
         if (!l || l->reserved != 0) return DC_ERR_INVALID_ARG;
         if (l->block_s < 1 || l->block_s > 64 || l->radius_blocks < 0 || l->radius_blocks > 16) return DC_ERR_INVALID_ARG;
         if (l->bins < 2 || l->bins > DC_MAX_BINS || !finite_in(l->alpha, 0.f, 1.f)) return DC_ERR_INVALID_ARG;
-        if (!std::isfinite(l->delta) || !(l->delta > 0.f)) return DC_ERR_INVALID_ARG;
+        if (!std::isfinite(l->delta) || !(l->delta >= FLT_MIN)) return DC_ERR_INVALID_ARG;
     }
     return DC_OK;
 }
@@ -102,8 +103,22 @@ struct Geometry {
 
 struct LaunchPlan {
     int in_dt;
+    bool plane;            // every image keeps an f32 plane between passes
     std::vector<int> idx;  // positions in the caller's arrays
 };
+
+// An image keeps its luminance (or its fixed-point log) in its f32 output between
+// passes: HDR input, a tone-mapping operation, f32 output.
+bool keeps_plane(const OpArgs& op, int in_dt, int out_dt)
+{
+    return op.opk != kOpkDecolor && in_dt != DC_U8 && out_dt == DC_F32;
+}
+
+// Passes that read the plane instead of recomputing L from RGB.
+bool reads_plane(int kind)
+{
+    return kind == PK_LOGHIST || kind == PK_APPLY_G || kind == PK_BLOCKH || kind == PK_APPLY_L;
+}
 
 // Phase chain of an operation for one input class.
 int phase_list(const OpArgs& op, bool ldr, int32_t* kinds)
@@ -115,6 +130,7 @@ int phase_list(const OpArgs& op, bool ldr, int32_t* kinds)
     if (op.opk == kOpkGlobal) {
         kinds[0] = PK_STATS;
         if (op.g->mode == DC_HISTEQ && !ldr) {
+            kinds[0] = PK_STATS_LOG;  // the histogram of u needs the exact log coordinate
             kinds[1] = PK_LOGHIST;
             kinds[2] = PK_APPLY_G;
             return 3;
@@ -123,7 +139,7 @@ int phase_list(const OpArgs& op, bool ldr, int32_t* kinds)
         return 2;
     }
     int n = 0;
-    if (!ldr) kinds[n++] = PK_STATS;
+    if (!ldr) kinds[n++] = PK_STATS_LOG;
     kinds[n++] = PK_BLOCKH;
     kinds[n++] = PK_CDF;
     kinds[n++] = PK_APPLY_L;
@@ -157,7 +173,7 @@ void make_geometry(const dc_image_in& in, const dc_image_out& out, const OpArgs&
     bool vec = al16(in.data) && al16(out.data);
     if (im.rows > 1) vec = vec && (in.stride_bytes % 16 == 0) && (out.stride_bytes % 16 == 0);
     im.flags = vec ? IF_VEC : 0u;
-    if (op.opk != kOpkDecolor && in.dtype != DC_U8 && out.dtype == DC_F32) {
+    if (keeps_plane(op, in.dtype, out.dtype)) {
         im.flags |= IF_LPLANE;
         // the local operator and HDR histogram equalisation only need ln(L + delta)
         if (op.opk == kOpkLocal || (op.opk == kOpkGlobal && op.g->mode == DC_HISTEQ)) im.flags |= IF_PLANE_LOG;
@@ -184,7 +200,7 @@ void make_geometry(const dc_image_in& in, const dc_image_out& out, const OpArgs&
 }
 
 template <int CAP>
-int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::vector<int>& idx,
+int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::vector<int>& idx, bool plane,
                      const dc_decolor_params* p, const OpArgs& op, uint8_t* ws, bool first, int64_t* need,
                      void* stream, bool launch)
 {
@@ -298,19 +314,20 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
     int rc = DC_OK;
     for (int ph = 0; ph < b->n_phase && rc == DC_OK; ++ph) {
         const int kind = b->phase_kind[ph];
-        int occ = in_dt == DC_U8 ? occupancy_u8(CAP, op.opk, kind)
-                                 : (in_dt == DC_F16 ? occupancy_f16(CAP, op.opk, kind) : occupancy_f32(CAP, op.opk, kind));
+        const bool pl = plane && reads_plane(kind);
+        int occ = in_dt == DC_U8 ? occupancy_u8(CAP, op.opk, kind, pl)
+                                 : (in_dt == DC_F16 ? occupancy_f16(CAP, op.opk, kind, pl) : occupancy_f32(CAP, op.opk, kind, pl));
         if (occ <= 0) occ = 1;
         const int per_sm = tu.ctas_per_sm > 0 ? std::min(tu.ctas_per_sm, occ) : occ;
         LaunchShape ls;
         ls.threads = 256;
         ls.grid = (int)std::min<int64_t>(b->seg_start[ph][n], (int64_t)per_sm * nsm);
         if (in_dt == DC_U8)
-            rc = launch_engine_u8(b, CAP, op.opk, kind, ph, ls, stream);
+            rc = launch_engine_u8(b, CAP, op.opk, kind, ph, pl, ls, stream);
         else if (in_dt == DC_F16)
-            rc = launch_engine_f16(b, CAP, op.opk, kind, ph, ls, stream);
+            rc = launch_engine_f16(b, CAP, op.opk, kind, ph, pl, ls, stream);
         else
-            rc = launch_engine_f32(b, CAP, op.opk, kind, ph, ls, stream);
+            rc = launch_engine_f32(b, CAP, op.opk, kind, ph, pl, ls, stream);
         if (rc == DC_OK) ++g_call_launches;
     }
     delete b;
@@ -339,21 +356,6 @@ int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_deco
             if (a0 < b1 && b0 < a1) return DC_ERR_INVALID_ARG;
         }
     }
-    // group by input sample type, keep caller order inside a group, chunk by capacity
-    std::vector<LaunchPlan> plans;
-    for (int dt = DC_U8; dt <= DC_F32; ++dt) {
-        LaunchPlan cur;
-        cur.in_dt = dt;
-        for (int k = 0; k < n; ++k) {
-            if (in[k].dtype != dt) continue;
-            cur.idx.push_back(k);
-            if ((int)cur.idx.size() == kCapLarge) {
-                plans.push_back(cur);
-                cur.idx.clear();
-            }
-        }
-        if (!cur.idx.empty()) plans.push_back(cur);
-    }
     // a fake (valid) output descriptor for size queries
     std::vector<dc_image_out> fake;
     const dc_image_out* outs = out;
@@ -367,16 +369,36 @@ int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_deco
         }
         outs = fake.data();
     }
+    // group by input sample type and plane use, keep caller order inside a group,
+    // chunk by capacity (a size query groups by sample type only: its groups are
+    // never smaller than the call's)
+    std::vector<LaunchPlan> plans;
+    for (int dt = DC_U8; dt <= DC_F32; ++dt) {
+        for (int pl = 0; pl < 2; ++pl) {
+            LaunchPlan cur;
+            cur.in_dt = dt;
+            cur.plane = pl != 0;
+            for (int k = 0; k < n; ++k) {
+                if (in[k].dtype != dt || keeps_plane(op, dt, outs[k].dtype) != cur.plane) continue;
+                cur.idx.push_back(k);
+                if ((int)cur.idx.size() == kCapLarge) {
+                    plans.push_back(cur);
+                    cur.idx.clear();
+                }
+            }
+            if (!cur.idx.empty()) plans.push_back(cur);
+        }
+    }
     int64_t need = kHeaderBytes;
     for (const LaunchPlan& pl : plans) {
         const int cnt = (int)pl.idx.size();
         int r2;
         if (cnt <= kCapSmall)
-            r2 = build_and_launch<kCapSmall>(in, outs, pl.idx, p, op, nullptr, false, &need, nullptr, false);
+            r2 = build_and_launch<kCapSmall>(in, outs, pl.idx, pl.plane, p, op, nullptr, false, &need, nullptr, false);
         else if (cnt <= kCapMid)
-            r2 = build_and_launch<kCapMid>(in, outs, pl.idx, p, op, nullptr, false, &need, nullptr, false);
+            r2 = build_and_launch<kCapMid>(in, outs, pl.idx, pl.plane, p, op, nullptr, false, &need, nullptr, false);
         else
-            r2 = build_and_launch<kCapLarge>(in, outs, pl.idx, p, op, nullptr, false, &need, nullptr, false);
+            r2 = build_and_launch<kCapLarge>(in, outs, pl.idx, pl.plane, p, op, nullptr, false, &need, nullptr, false);
         if (r2 != DC_OK) return r2;
     }
     if (query) {
@@ -392,11 +414,11 @@ int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_deco
         uint8_t* w = static_cast<uint8_t*>(ws);
         int r2;
         if (cnt <= kCapSmall)
-            r2 = build_and_launch<kCapSmall>(in, out, pl.idx, p, op, w, first, &dummy, stream, true);
+            r2 = build_and_launch<kCapSmall>(in, out, pl.idx, pl.plane, p, op, w, first, &dummy, stream, true);
         else if (cnt <= kCapMid)
-            r2 = build_and_launch<kCapMid>(in, out, pl.idx, p, op, w, first, &dummy, stream, true);
+            r2 = build_and_launch<kCapMid>(in, out, pl.idx, pl.plane, p, op, w, first, &dummy, stream, true);
         else
-            r2 = build_and_launch<kCapLarge>(in, out, pl.idx, p, op, w, first, &dummy, stream, true);
+            r2 = build_and_launch<kCapLarge>(in, out, pl.idx, pl.plane, p, op, w, first, &dummy, stream, true);
         if (r2 != DC_OK) return r2;
         first = false;
     }

@@ -1,16 +1,19 @@
-// Persistent engine kernel: decolorization (Eq. 1-6, Sec. II-B) fused with the
-// global (Sec. III-B-1) and local (Sec. III-B-2) tone-mapping passes.
+// Pass kernels: decolorization (Eq. 1-6, Sec. II-B) fused with the global
+// (Sec. III-B-1) and local (Sec. III-B-2) tone-mapping passes.
 //
 // Layout and schedule (see dc_internal.h): a batch of images, each a chain of
-// phases, each phase cut into tiles; CTAs pull tile numbers from one atomic
-// counter.  Pixels are read as 48-byte groups (16 u8 / 8 f16 / 4 f32 pixels) with
-// three 16-byte vector loads when the image is 16-byte aligned; everything else
-// (ragged row tails, unaligned images) takes a per-pixel path with identical
-// arithmetic.  All arithmetic is binary32; every cross-thread reduction is exact
-// integer arithmetic (the log-sum in 2^-20 fixed point, min/max on ordered bit
-// patterns, histograms as counts), so results do not depend on the launch shape.
+// passes, each pass cut into tiles; one persistent launch per pass takes the
+// tiles of every image in a fixed round-robin order (tile t goes to CTA
+// t mod grid).  Pixels are read in groups (8 u8 pixels = 24 bytes, 8 f16 or
+// 4 f32 pixels = 48 bytes) with 8- or 16-byte vector loads when the image is
+// 16-byte aligned; everything else (ragged row tails, unaligned images) takes a
+// per-pixel path with identical arithmetic.  All arithmetic is binary32; every
+// cross-thread reduction is exact integer arithmetic (the log-sum in 2^-20 fixed
+// point, min/max on ordered bit patterns, histograms as counts), so results do
+// not depend on the launch shape.
 #pragma once
 
+#include <climits>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -177,6 +180,28 @@ __device__ __forceinline__ float luminance_hdr(float R, float G, float B, const 
     return L;
 }
 
+// ------------------------------------------------------ fixed-point log ------
+// ln x in units of 2^-24, for x >= FLT_MIN: x = 2^e m with m in (1/sqrt 2, sqrt 2],
+// ln x = e ln 2 + ln m, the first term exact in 2^-40 units, ln m (|ln m| < 0.35)
+// from the hardware base-2 logarithm (absolute error about 2^-22 on [1/2, 2]), one
+// rounding at the end.  Absolute error about 2e-7 whatever the magnitude of ln x,
+// where a binary32 ln x near 7 is only good to 5e-7 and its normalisation by the
+// log range adds as much again: the histogram forms need the absolute error.
+constexpr long long kLn2Q40 = 762123384786LL;  // round(ln 2 * 2^40)
+__device__ __forceinline__ int ln_q24(float x)
+{
+    const uint32_t bits = __float_as_uint(x);
+    int e = (int)(bits >> 23) - 127;
+    uint32_t mb = (bits & 0x007FFFFFu) | 0x3F800000u;  // m in [1, 2)
+    if (mb > 0x3FB504F3u) {                            // m > sqrt 2: use m / 2
+        mb -= 0x00800000u;
+        ++e;
+    }
+    const float lm = __log2f(__uint_as_float(mb)) * 0.693147180559945309f;
+    const long long q = (long long)e * kLn2Q40 + __float2ll_rn(lm * 1099511627776.0f);  // 2^-40 units
+    return (int)((q + (1ll << 15)) >> 16);
+}
+
 // 8-bit code of y in [0,1]: floor(255 y + 1/2), clamped.
 __device__ __forceinline__ uint32_t quant_u8(float y)
 {
@@ -232,7 +257,7 @@ struct GroupIO {
 #pragma unroll
             for (int k = 0; k < G; ++k)
                 Lv[k] = luminance_hdr(__uint_as_float(w[3 * k]), __uint_as_float(w[3 * k + 1]),
-                                      __uint_as_float(w[3 * k + 2]), be);
+                                               __uint_as_float(w[3 * k + 2]), be);
         }
     }
 
@@ -431,13 +456,6 @@ __device__ __forceinline__ DcImgCtrl* img_ctrl(DcCtrl* c, int i)
     return reinterpret_cast<DcImgCtrl*>(reinterpret_cast<uint8_t*>(c) + sizeof(DcCtrl)) + i;
 }
 
-// Normalised log luminance u in [0,1] for the HDR histogram forms, from a plane
-// value that is either L or already ln(L + delta).
-__device__ __forceinline__ float log_u(float val, bool is_log, float delta, float lmin, float inv_range)
-{
-    if (inv_range == 0.0f) return 0.5f;
-    const float v = is_log ? val : ln_fast(val + delta);
-    return fminf(fmaxf((v - lmin) * inv_range, 0.0f), 1.0f);
-}
+
 
 }  // namespace dc

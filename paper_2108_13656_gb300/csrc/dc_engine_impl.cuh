@@ -11,9 +11,15 @@ struct TileRect {
     int r0, r1, c0, c1;
 };
 
-// Values a tile derives from an image's finished statistics pass.
+// Values a tile derives from an image's finished statistics pass.  For the
+// fixed-point log forms: vmin, vmax of v = round(ln(L + delta) 2^24), the range
+// R = vmax - vmin shifted right by sh until it is below 2^30 (Rs), and 1/Rs.  A
+// constant image gets the range [v - 1, v + 1], which puts every pixel at u = 1/2.
 struct Derived {
-    float mu, exp_mu, lmin, lmax, inv_range;
+    float mu, exp_mu, lmin, lmax;
+    int vmin, vmax, sh;
+    uint32_t Rs;
+    float invRs;
 };
 
 __device__ __forceinline__ void cta_sync() { __syncthreads(); }
@@ -76,24 +82,79 @@ __device__ __forceinline__ TileRect tile_rect(const DcBatch<CAP>& P, const DcIma
     return tr;
 }
 
-// Phases after the first read the f32 plane when the image keeps one.
-__device__ __forceinline__ bool from_plane(const DcImage& im, int kind)
-{
-    return (im.flags & IF_LPLANE) != 0 && kind != PK_STATS && kind != PK_DECOLOR;
-}
 
-// mu, lmin, lmax from the exact integer accumulators of a finished stats pass.
-__device__ __forceinline__ Derived derive(const DcImgCtrl* ic, long long N)
+// mu, lmin, lmax from the exact integer accumulators of a finished stats pass
+// (fixed_log: the min and max are of the 2^-24 fixed-point logarithms).
+__device__ __forceinline__ Derived derive(const DcImgCtrl* ic, long long N, bool fixed_log)
 {
     Derived d;
     const long long sum = (long long)ld_cg_u64(&ic->logsum);
     const long long q = sum / N, rem = sum - q * N;
-    d.mu = (__ll2float_rn(q) + __ll2float_rn(rem) / __ll2float_rn(N)) * (1.0f / (float)(1 << kLogFixedShift));
+    constexpr float unit = 1.0f / (float)(1 << kLogFixedShift);
+    d.mu = (__ll2float_rn(q) + __ll2float_rn(rem) / __ll2float_rn(N)) * unit;
     d.exp_mu = expf(d.mu);
-    d.lmin = ord_dec(~ld_cg_u32(&ic->lmin_nord));
-    d.lmax = ord_dec(ld_cg_u32(&ic->lmax_ord));
-    d.inv_range = d.lmax > d.lmin ? 1.0f / (d.lmax - d.lmin) : 0.0f;
+    d.vmin = d.vmax = d.sh = 0;
+    d.Rs = 2u;
+    d.invRs = 0.5f;
+    if (fixed_log) {
+        const int vmax = (int)(ld_cg_u32(&ic->lmax_ord) ^ 0x80000000u);
+        const int vmin = (int)(~ld_cg_u32(&ic->lmin_nord) ^ 0x80000000u);
+        d.lmin = (float)vmin * unit;
+        d.lmax = (float)vmax * unit;
+        if (vmax > vmin) {
+            d.vmin = vmin;
+            d.vmax = vmax;
+            uint32_t R = (uint32_t)vmax - (uint32_t)vmin;
+            while (R >= (1u << 30)) {
+                R >>= 1;
+                ++d.sh;
+            }
+            d.Rs = R;
+            d.invRs = 1.0f / (float)R;
+        } else {
+            d.vmin = vmin - 1;
+            d.vmax = vmin + 1;
+        }
+    } else {
+        d.lmin = ord_dec(~ld_cg_u32(&ic->lmin_nord));
+        d.lmax = ord_dec(ld_cg_u32(&ic->lmax_ord));
+    }
     return d;
+}
+
+// Bin coordinate t = nb u = nb (v - vmin) / R of a fixed-point log value, in units
+// of 2^-S (0 <= t <= nb).  The integer part comes out exact: a float quotient
+// estimates it to within one and the exact 32-bit remainder (|rem| < 2^31 because
+// Rs < 2^30) corrects it; the one rounding left is that of the fraction to 2^-S.
+template <int S>
+__device__ __forceinline__ uint32_t bin_coord(int v, const Derived& d, int nb)
+{
+    v = min(max(v, d.vmin), d.vmax);
+    const uint32_t dv = ((uint32_t)v - (uint32_t)d.vmin) >> d.sh;
+    int j = (int)((float)dv * ((float)nb * d.invRs));
+    int rem = (int)(dv * (uint32_t)nb - (uint32_t)j * d.Rs);
+    if (rem < 0) {
+        --j;
+        rem += (int)d.Rs;
+    } else if (rem >= (int)d.Rs) {
+        ++j;
+        rem -= (int)d.Rs;
+    }
+    const uint32_t f = __float2uint_rn((float)rem * (d.invRs * (float)(1u << S)));
+    return ((uint32_t)j << S) + f;
+}
+
+// Coordinate shifts: 2^-24 of a bin for the local operator (bins <= 64), 2^-22 of
+// a bin for the 256-bin global histogram, so that nb 2^S stays below 2^31.
+constexpr int kLocTS = 24, kGlobTS = 22;
+
+// Bin coordinate of a value a histogram pass sees: from the plane's fixed-point
+// log (a histogram pass then keeps the coordinate in the plane for the apply
+// pass), or from L recomputed from RGB.
+template <int S>
+__device__ __forceinline__ uint32_t coord_of(float val, bool is_log_plane, float delta, const Derived& d, int nb)
+{
+    return bin_coord<S>(is_log_plane ? __float_as_int(val) : ln_q24(val + delta), d, nb);
 }
 
 // ------------------------------------------------------------- group walk ---
@@ -174,17 +235,12 @@ __device__ __forceinline__ void walk_tile(const DcImage& im, const TileRect& t, 
     }
 }
 
-template <int IN_DT, class F>
-__device__ __forceinline__ void consume_tile(const DcImage& im, const TileRect& t, bool plane, const Beta& be, F&& f)
+// PLANE: the pass reads the f32 plane an earlier pass kept (every image of the
+// launch has one), else it recomputes the luminance from RGB.
+template <int IN_DT, bool PLANE, class F>
+__device__ __forceinline__ void consume_tile(const DcImage& im, const TileRect& t, const Beta& be, F&& f)
 {
-    if constexpr (IN_DT == DC_U8) {
-        walk_tile<IN_DT, false>(im, t, be, f);  // 8-bit images never keep a plane
-    } else {
-        if (plane)
-            walk_tile<IN_DT, true>(im, t, be, f);
-        else
-            walk_tile<IN_DT, false>(im, t, be, f);
-    }
+    walk_tile<IN_DT, PLANE && IN_DT != DC_U8>(im, t, be, f);  // 8-bit images never keep a plane
 }
 
 // --------------------------------------------------------------- reductions --
@@ -225,13 +281,17 @@ __device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t* scratc
 }
 
 // ------------------------------------------------------------- phase: stats --
-template <int IN_DT, int CAP>
+// LOGQ = false (sigmoid curve, 8-bit input): ln(L + delta) from the hardware
+// logarithm, each group's pairwise sum rounded once to 2^-24; min/max on the
+// floats.  LOGQ = true (HDR histogram forms): the fixed-point logarithm of every
+// pixel, summed exactly; min/max on the integers; the plane keeps the integers.
+template <int IN_DT, bool LOGQ, int CAP>
 __device__ void tile_stats(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* ic,
                            const TileRect& t, const Beta& be, unsigned char* smem)
 {
     constexpr int G = InT<IN_DT>::G;
     SmemStats& S = *reinterpret_cast<SmemStats*>(smem);
-    const bool want_hist = P.need_gray_hist != 0;
+    const bool want_hist = !LOGQ && P.need_gray_hist != 0;
     const bool plane_out = (im.flags & IF_LPLANE) != 0;
     const bool plane_log = (im.flags & IF_PLANE_LOG) != 0;
     if (want_hist) {
@@ -240,45 +300,84 @@ __device__ void tile_stats(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* 
     }
     long long acc = 0;
     float vmin = INFINITY, vmax = -INFINITY;
+    int qmin = INT_MAX, qmax = INT_MIN;
     const float delta = P.delta;
-    consume_tile<IN_DT>(im, t, false, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+    consume_tile<IN_DT, false>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
         float v[G];
+        if constexpr (LOGQ) {
 #pragma unroll
-        for (int k = 0; k < G; ++k) {
-            if (k < n) {
-                v[k] = ln_fast(Lv[k] + delta);
-                vmin = fminf(vmin, v[k]);
-                vmax = fmaxf(vmax, v[k]);
-                if (want_hist) atomicAdd(&S.hist[quant_u8(Lv[k])], 1u);
-            } else {
-                v[k] = 0.0f;
+            for (int k = 0; k < G; ++k) {
+                if (k < n) {
+                    const int q = ln_q24(Lv[k] + delta);
+                    acc += q;
+                    qmin = min(qmin, q);
+                    qmax = max(qmax, q);
+                    v[k] = __int_as_float(q);
+                } else {
+                    v[k] = 0.0f;
+                }
             }
+            if (plane_out) GroupIO<IN_DT>::store_plane(im, r, c, n, vec, plane_log ? v : Lv);
+        } else {
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                if (k < n) {
+                    v[k] = ln_fast(Lv[k] + delta);
+                    vmin = fminf(vmin, v[k]);
+                    vmax = fmaxf(vmax, v[k]);
+                    if (want_hist) atomicAdd(&S.hist[quant_u8(Lv[k])], 1u);
+                } else {
+                    v[k] = 0.0f;
+                }
+            }
+            if (plane_out) GroupIO<IN_DT>::store_plane(im, r, c, n, vec, Lv);
+            acc += __float2ll_rn(pairwise_sum<G>(v) * (float)(1 << kLogFixedShift));
         }
-        if (plane_out) GroupIO<IN_DT>::store_plane(im, r, c, n, vec, plane_log ? v : Lv);
-        acc += __float2ll_rn(pairwise_sum<G>(v) * (float)(1 << kLogFixedShift));
     });
     acc = warp_sum_ll(acc);
-    vmin = warp_min(vmin);
-    vmax = warp_max(vmax);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) {
-        S.wsum[warp] = acc;
-        S.wmin[warp] = vmin;
-        S.wmax[warp] = vmax;
+    if constexpr (LOGQ) {
+        qmin = __reduce_min_sync(0xffffffffu, qmin);
+        qmax = __reduce_max_sync(0xffffffffu, qmax);
+        if (lane == 0) {
+            S.wsum[warp] = acc;
+            S.wmin[warp] = __int_as_float(qmin);
+            S.wmax[warp] = __int_as_float(qmax);
+        }
+    } else {
+        vmin = warp_min(vmin);
+        vmax = warp_max(vmax);
+        if (lane == 0) {
+            S.wsum[warp] = acc;
+            S.wmin[warp] = vmin;
+            S.wmax[warp] = vmax;
+        }
     }
     cta_sync();
     if (threadIdx.x == 0) {
-        long long s = 0;
-        float mn = INFINITY, mx = -INFINITY;
-        for (int w = 0; w < (kThreads / 32); ++w) {
-            s += S.wsum[w];
-            mn = fminf(mn, S.wmin[w]);
-            mx = fmaxf(mx, S.wmax[w]);
-        }
-        atomicAdd(&ic->logsum, (unsigned long long)s);
-        if (mx >= mn) {
-            atomicMax(&ic->lmax_ord, ord_enc(mx));
-            atomicMax(&ic->lmin_nord, ~ord_enc(mn));
+        long long sum = 0;
+        for (int w = 0; w < (kThreads / 32); ++w) sum += S.wsum[w];
+        atomicAdd(&ic->logsum, (unsigned long long)sum);
+        if constexpr (LOGQ) {
+            int mn = INT_MAX, mx = INT_MIN;
+            for (int w = 0; w < (kThreads / 32); ++w) {
+                mn = min(mn, __float_as_int(S.wmin[w]));
+                mx = max(mx, __float_as_int(S.wmax[w]));
+            }
+            if (mx >= mn) {  // ordered encoding of a signed integer: flip the sign bit
+                atomicMax(&ic->lmax_ord, (uint32_t)mx ^ 0x80000000u);
+                atomicMax(&ic->lmin_nord, ~((uint32_t)mn ^ 0x80000000u));
+            }
+        } else {
+            float mn = INFINITY, mx = -INFINITY;
+            for (int w = 0; w < (kThreads / 32); ++w) {
+                mn = fminf(mn, S.wmin[w]);
+                mx = fmaxf(mx, S.wmax[w]);
+            }
+            if (mx >= mn) {
+                atomicMax(&ic->lmax_ord, ord_enc(mx));
+                atomicMax(&ic->lmin_nord, ~ord_enc(mn));
+            }
         }
     }
     if (want_hist) {
@@ -288,24 +387,27 @@ __device__ void tile_stats(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* 
 }
 
 // ---------------------------------------------------------- phase: log hist --
-template <int IN_DT, int CAP>
+template <int IN_DT, bool PLANE, int CAP>
 __device__ void tile_loghist(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* ic,
                              const TileRect& t, const Beta& be, const Derived& d, unsigned char* smem)
 {
     constexpr int G = InT<IN_DT>::G;
     SmemStats& S = *reinterpret_cast<SmemStats*>(smem);
     for (int b = threadIdx.x; b < 256; b += kThreads) S.hist[b] = 0;
-    const bool plane = from_plane(im, PK_LOGHIST);
-    const bool is_log = (im.flags & IF_PLANE_LOG) != 0;
+    constexpr bool plane = PLANE;
+    const bool is_log = plane && (im.flags & IF_PLANE_LOG) != 0;
     const float delta = P.delta;
     cta_sync();
-    consume_tile<IN_DT>(im, t, plane, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+    consume_tile<IN_DT, PLANE>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+        float tq[G] = {};
 #pragma unroll
-        for (int k = 0; k < G; ++k)
-            if (k < n) {
-                const float u = log_u(Lv[k], plane && is_log, delta, d.lmin, d.inv_range);
-                atomicAdd(&S.hist[min((int)(256.0f * u), 255)], 1u);
-            }
+        for (int k = 0; k < G; ++k) {
+            const uint32_t q = k < n ? coord_of<kGlobTS>(Lv[k], is_log, delta, d, 256) : 0u;
+            tq[k] = __uint_as_float(q);
+            if (k < n) atomicAdd(&S.hist[min(q >> kGlobTS, 255u)], 1u);
+        }
+        // the apply pass reads the coordinate instead of the logarithm
+        if (is_log) GroupIO<IN_DT>::store_plane(im, r, c, n, vec, tq);
     });
     cta_sync();
     for (int b = threadIdx.x; b < 256; b += kThreads)
@@ -331,20 +433,20 @@ __device__ void write_stats(const DcBatch<CAP>& P, const DcImage& im, const DcIm
 }
 
 // ------------------------------------------------------- phase: global apply --
-template <int IN_DT, int CAP>
+template <int IN_DT, bool PLANE, int CAP>
 __device__ void tile_apply_global(const DcBatch<CAP>& P, const DcImage& im,
                                   DcImgCtrl* ic, const TileRect& t, const Beta& be, const Derived& d,
                                   unsigned char* smem)
 {
     constexpr int G = InT<IN_DT>::G;
     SmemApplyG& S = *reinterpret_cast<SmemApplyG*>(smem);
-    const bool plane = from_plane(im, PK_APPLY_G);
+    constexpr bool plane = PLANE;
     const bool is_log = plane && (im.flags & IF_PLANE_LOG) != 0;
     const float delta = P.delta;
     if (P.mode == DC_SIGMOID) {
         const float mu = d.mu, exp_mu = d.exp_mu, k = P.gain_k;
         const bool one = P.gain_is_one != 0;
-        consume_tile<IN_DT>(im, t, plane, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+        consume_tile<IN_DT, PLANE>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
 #pragma unroll
             for (int j = 0; j < G; ++j) {
                 const float x = Lv[j] + delta;
@@ -368,16 +470,19 @@ __device__ void tile_apply_global(const DcBatch<CAP>& P, const DcImage& im,
         }
         cta_sync();
         const bool ldr = P.ldr != 0;
-        consume_tile<IN_DT>(im, t, plane, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+        consume_tile<IN_DT, PLANE>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
 #pragma unroll
             for (int j = 0; j < G; ++j) {
                 if (ldr) {
                     Lv[j] = S.lut[quant_u8(Lv[j])];
                 } else {
-                    const float u = 256.0f * log_u(Lv[j], is_log, delta, d.lmin, d.inv_range);
-                    const int b = min((int)u, 255);
+                    // bin coordinate: kept in the plane by the histogram pass, or
+                    // computed from L recomputed from RGB
+                    const uint32_t q = is_log ? __float_as_uint(Lv[j]) : coord_of<kGlobTS>(Lv[j], false, delta, d, 256);
+                    const uint32_t b = min(q >> kGlobTS, 255u);
+                    const float frac = (float)(q - (b << kGlobTS)) * (1.0f / (float)(1u << kGlobTS));
                     const float e0 = S.lut[b], e1 = S.lut[b + 1];
-                    Lv[j] = fmaf(u - (float)b, e1 - e0, e0);
+                    Lv[j] = fmaf(frac, e1 - e0, e0);
                 }
             }
             GroupIO<IN_DT>::store(im, r, c, n, vec, Lv);
@@ -391,7 +496,7 @@ __device__ void tile_apply_global(const DcBatch<CAP>& P, const DcImage& im,
 // pixels with lower bin j and sums their f (two native 32-bit shared atomics per
 // run of equal keys; exact for blocks up to 64 x 64).  Bin j's mass is then
 // count_j 2^20 - F_j + F_{j-1}, stored as a 64-bit integer in units of 2^-20.
-template <int IN_DT, int CAP>
+template <int IN_DT, bool PLANE, int CAP>
 __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const TileRect& t, int I,
                             const Beta& be, const Derived& d, unsigned char* smem)
 {
@@ -403,7 +508,7 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
         S.cnt[k] = 0u;
         S.fs[k] = 0u;
     }
-    const bool plane = from_plane(im, PK_BLOCKH);
+    constexpr bool plane = PLANE;
     const bool is_log = plane && (im.flags & IF_PLANE_LOG) != 0;
     const bool ldr = P.ldr != 0;
     const float delta = P.delta, scale = (float)B * 1048576.0f;
@@ -411,15 +516,23 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
     const uint32_t magic = P.s_magic;
     const bool group_in_block = magic != 0u && s % G == 0;  // a G-pixel group never straddles blocks
     cta_sync();
-    consume_tile<IN_DT>(im, t, plane, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+    consume_tile<IN_DT, PLANE>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
         const int blk0 = group_in_block ? (int)__umulhi((uint32_t)(c - t.c0), magic) : 0;
+        float tq[G] = {};
         int cur = -1;
         uint32_t rc = 0u, rf = 0u;
 #pragma unroll
         for (int k = 0; k < G; ++k) {
             if (k < n) {
-                const float u = ldr ? fminf(fmaxf(Lv[k], 0.0f), 1.0f) : log_u(Lv[k], is_log, delta, d.lmin, d.inv_range);
-                const int x = min(max(__float2int_rn(fmaf(u, scale, -524288.0f)), 0), xmax);
+                int x;
+                if (ldr) {
+                    x = min(max(__float2int_rn(fmaf(fminf(fmaxf(Lv[k], 0.0f), 1.0f), scale, -524288.0f)), 0), xmax);
+                } else {
+                    // t - 1/2 from 2^-24 to 2^-20 units, rounded
+                    const uint32_t q = coord_of<kLocTS>(Lv[k], is_log, delta, d, B);
+                    tq[k] = __uint_as_float(q);
+                    x = min(max(((int)q - (1 << (kLocTS - 1)) + 8) >> (kLocTS - 20), 0), xmax);
+                }
                 int blk = blk0;
                 if (!group_in_block) {
                     const uint32_t off = (uint32_t)(c + k - t.c0);
@@ -445,6 +558,8 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
             atomicAdd(&S.cnt[cur], rc);
             atomicAdd(&S.fs[cur], rf);
         }
+        // the apply pass reads the coordinate instead of the logarithm
+        if (is_log) GroupIO<IN_DT>::store_plane(im, r, c, n, vec, tq);
     });
     cta_sync();
     unsigned long long* H = reinterpret_cast<unsigned long long*>(P.ws + im.ws_hist);
@@ -504,7 +619,7 @@ __device__ void tile_cdf(const DcBatch<CAP>& P, const DcImage& im, int I, const 
 // (F at the start of bin j, F(j+1) - F(j)) pairs, so each of the four block curves
 // costs one 64-bit shared load and one FMA.  When block_s is a power of two and a
 // multiple of 2G, the bilinear column pair and weight step are fixed per group.
-template <int IN_DT, int CAP>
+template <int IN_DT, bool PLANE, int CAP>
 __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const TileRect& t, int I,
                                  const Beta& be, const Derived& d, unsigned char* smem)
 {
@@ -526,13 +641,14 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
         const float e0 = ld_cg_f(e), e1 = ld_cg_f(e + 1);
         S.tab[slot * SB + j] = make_float2(e0, e1 - e0);
     }
-    const bool plane = from_plane(im, PK_APPLY_L);
+    constexpr bool plane = PLANE;
     const bool is_log = plane && (im.flags & IF_PLANE_LOG) != 0;
     const bool ldr = P.ldr != 0;
     const float delta = P.delta, Bf = (float)B, inv_s = 1.0f / (float)s, alpha = P.alpha;
     const bool group_cols = (s & (s - 1)) == 0 && s % (2 * G) == 0;
     cta_sync();
-    consume_tile<IN_DT>(im, t, plane, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+    const float inv_B = 1.0f / Bf;
+    consume_tile<IN_DT, PLANE>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
         const float fy = fmaf((float)r + 0.5f, inv_s, -0.5f);
         const float fly = floorf(fy);
         const float wy = fy - fly;
@@ -544,7 +660,24 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
         const float wx0 = fx0 - flx0;
 #pragma unroll
         for (int k = 0; k < G; ++k) {
-            const float u = ldr ? fminf(fmaxf(Lv[k], 0.0f), 1.0f) : log_u(Lv[k], is_log, delta, d.lmin, d.inv_range);
+            // bin j and position tt in it: from u = L (8-bit input) or exactly from
+            // the fixed-point log (HDR)
+            int j;
+            float tt, u;
+            if (ldr) {
+                u = fminf(fmaxf(Lv[k], 0.0f), 1.0f);
+                const float Bu = Bf * u;
+                j = min((int)Bu, B - 1);
+                tt = Bu - (float)j;
+            } else {
+                // bin coordinate: kept in the plane by the histogram pass, or
+                // computed from L recomputed from RGB
+                const uint32_t q = is_log ? __float_as_uint(Lv[k]) : coord_of<kLocTS>(Lv[k], false, delta, d, B);
+                const uint32_t jq = min(q >> kLocTS, (uint32_t)(B - 1));
+                j = (int)jq;
+                tt = (float)(q - (jq << kLocTS)) * (1.0f / (float)(1u << kLocTS));
+                u = (float)q * (inv_B / (float)(1u << kLocTS));
+            }
             int sc0;
             float wx;
             if (group_cols) {
@@ -556,9 +689,6 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
                 wx = fx - flx;
                 sc0 = (int)flx - (J0 - 1);
             }
-            const float Bu = Bf * u;
-            const int j = min((int)Bu, B - 1);
-            const float tt = Bu - (float)j;
             const float2 a = row0[sc0 * SB + j], b = row0[(sc0 + 1) * SB + j];
             const float2 cc = row1[sc0 * SB + j], dd = row1[(sc0 + 1) * SB + j];
             const float f00 = fmaf(tt, a.y, a.x), f01 = fmaf(tt, b.y, b.x);
@@ -577,7 +707,7 @@ static_assert(kThreads == 256, "per-bin work uses one consumer thread per histog
 
 template <int KIND>
 struct PassSmem {
-    static constexpr size_t value = KIND == PK_STATS || KIND == PK_LOGHIST ? sizeof(SmemStats)
+    static constexpr size_t value = KIND == PK_STATS || KIND == PK_STATS_LOG || KIND == PK_LOGHIST ? sizeof(SmemStats)
                                     : KIND == PK_APPLY_G                   ? sizeof(SmemApplyG) + sizeof(SmemStats)
                                     : KIND == PK_BLOCKH                    ? sizeof(SmemBlockH)
                                     : KIND == PK_CDF                       ? sizeof(SmemCdf)
@@ -592,7 +722,7 @@ struct PassSmem {
 // One pass over all tiles of pass `ph` (kind KIND) of every image in the batch.
 // CTAs take tiles round-robin (last-first when the pass re-reads what the previous
 // pass just read, so the most recently touched data is still in L2).
-template <int IN_DT, int OPK, int KIND, int CAP>
+template <int IN_DT, int OPK, int KIND, int CAP, bool PL>
 __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __grid_constant__ DcBatch<CAP> P, int ph)
 {
     __shared__ __align__(16) unsigned char smem[PassSmem<KIND>::value];
@@ -602,7 +732,9 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
     const bool rev = P.reverse[ph] != 0;
     // derived values of the stats pass are needed by every later pass that
     // normalises log luminance or applies the sigmoid
-    const bool need_d = KIND != PK_STATS && KIND != PK_CDF && KIND != PK_DECOLOR && P.phase_kind[0] == PK_STATS;
+    const bool fixed_log = P.phase_kind[0] == PK_STATS_LOG;
+    const bool need_d = KIND != PK_STATS && KIND != PK_STATS_LOG && KIND != PK_CDF && KIND != PK_DECOLOR &&
+                        (P.phase_kind[0] == PK_STATS || fixed_log);
     // programmatic dependent launch: let the next pass start launching its CTAs as
     // ours retire, and wait here until the previous pass has completed and its
     // memory is visible
@@ -621,7 +753,7 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
         const DcImage& im = P.img[img];
         DcImgCtrl* ic = img_ctrl(P.ctrl, img);
         if (need_d && img != cached) {
-            if (threadIdx.x == 0) s_d = derive(ic, (long long)im.prow * (long long)im.pcol);
+            if (threadIdx.x == 0) s_d = derive(ic, (long long)im.prow * (long long)im.pcol, fixed_log);
             cta_sync();
             cached = img;
         }
@@ -630,22 +762,24 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
         const TileRect tr = tile_rect<OPK>(P, im, KIND, lt, I);
         if constexpr (KIND == PK_DECOLOR) {
             constexpr int G = InT<IN_DT>::G;
-            consume_tile<IN_DT>(im, tr, false, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) {
+            consume_tile<IN_DT, false>(im, tr, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) {
                 GroupIO<IN_DT>::store(im, r, c, n, vec, Lv);
             });
         } else if constexpr (KIND == PK_STATS) {
-            tile_stats<IN_DT>(P, im, ic, tr, be, smem);
+            tile_stats<IN_DT, false>(P, im, ic, tr, be, smem);
+        } else if constexpr (KIND == PK_STATS_LOG) {
+            tile_stats<IN_DT, true>(P, im, ic, tr, be, smem);
         } else if constexpr (KIND == PK_LOGHIST) {
-            tile_loghist<IN_DT>(P, im, ic, tr, be, s_d, smem);
+            tile_loghist<IN_DT, PL>(P, im, ic, tr, be, s_d, smem);
         } else if constexpr (KIND == PK_APPLY_G) {
             if (P.stats && lt == 0) write_stats(P, im, ic, img, s_d);
-            tile_apply_global<IN_DT>(P, im, ic, tr, be, s_d, smem);
+            tile_apply_global<IN_DT, PL>(P, im, ic, tr, be, s_d, smem);
         } else if constexpr (KIND == PK_BLOCKH) {
-            tile_blockh<IN_DT>(P, im, tr, I, be, s_d, smem);
+            tile_blockh<IN_DT, PL>(P, im, tr, I, be, s_d, smem);
         } else if constexpr (KIND == PK_CDF) {
             tile_cdf(P, im, I, tr, smem);
         } else {
-            tile_apply_local<IN_DT>(P, im, tr, I, be, s_d, smem);
+            tile_apply_local<IN_DT, PL>(P, im, tr, I, be, s_d, smem);
         }
         cta_sync();  // shared memory is reused by the next tile
         if (P.profile && threadIdx.x == 0) {
@@ -656,7 +790,7 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
     if (P.profile && threadIdx.x == 0) atomicMax(&P.ctrl->prof[PROF_KEND], globaltimer_ns());
 }
 
-template <int IN_DT, int OPK, int KIND, int CAP>
+template <int IN_DT, int OPK, int KIND, int CAP, bool PL>
 int launch_one(const void* batch, int ph, LaunchShape ls, void* stream)
 {
     const DcBatch<CAP>& b = *reinterpret_cast<const DcBatch<CAP>*>(batch);
@@ -670,33 +804,39 @@ int launch_one(const void* batch, int ph, LaunchShape ls, void* stream)
     attr[0].val.programmaticStreamSerializationAllowed = ph > 0 ? 1 : 0;  // the first pass follows the memset
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (cudaLaunchKernelEx(&cfg, pass_kernel<IN_DT, OPK, KIND, CAP>, b, ph) != cudaSuccess) return DC_ERR_CUDA;
+    if (cudaLaunchKernelEx(&cfg, pass_kernel<IN_DT, OPK, KIND, CAP, PL>, b, ph) != cudaSuccess) return DC_ERR_CUDA;
     return cudaGetLastError() == cudaSuccess ? DC_OK : DC_ERR_CUDA;
 }
 
-template <int IN_DT, int OPK, int KIND, int CAP>
+template <int IN_DT, int OPK, int KIND, int CAP, bool PL>
 int occupancy_one()
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<IN_DT, OPK, KIND, CAP>, kThreads, 0) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<IN_DT, OPK, KIND, CAP, PL>, kThreads, 0) !=
         cudaSuccess)
         return 0;
     return nb;
 }
 
-// Valid (operation, pass kind) pairs, expanded for every batch capacity.
-#define DC_FOR_EACH_PASS(X)                                                                                     \
-    X(OPK_DECOLOR, PK_DECOLOR) X(OPK_GLOBAL, PK_STATS) X(OPK_GLOBAL, PK_LOGHIST) X(OPK_GLOBAL, PK_APPLY_G)      \
-        X(OPK_LOCAL, PK_STATS) X(OPK_LOCAL, PK_BLOCKH) X(OPK_LOCAL, PK_CDF) X(OPK_LOCAL, PK_APPLY_L)
+// Valid (operation, pass kind, reads a plane) triples, expanded for every batch
+// capacity.  Only f16/f32 input keeps a plane.
+#define DC_FOR_EACH_PASS(X)                                                                                  \
+    X(OPK_DECOLOR, PK_DECOLOR, false) X(OPK_GLOBAL, PK_STATS, false) X(OPK_GLOBAL, PK_STATS_LOG, false)      \
+        X(OPK_GLOBAL, PK_LOGHIST, false) X(OPK_GLOBAL, PK_LOGHIST, true) X(OPK_GLOBAL, PK_APPLY_G, false)    \
+        X(OPK_GLOBAL, PK_APPLY_G, true) X(OPK_LOCAL, PK_STATS_LOG, false) X(OPK_LOCAL, PK_BLOCKH, false)     \
+        X(OPK_LOCAL, PK_BLOCKH, true) X(OPK_LOCAL, PK_CDF, false) X(OPK_LOCAL, PK_APPLY_L, false)            \
+        X(OPK_LOCAL, PK_APPLY_L, true)
 
 template <int IN_DT>
-int launch_dispatch(const void* batch, int cap, int opk, int kind, int ph, LaunchShape ls, void* stream)
+int launch_dispatch(const void* batch, int cap, int opk, int kind, int ph, bool pl, LaunchShape ls, void* stream)
 {
-#define DC_CASE(OP, K)                                                                      \
-    if (opk == OP && kind == K) {                                                          \
-        if (cap == kCapSmall) return launch_one<IN_DT, OP, K, kCapSmall>(batch, ph, ls, stream); \
-        if (cap == kCapMid) return launch_one<IN_DT, OP, K, kCapMid>(batch, ph, ls, stream);     \
-        if (cap == kCapLarge) return launch_one<IN_DT, OP, K, kCapLarge>(batch, ph, ls, stream); \
+#define DC_CASE(OP, K, PL)                                                                               \
+    if constexpr (!PL || IN_DT != DC_U8) {                                                              \
+        if (opk == OP && kind == K && pl == PL) {                                                       \
+            if (cap == kCapSmall) return launch_one<IN_DT, OP, K, kCapSmall, PL>(batch, ph, ls, stream); \
+            if (cap == kCapMid) return launch_one<IN_DT, OP, K, kCapMid, PL>(batch, ph, ls, stream);     \
+            if (cap == kCapLarge) return launch_one<IN_DT, OP, K, kCapLarge, PL>(batch, ph, ls, stream); \
+        }                                                                                               \
     }
     DC_FOR_EACH_PASS(DC_CASE)
 #undef DC_CASE
@@ -704,13 +844,15 @@ int launch_dispatch(const void* batch, int cap, int opk, int kind, int ph, Launc
 }
 
 template <int IN_DT>
-int occupancy_dispatch(int cap, int opk, int kind)
+int occupancy_dispatch(int cap, int opk, int kind, bool pl)
 {
-#define DC_CASE(OP, K)                                                          \
-    if (opk == OP && kind == K) {                                              \
-        if (cap == kCapSmall) return occupancy_one<IN_DT, OP, K, kCapSmall>(); \
-        if (cap == kCapMid) return occupancy_one<IN_DT, OP, K, kCapMid>();     \
-        if (cap == kCapLarge) return occupancy_one<IN_DT, OP, K, kCapLarge>(); \
+#define DC_CASE(OP, K, PL)                                                                 \
+    if constexpr (!PL || IN_DT != DC_U8) {                                                \
+        if (opk == OP && kind == K && pl == PL) {                                         \
+            if (cap == kCapSmall) return occupancy_one<IN_DT, OP, K, kCapSmall, PL>(); \
+            if (cap == kCapMid) return occupancy_one<IN_DT, OP, K, kCapMid, PL>();     \
+            if (cap == kCapLarge) return occupancy_one<IN_DT, OP, K, kCapLarge, PL>(); \
+        }                                                                                 \
     }
     DC_FOR_EACH_PASS(DC_CASE)
 #undef DC_CASE

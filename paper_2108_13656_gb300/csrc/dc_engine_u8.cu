@@ -3,14 +3,14 @@
 
 namespace dc {
 
-int launch_engine_u8(const void* batch, int cap, int opk, int kind, int ph, LaunchShape ls, void* stream)
+int launch_engine_u8(const void* batch, int cap, int opk, int kind, int ph, bool pl, LaunchShape ls, void* stream)
 {
-    return launch_dispatch<DC_U8>(batch, cap, opk, kind, ph, ls, stream);
+    return launch_dispatch<DC_U8>(batch, cap, opk, kind, ph, pl, ls, stream);
 }
 
-int occupancy_u8(int cap, int opk, int kind)
+int occupancy_u8(int cap, int opk, int kind, bool pl)
 {
-    return occupancy_dispatch<DC_U8>(cap, opk, kind);
+    return occupancy_dispatch<DC_U8>(cap, opk, kind, pl);
 }
 
 }  // namespace dc

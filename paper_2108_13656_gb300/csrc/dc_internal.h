@@ -17,7 +17,7 @@ constexpr int kMaxPhases = 4;
 constexpr int kCapSmall = 1;     // params capacity for single-image calls
 constexpr int kCapMid = 16;
 constexpr int kCapLarge = 256;   // largest batch per launch (kernel parameter space)
-constexpr int kLogFixedShift = 20;  // logsum unit is 2^-20
+constexpr int kLogFixedShift = 24;  // logsum and fixed-point log unit is 2^-24
 
 // phase kinds
 enum PhaseKind : int32_t {
@@ -28,13 +28,14 @@ enum PhaseKind : int32_t {
     PK_BLOCKH = 4,    // local: block histograms
     PK_CDF = 5,       // local: window sums -> per-block cumulative tables
     PK_APPLY_L = 6,   // local: bilinear blend of block curves -> out
+    PK_STATS_LOG = 7, // HDR histogram forms: exact fixed-point log statistics (+ plane)
 };
 
 // per-image flags
 enum : uint32_t {
     IF_VEC = 1u,      // 16-byte aligned pointers and strides: vector path
     IF_LPLANE = 2u,   // out is an f32 plane that holds L between phases
-    IF_PLANE_LOG = 4u,  // ... and it holds ln(L + delta) instead of L
+    IF_PLANE_LOG = 4u,  // ... and it holds round(ln(L + delta) 2^24) as int32 bits instead of L
 };
 
 struct DcImage {                 // 80 bytes
@@ -52,15 +53,16 @@ struct DcImage {                 // 80 bytes
     int64_t ws_hist;             // byte offsets into the workspace (local)
 };
 
-// Per-image control block, cleared by the host before every launch.  Tiles publish
-// their completion by incrementing done[phase] with release semantics; a tile of the
-// next phase waits (acquire) until the count reaches the phase's tile count and then
-// derives what it needs (mu, lmin, lmax, cumulative tables) from the integer
-// accumulators itself, so no tile has to finalise a phase.
+// Per-image control block, cleared (memset) before the first pass of a call.  The
+// statistics pass accumulates into it with integer atomics; a later pass, which
+// starts only after the previous one has completed, derives what it needs (mu,
+// lmin, lmax) from the integer accumulators itself, so no tile has to finalise a
+// pass.  done[] is not used by the pass kernels.
 struct DcImgCtrl {
     uint32_t done[kMaxPhases];
     unsigned long long logsum;   // two's complement, units of 2^-20
-    uint32_t lmax_ord;           // ordered-uint encoding of max ln(L+delta)
+    uint32_t lmax_ord;           // ordered encoding of max ln(L+delta): of the float
+                                 // (PK_STATS) or of the 2^-24 fixed-point value (PK_STATS_LOG)
     uint32_t lmin_nord;          // bitwise NOT of the ordered encoding of the min
     uint32_t pad[2];
     // profiling (only when enabled): per phase, NOT of the earliest tile start and
@@ -70,12 +72,14 @@ struct DcImgCtrl {
     uint32_t hist[256];
 };
 
-// Profile counters of one launch (only when enabled), summed over CTAs, ns.
+// Profile counters of one call (only when enabled), ns.  The pass kernels fill
+// PROF_TILES, PROF_KSTART_NOT and PROF_KEND; the wait slots stay zero (no pass
+// kernel waits on another CTA) and are kept for the layout of the read-back.
 enum ProfSlot {
-    PROF_DEP_WAIT = 0,    // producer: waiting for earlier phases
-    PROF_EMPTY_WAIT = 1,  // producer: waiting for a free stage
-    PROF_TILE_WAIT = 2,   // consumers: waiting for the next tile message
-    PROF_DATA_WAIT = 3,   // consumers: waiting for stage data
+    PROF_DEP_WAIT = 0,
+    PROF_EMPTY_WAIT = 1,
+    PROF_TILE_WAIT = 2,
+    PROF_DATA_WAIT = 3,
     PROF_TILES = 4,       // tiles processed
     PROF_KSTART_NOT = 5,  // NOT of the earliest CTA start
     PROF_KEND = 6,        // latest CTA end
@@ -84,7 +88,7 @@ enum ProfSlot {
 
 // Per-launch control block, cleared by the host before the launch.
 struct DcCtrl {
-    uint32_t next_tile;
+    uint32_t next_tile;          // unused by the pass kernels (static schedule)
     uint32_t pad[15];
     unsigned long long prof[PROF_SLOTS];
     uint32_t pad2[32];
@@ -134,12 +138,13 @@ struct LaunchShape {
     int grid;
 };
 
-// opk: 0 decolorize, 1 global, 2 local; kind: PhaseKind; ph: index of the pass
-int launch_engine_u8(const void* batch, int cap, int opk, int kind, int ph, LaunchShape ls, void* stream);
-int launch_engine_f16(const void* batch, int cap, int opk, int kind, int ph, LaunchShape ls, void* stream);
-int launch_engine_f32(const void* batch, int cap, int opk, int kind, int ph, LaunchShape ls, void* stream);
-int occupancy_u8(int cap, int opk, int kind);
-int occupancy_f16(int cap, int opk, int kind);
-int occupancy_f32(int cap, int opk, int kind);
+// opk: 0 decolorize, 1 global, 2 local; kind: PhaseKind; ph: index of the pass;
+// pl: the pass reads the plane every image of the launch keeps (f16/f32 input only)
+int launch_engine_u8(const void* batch, int cap, int opk, int kind, int ph, bool pl, LaunchShape ls, void* stream);
+int launch_engine_f16(const void* batch, int cap, int opk, int kind, int ph, bool pl, LaunchShape ls, void* stream);
+int launch_engine_f32(const void* batch, int cap, int opk, int kind, int ph, bool pl, LaunchShape ls, void* stream);
+int occupancy_u8(int cap, int opk, int kind, bool pl);
+int occupancy_f16(int cap, int opk, int kind, bool pl);
+int occupancy_f32(int cap, int opk, int kind, bool pl);
 
 }  // namespace dc

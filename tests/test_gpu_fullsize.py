@@ -1,0 +1,89 @@
+"""Parity at the full workload sizes, in the launch configuration bench.py times.
+
+- 512 x 512 8-bit S-LDR (seed 0), decolorize only: every pixel against the oracle.
+- 3840 x 2160 8-bit S-LDR (seed 1) and FP32 S-HDR over 5 decades (seed 2), both
+  tone-mapping operators: every pixel against the oracle.
+- 7680 x 4320 S-HDR over 6 decades (mu = 0, sigma = 2.76, seed 4), local operator, FP16 storage and FP32
+  storage with FP32 arithmetic: every pixel against the oracle run on the stored
+  samples, and the error against the FP32 original reported (the precision study;
+  run with -s to see the numbers).
+"""
+import numpy as np
+import pytest
+
+from _cmp import TOL_F32, check_f32, check_u8
+from _dev import to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dc():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    import paper_2108_13656_gb300 as m
+    m.load()
+    return m
+
+
+def _run(dc, op, img, out_dtype, **kw):
+    """One call through the C ABI with the default (bench) launch configuration."""
+    import torch
+    x = to_dev(img)
+    y = torch.empty(img.shape[:2], dtype=out_dtype, device="cuda")
+    ws = dc.Workspace()
+    dc.PreparedCall(op, x, y, workspace=ws, **kw)()
+    torch.cuda.synchronize()
+    assert dc.query_status(ws) == 0
+    return y.cpu().numpy()
+
+
+def test_config_512_decolorize(dc, oracle_mod):
+    import torch
+    from paper_2108_13656_gb300 import synth
+    img = synth.s_ldr(512, 512, seed=0)
+    y = _run(dc, "decolorize", img, torch.uint8)
+    check_u8(y, oracle_mod.decolorize(img), "512x512 decolorize")
+
+
+@pytest.mark.parametrize("variant", ["u8", "f32"])
+@pytest.mark.parametrize("op", ["global", "local"])
+def test_config_4k(dc, oracle_mod, variant, op):
+    import torch
+    from paper_2108_13656_gb300 import synth
+    if variant == "u8":
+        img = synth.s_ldr(3840, 2160, seed=1)
+    else:
+        img = synth.s_hdr(3840, 2160, seed=2, decades=5.0, sigma=2.5)
+    L64 = oracle_mod.decolorize(img)
+    ldr = variant == "u8"
+    if op == "global":
+        y64, _ = oracle_mod.tonemap_global_plane(L64, ldr=ldr)
+    else:
+        y64 = oracle_mod.tonemap_local_plane(L64, ldr=ldr)
+    if variant == "u8":
+        y = _run(dc, op, img, torch.uint8)
+        check_u8(y, y64, "4K u8 %s" % op)
+    else:
+        y = _run(dc, op, img, torch.float32)
+        err = check_f32(y, y64, what="4K f32 %s" % op)
+        print("4K f32 %s: max |err| %.3g" % (op, err))
+
+
+@pytest.mark.parametrize("storage", [np.float16, np.float32])
+def test_config_8k_local_precision(dc, oracle_mod, storage):
+    import torch
+    from paper_2108_13656_gb300 import synth
+    img32 = synth.s_hdr(7680, 4320, seed=4, decades=6.0, sigma=2.76)
+    img = img32.astype(storage)
+    y = _run(dc, "local", img, torch.float32).astype(np.float64)
+    y64 = oracle_mod.tonemap_local(img)  # oracle on the stored samples
+    err = np.abs(y - y64)
+    assert err.max() <= TOL_F32, err.max()
+    if storage == np.float16:
+        y64_orig = oracle_mod.tonemap_local(img32)  # effect of FP16 storage itself
+        e2 = np.abs(y - y64_orig)
+        print("8K local f16 storage: vs oracle(stored) max %.3g mean %.3g; vs oracle(f32 original) max %.3g mean %.3g"
+              % (err.max(), err.mean(), e2.max(), e2.mean()))
+    else:
+        print("8K local f32 storage: vs oracle max %.3g mean %.3g" % (err.max(), err.mean()))
