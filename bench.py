@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--busy-s", type=float, default=0.3, help="device-busy period while clock sampling starts")
+    ap.add_argument("--no-extras", action="store_true", help="skip the ragged-batch and serving measurements")
+    ap.add_argument("--ragged-images", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-rate", type=float, default=2000.0)
     return ap.parse_args()
 
 
@@ -234,6 +238,95 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------- ragged batch ----
+def _event_ms(fn, reps, flush=None):
+    import torch
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.fill_(0)
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        fn()
+        e.record()
+        torch.cuda.synchronize()
+        ts.append(s.elapsed_time(e))
+    return float(np.median(ts))
+
+
+def ragged_batch(dev, n_images: int, peak: float) -> dict:
+    """Ragged batch of 8-bit images (sizes U{320x240 ... 4096x3072}, seed 3), decolorize
+    + global sigmoid: one batched call replayed from a CUDA graph (launch shape from
+    the autotuner) against the same batch as one eager call and as one call per image."""
+    import torch
+    import paper_2108_13656_gb300 as dc
+    from paper_2108_13656_gb300 import synth
+    from paper_2108_13656_gb300.autotune import Autotuner, TuneCache
+    from paper_2108_13656_gb300.batch import GraphCall, plain_calls
+    sizes, shifts = synth.ragged_batch_spec(n_images, 3)
+    bases = {sz: torch.from_numpy(synth.ragged_base(sz)).to(dev) for sz in sorted(set(sizes))}
+    xs = [torch.roll(bases[sz], shifts=sh, dims=(0, 1)).contiguous() for sz, sh in zip(sizes, shifts)]
+    del bases
+    ys = [torch.empty(x.shape[:2], dtype=torch.uint8, device=dev) for x in xs]
+    px = sum(w * h for w, h in sizes)
+    orig = dc.get_tuning(dc.DC_OP_GLOBAL, dc.DC_U8)
+    try:
+        tune_path = os.path.join(os.path.expanduser("~"), ".cache", "decolor_gb300", "bench_tune.json")
+        choice, timings = Autotuner(TuneCache(tune_path), reps=3).tune("global", xs, ys)
+        g = GraphCall("global", xs, ys)
+        graph_ms = _event_ms(g.replay, 7)
+        eager = dc.PreparedCall("global", xs, ys, workspace=dc.Workspace(device=dev))
+        eager_ms = _event_ms(eager, 7)
+        eager_launches = dc.last_launch_count()
+        calls = plain_calls("global", xs, ys)
+
+        def run_plain():
+            for c in calls:
+                c()
+        plain_ms = _event_ms(run_plain, 5)
+        plain_launches = sum(1 for _ in calls) * 2
+        same = True
+        ref = [torch.empty_like(y) for y in ys[:16]]
+        for c, y in zip(plain_calls("global", xs[:16], ref), ref):
+            c()
+        g.replay()
+        torch.cuda.synchronize()
+        same = all(torch.equal(a, b) for a, b in zip(ys[:16], ref))
+    finally:
+        dc.set_tuning(dc.DC_OP_GLOBAL, dc.DC_U8, *orig)
+    alg = 4 * px
+    return {"images": n_images, "mpix": px / 1e6, "input_gb": 3 * px / 1e9,
+            "graph": {"ms": graph_ms, "gpix_s": px / graph_ms / 1e6, "launches": g.launches,
+                      "GBps": alg / graph_ms / 1e6, "frac_of_measured_hbm": alg / graph_ms / 1e6 / peak},
+            "batched_eager": {"ms": eager_ms, "gpix_s": px / eager_ms / 1e6, "launches": eager_launches},
+            "plain_per_image": {"ms": plain_ms, "gpix_s": px / plain_ms / 1e6, "launches": plain_launches},
+            "speedup_graph_vs_plain": plain_ms / graph_ms,
+            "autotune": {"choice_tile_cols_ctas_per_sm": list(choice), "us": timings},
+            "batch_equals_per_image_first16": same,
+            "l2": "inputs (%.2f GB) larger than L2" % (3 * px / 1e9)}
+
+
+# ------------------------------------------------------------------ serving ----
+def serving(dev, n_requests: int, rate: float) -> dict:
+    """The serving trace (Poisson arrivals, sizes 720p..8K, 70% u8 / 30% f16, half
+    global, half local, 16 GB budget) through the continuous-batching loop and through
+    serial single-image calls."""
+    from paper_2108_13656_gb300 import serve
+    trace = serve.make_trace(n_requests, rate, seed=5)
+    pool = serve.HostPool(trace)
+    warm = serve.make_trace(min(200, n_requests), rate, seed=6)
+    serve.serve_batched(warm, pool, device=dev)
+    serve.serve_serial(warm, pool, device=dev)
+    b = serve.serve_batched(trace, pool, budget_bytes=16 << 30, device=dev).summary()
+    s = serve.serve_serial(trace, pool, device=dev).summary()
+    return {"requests": n_requests, "rate_per_s": rate, "budget_gb": 16,
+            "offered_gpix_s": sum(r.size[0] * r.size[1] for r in trace) / (trace[-1].t_arrive - trace[0].t_arrive) / 1e9,
+            "batched": b, "serial_plain": s,
+            "note": "latency = host-observed completion (event after the device-to-host copy) minus arrival; "
+                    "inputs start in pinned host memory, outputs end there"}
+
+
 # --------------------------------------------------------------------- native ----
 def run_native(args):
     import torch
@@ -365,6 +458,10 @@ def run_native(args):
     }
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(imgs)
+    if not args.no_extras:
+        line["ragged_batch"] = ragged_batch(dev, args.ragged_images, peak)
+        torch.cuda.empty_cache()
+        line["serving"] = serving(dev, args.serve_requests, args.serve_rate)
     print(json.dumps(line))
     return 0
 

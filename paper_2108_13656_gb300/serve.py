@@ -1,0 +1,257 @@
+"""Serving loop: decolorize + tone-map requests with continuous batching.
+
+Requests (an image in pinned host memory, an operation, a sample type) arrive on a
+trace.  The loop admits every request that has arrived as soon as the device-memory
+budget has room for its input, output and tables, FIFO; admitted requests are
+launched in batches - one C-ABI call per operation for everything admitted since
+the last launch, on the least loaded of a few CUDA streams, each with its own
+workspace - with the host->device copies, the call and the device->host copies
+stream-ordered.  So requests that arrive while others run are admitted as memory
+frees up and their copies and kernels overlap with the work already on the device.
+A request completes when the host sees the event recorded after its batch's copies;
+its latency is completion minus arrival.  `serve_serial` runs the same trace one
+request at a time with a single-image call, the per-image baseline.
+
+Every step on the device is a library call or a copy; the Python here only
+schedules.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import time
+
+import numpy as np
+
+from . import _abi, synth
+
+SERVE_SIZES = ((1280, 720), (1920, 1080), (3840, 2160), (7680, 4320))
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    t_arrive: float  # seconds after the start of the trace
+    op: str          # "global" or "local"
+    dtype: str       # "u8" (sRGB, output u8) or "f16" (linear HDR, output f32)
+    size: tuple      # (width, height)
+    variant: int     # which pooled image of that size and type
+
+
+def make_trace(n: int, rate: float, seed: int, sizes=SERVE_SIZES, p_u8: float = 0.7, p_global: float = 0.5,
+               variants: int = 2) -> list[Request]:
+    """n requests with Poisson arrivals of mean `rate` per second (seeded)."""
+    rng = synth.rng_for(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    size_idx = rng.integers(0, len(sizes), n)
+    u8 = rng.random(n) < p_u8
+    glob = rng.random(n) < p_global
+    var = rng.integers(0, variants, n)
+    return [Request(i, float(t[i]), "global" if glob[i] else "local", "u8" if u8[i] else "f16",
+                    tuple(sizes[int(size_idx[i])]), int(var[i])) for i in range(n)]
+
+
+class _OutPool:
+    """Recycled pinned host output buffers per (size, dtype)."""
+
+    def __init__(self):
+        self.free = collections.defaultdict(list)
+
+    def get(self, shape, dtype):
+        import torch
+        lst = self.free[(shape, dtype)]
+        return lst.pop() if lst else torch.empty(shape, dtype=dtype).pin_memory()
+
+    def put(self, t):
+        self.free[(tuple(t.shape), t.dtype)].append(t)
+
+
+class HostPool:
+    """Pinned host images, one per (size, sample type, variant) of a trace: S-LDR for
+    u8, S-HDR (5 decades) stored as binary16 for f16; variants are cyclic shifts.
+    Also the pinned output buffers, `outputs_per_class` per (size, output type)
+    allocated up front (pinning is slow; more are added on demand)."""
+
+    def __init__(self, trace, seed: int = 5, outputs_per_class: int = 4):
+        import torch
+        self.images = {}
+        self.outpool = _OutPool()
+        keys = sorted({(r.size, r.dtype, r.variant) for r in trace})
+        bases = {}
+        for size, dt, var in keys:
+            if (size, dt) not in bases:
+                w, h = size
+                base = synth.s_ldr(w, h, seed) if dt == "u8" else synth.s_hdr(w, h, seed).astype(np.float16)
+                bases[(size, dt)] = base
+            base = bases[(size, dt)]
+            img = synth.shifted(base, (97 * var) % size[1], (389 * var) % size[0]) if var else base
+            self.images[(size, dt, var)] = torch.from_numpy(np.ascontiguousarray(img)).pin_memory()
+        for size, dt in sorted({(r.size, r.dtype) for r in trace}):
+            odt = torch.uint8 if dt == "u8" else torch.float32
+            for _ in range(outputs_per_class):
+                self.outpool.put(torch.empty((size[1], size[0]), dtype=odt).pin_memory())
+
+    def host_input(self, r: Request):
+        return self.images[(r.size, r.dtype, r.variant)]
+
+
+def out_dtype(r: Request):
+    import torch
+    return torch.uint8 if r.dtype == "u8" else torch.float32
+
+
+def request_bytes(r: Request, lp=None) -> int:
+    """Device bytes a request holds while admitted: input, output and its share of the
+    local operator's tables."""
+    w, h = r.size
+    nbytes = w * h * (3 if r.dtype == "u8" else 6) + w * h * (1 if r.dtype == "u8" else 4)
+    if r.op == "local":
+        hb, wb = (h + 31) // 32, (w + 31) // 32
+        nbytes += hb * wb * (32 * 8 + 33 * 4) + 4096
+    return nbytes + 2048
+
+
+@dataclasses.dataclass
+class ServeResult:
+    latency_s: np.ndarray      # per request, in request order
+    makespan_s: float          # first arrival to last completion
+    pixels: int
+    batches: int
+    max_inflight_bytes: int
+    outputs: dict | None       # rid -> host tensor, when kept
+    sizes: list | None = None  # per request (width, height), in request order
+
+    def summary(self) -> dict:
+        lat = self.latency_s * 1e3
+        out = {"requests": int(len(lat)), "p50_ms": float(np.percentile(lat, 50)),
+               "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
+               "gpix_s": self.pixels / self.makespan_s / 1e9, "makespan_s": self.makespan_s,
+               "batches": self.batches, "max_inflight_gb": self.max_inflight_bytes / 1e9}
+        if self.sizes:
+            per = {}
+            for sz in sorted(set(self.sizes)):
+                m = np.array([q == sz for q in self.sizes])
+                per["%dx%d" % sz] = {"p50_ms": float(np.percentile(lat[m], 50)),
+                                     "p99_ms": float(np.percentile(lat[m], 99))}
+            out["by_size"] = per
+        return out
+
+
+def _wait_until(t_abs: float):
+    while True:
+        d = t_abs - time.perf_counter()
+        if d <= 0:
+            return
+        if d > 2e-4:
+            time.sleep(d - 1e-4)
+
+
+def serve_batched(trace, pool: HostPool, budget_bytes: int = 16 << 30, n_streams: int = 4, max_batch: int = 64,
+                  keep_outputs: bool = False, device=None) -> ServeResult:
+    """Continuous batching over the trace (arrival times are honoured in real time)."""
+    import torch
+    dev = torch.device(device or "cuda")
+    streams = [torch.cuda.Stream(device=dev) for _ in range(n_streams)]
+    wss = [_abi.Workspace(device=dev) for _ in range(n_streams)]
+    inflight_per_stream = [0] * n_streams
+    outpool = pool.outpool
+    pending = collections.deque(sorted(trace, key=lambda r: r.t_arrive))
+    waiting = collections.deque()
+    inflight = []  # (event, stream index, [(req, x, y, host_out)], bytes)
+    lat = {}
+    outputs = {} if keep_outputs else None
+    used = peak = 0
+    batches = 0
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    while pending or waiting or inflight:
+        now = time.perf_counter() - t0
+        while pending and pending[0].t_arrive <= now:
+            waiting.append(pending.popleft())
+        # retire finished batches
+        still = []
+        for ev, si, items, nbytes in inflight:
+            if ev.query():
+                t_done = time.perf_counter() - t0
+                for r, x, y, ho in items:
+                    lat[r.rid] = t_done - r.t_arrive
+                    if keep_outputs:
+                        outputs[r.rid] = ho.clone()
+                    outpool.put(ho)
+                used -= nbytes
+                inflight_per_stream[si] -= 1
+            else:
+                still.append((ev, si, items, nbytes))
+        inflight = still
+        # admit what fits, FIFO, and launch it as one batch per operation
+        admitted = []
+        while waiting and len(admitted) < max_batch:
+            need = request_bytes(waiting[0])
+            if used + need > budget_bytes:
+                break
+            used += need
+            admitted.append((waiting.popleft(), need))
+        peak = max(peak, used)
+        if admitted:
+            si = min(range(n_streams), key=lambda k: inflight_per_stream[k])
+            s = streams[si]
+            with torch.cuda.stream(s):
+                items = []
+                for r, _ in admitted:
+                    hx = pool.host_input(r)
+                    x = torch.empty(hx.shape, dtype=hx.dtype, device=dev)
+                    x.copy_(hx, non_blocking=True)
+                    y = torch.empty(hx.shape[:2], dtype=out_dtype(r), device=dev)
+                    items.append((r, x, y, outpool.get(tuple(hx.shape[:2]), out_dtype(r))))
+                for op in ("global", "local"):
+                    sel = [(x, y) for r, x, y, _ in items if r.op == op]
+                    if sel:
+                        _abi.PreparedCall(op, [a for a, _ in sel], [b for _, b in sel], workspace=wss[si])(s)
+                for r, x, y, ho in items:
+                    ho.copy_(y, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(s)
+            inflight.append((ev, si, items, sum(n for _, n in admitted)))
+            inflight_per_stream[si] += 1
+            batches += 1
+            continue
+        # nothing to launch: wait for the next arrival or completion
+        if pending and not inflight and not waiting:
+            _wait_until(t0 + pending[0].t_arrive)
+        else:
+            time.sleep(2e-5)
+    makespan = max(r.t_arrive + lat[r.rid] for r in trace) - min(r.t_arrive for r in trace)
+    order = sorted(trace, key=lambda r: r.rid)
+    return ServeResult(np.array([lat[r.rid] for r in order]), makespan,
+                       sum(r.size[0] * r.size[1] for r in trace), batches, peak, outputs, [r.size for r in order])
+
+
+def serve_serial(trace, pool: HostPool, keep_outputs: bool = False, device=None) -> ServeResult:
+    """The per-image baseline: each request in arrival order, alone, as a single-image
+    call with its copies, synchronously."""
+    import torch
+    dev = torch.device(device or "cuda")
+    ws = _abi.Workspace(device=dev)
+    outpool = pool.outpool
+    lat = {}
+    outputs = {} if keep_outputs else None
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for r in sorted(trace, key=lambda q: q.t_arrive):
+        _wait_until(t0 + r.t_arrive)
+        hx = pool.host_input(r)
+        x = torch.empty(hx.shape, dtype=hx.dtype, device=dev)
+        x.copy_(hx, non_blocking=True)
+        y = torch.empty(hx.shape[:2], dtype=out_dtype(r), device=dev)
+        _abi.PreparedCall(r.op, x, y, workspace=ws)()
+        ho = outpool.get(tuple(hx.shape[:2]), out_dtype(r))
+        ho.copy_(y, non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+        lat[r.rid] = time.perf_counter() - t0 - r.t_arrive
+        if keep_outputs:
+            outputs[r.rid] = ho.clone()
+        outpool.put(ho)
+    makespan = max(r.t_arrive + lat[r.rid] for r in trace) - min(r.t_arrive for r in trace)
+    order = sorted(trace, key=lambda r: r.rid)
+    return ServeResult(np.array([lat[r.rid] for r in order]), makespan,
+                       sum(r.size[0] * r.size[1] for r in trace), len(trace), 0, outputs, [r.size for r in order])

@@ -8,6 +8,12 @@ here imports either of them.
 
 Recipes
 -------
+Ragged batch (n, seed)
+    Sizes drawn uniformly from RAGGED_SIZE_CHOICES (seeded); one S-LDR base image
+    per distinct size (seed 1000 + the size's index); image i is its base
+    cyclically shifted by a seeded (dy, dx), so that every image of the batch is a
+    distinct buffer with distinct content at the same statistics.
+
 S-LDR(W, H, seed)
     A smooth linear gradient per channel (random endpoints and direction),
     overlaid with 64 axis-aligned patches of uniform colour.  Patch colour is
@@ -34,6 +40,9 @@ __all__ = [
     "s_ldr",
     "s_hdr",
     "ragged_sizes",
+    "ragged_batch_spec",
+    "ragged_base",
+    "shifted",
     "RAGGED_SIZE_CHOICES",
 ]
 
@@ -156,3 +165,23 @@ def ragged_sizes(n: int, seed: int, choices=RAGGED_SIZE_CHOICES) -> list[tuple[i
     rng = rng_for(seed)
     idx = rng.integers(0, len(choices), n)
     return [tuple(choices[int(i)]) for i in idx]
+
+
+def ragged_batch_spec(n: int, seed: int, choices=RAGGED_SIZE_CHOICES):
+    """(sizes, shifts): n (width, height) pairs as ragged_sizes and a seeded cyclic
+    shift (dy, dx) per image; the base image of size index k is s_ldr(W, H, 1000 + k)."""
+    sizes = ragged_sizes(n, seed, choices)
+    rng = rng_for(seed + 1)
+    shifts = [(int(rng.integers(0, h)), int(rng.integers(0, w))) for (w, h) in sizes]
+    return sizes, shifts
+
+
+def ragged_base(size, choices=RAGGED_SIZE_CHOICES) -> np.ndarray:
+    """The S-LDR base image of one size of the ragged batch."""
+    k = [tuple(c) for c in choices].index(tuple(size))
+    return s_ldr(size[0], size[1], 1000 + k)
+
+
+def shifted(img: np.ndarray, dy: int, dx: int) -> np.ndarray:
+    """Cyclic shift of an (H, W, C) image by dy rows and dx columns (np.roll)."""
+    return np.roll(img, (dy, dx), axis=(0, 1))
