@@ -21,6 +21,7 @@ constexpr int64_t kHeaderBytes = 256;
 constexpr int64_t kMaxPixels = int64_t(1) << 28;
 constexpr int kMaxLocalSide = 1 << 16;
 constexpr int kLocMaxBlocksX = 32;
+constexpr int kLocMaxCols = 1024;
 constexpr int kCdfChunk = 16;
 
 std::mutex g_mu;
@@ -28,7 +29,7 @@ std::mutex g_mu;
 dc_tuning g_tune[3][3] = {
     {{256, 1, 0, 0}, {256, 1, 0, 0}, {256, 1, 0, 0}},
     {{256, 1, 0, 0}, {256, 1, 0, 0}, {256, 1, 0, 0}},
-    {{256, 32, 256, 0}, {256, 32, 256, 0}, {256, 32, 256, 0}},
+    {{256, 32, 512, 0}, {256, 32, 512, 0}, {256, 32, 512, 0}},
 };
 constexpr int kAutoCtasPerSm = 4;  // resident CTAs of a pass kernel (launch bounds)
 int g_profile = 0;
@@ -86,12 +87,13 @@ int validate_params(const dc_decolor_params* p, const OpArgs& op)
 
 int gcd_i(int a, int b) { return b == 0 ? a : gcd_i(b, a % b); }
 
-// Local tile width: a multiple of lcm(block_s, 16), at most kLocMaxBlocksX blocks.
+// Local tile width: a multiple of lcm(block_s, 16) (at most 1024 for block_s <= 64),
+// at most kLocMaxBlocksX blocks and 1024 pixels.
 int local_tile_cols(int s, int want)
 {
     const int l = s / gcd_i(s, 16) * 16;
     int m = std::max(1, want / l);
-    while (m > 1 && (l * m) / s > kLocMaxBlocksX) --m;
+    while (m > 1 && ((l * m) / s > kLocMaxBlocksX || l * m > kLocMaxCols)) --m;
     return l * m;
 }
 

@@ -141,19 +141,82 @@ struct Beta {
     float bR, one_m_bR, bk, one_m_bk;
 };
 
+// ------------------------------------------------- paired binary32 (f32x2) ---
+// Blackwell executes add/sub/mul/fma on a pair of binary32 values as one
+// instruction; each lane rounds exactly like the scalar instruction, so a pixel
+// gives the same bits through the paired and the scalar form below.
+struct F2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ F2 f2(float a, float b)
+{
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ F2 f2s(float a) { return f2(a, a); }
+__device__ __forceinline__ void f2split(F2 x, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v)); }
+__device__ __forceinline__ F2 operator+(F2 a, F2 b)
+{
+    F2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ F2 operator-(F2 a, F2 b)
+{
+    F2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ F2 operator*(F2 a, F2 b)
+{
+    F2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+    return d;
+}
+__device__ __forceinline__ F2 f2fma(F2 a, F2 b, F2 c)
+{
+    F2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return d;
+}
+
 // Eq. 1-6 in binary32 for one pixel.  R+G+B = 0 gives 0 (continuous extension).
+// The operation order is that of luminance_x2, lane by lane.
 __device__ __forceinline__ float luminance_f32(float R, float G, float B, const Beta& be)
 {
-    const float S = R + G + B;
-    const float L_WHITE = sqrt_fast(fmaf(R, R, fmaf(G, G, B * B)) * (1.0f / 3.0f));  // Eq. 1
-    const float L_B = B;                                                           // Eq. 2
-    const float L_GR = sqrt_fast(fmaf(be.bR, R * R, be.one_m_bR * (G * G)));        // Eq. 3
+    const float S = (R + G) + B;
+    const float R2 = R * R, G2 = G * G;
+    const float L_WHITE = sqrt_fast(fmaf(B, B, R2 + G2) * (1.0f / 3.0f));  // Eq. 1
+    const float L_B = B;                                                     // Eq. 2
+    const float L_GR = sqrt_fast(fmaf(be.bR, R2, be.one_m_bR * G2));         // Eq. 3
     const float inv = rcp_fast(S);
     const float r = R * inv, b = B * inv;
-    const float L_WARM = fmaf(r, L_GR - L_WHITE, L_WHITE);                          // Eq. 4
-    const float L_COOL = fmaf(b, L_WHITE - L_B, L_B);                               // Eq. 5
-    const float L = sqrt_fast(fmaf(be.bk, L_WARM * L_WARM, be.one_m_bk * (L_COOL * L_COOL)));  // Eq. 6
+    const float L_WARM = fmaf(r, L_GR - L_WHITE, L_WHITE);                    // Eq. 4
+    const float L_COOL = fmaf(b, L_WHITE - L_B, L_B);                         // Eq. 5
+    const float L = sqrt_fast(fmaf(be.bk, L_WARM * L_WARM, (be.one_m_bk * L_COOL) * L_COOL));  // Eq. 6
     return S > 0.0f ? L : 0.0f;
+}
+
+// Eq. 1-6 for two pixels: the additions and products in f32x2, the square roots
+// and the reciprocal per lane.
+__device__ __forceinline__ void luminance_x2(F2 R, F2 G, F2 B, const Beta& be, float& L0, float& L1)
+{
+    const F2 S = (R + G) + B;
+    const F2 R2 = R * R, G2 = G * G;
+    float a0, a1, c0, c1, s0, s1;
+    f2split(f2fma(B, B, R2 + G2) * f2s(1.0f / 3.0f), a0, a1);
+    const F2 L_WHITE = f2(sqrt_fast(a0), sqrt_fast(a1));                      // Eq. 1
+    f2split(f2fma(f2s(be.bR), R2, f2s(be.one_m_bR) * G2), c0, c1);
+    const F2 L_GR = f2(sqrt_fast(c0), sqrt_fast(c1));                         // Eq. 3
+    f2split(S, s0, s1);
+    const F2 inv = f2(rcp_fast(s0), rcp_fast(s1));
+    const F2 r = R * inv, b = B * inv;
+    const F2 L_WARM = f2fma(r, L_GR - L_WHITE, L_WHITE);                      // Eq. 4
+    const F2 L_COOL = f2fma(b, L_WHITE - B, B);                               // Eq. 5 (L_B = B)
+    f2split(f2fma(f2s(be.bk), L_WARM * L_WARM, (f2s(be.one_m_bk) * L_COOL) * L_COOL), a0, a1);
+    L0 = s0 > 0.0f ? sqrt_fast(a0) : 0.0f;                                    // Eq. 6
+    L1 = s1 > 0.0f ? sqrt_fast(a1) : 0.0f;
 }
 
 // Linear samples of arbitrary magnitude: Eq. 1-6 are 1-homogeneous, so a pixel
@@ -202,6 +265,22 @@ __device__ __forceinline__ int ln_q24(float x)
     return (int)((q + (1ll << 15)) >> 16);
 }
 
+// Two linear pixels: negatives (and NaN) to 0, the paired Eq. 1-6, and the scaled
+// path for a pixel whose squares leave the binary32 range.
+__device__ __forceinline__ void luminance_hdr_x2(float R0, float G0, float B0, float R1, float G1, float B1,
+                                                 const Beta& be, float& L0, float& L1)
+{
+    R0 = fmaxf(R0, 0.0f);
+    G0 = fmaxf(G0, 0.0f);
+    B0 = fmaxf(B0, 0.0f);
+    R1 = fmaxf(R1, 0.0f);
+    G1 = fmaxf(G1, 0.0f);
+    B1 = fmaxf(B1, 0.0f);
+    luminance_x2(f2(R0, R1), f2(G0, G1), f2(B0, B1), be, L0, L1);
+    if (!(L0 <= 3.0e38f) || (L0 == 0.0f && R0 + G0 + B0 > 0.0f)) L0 = luminance_rescaled(R0, G0, B0, be);
+    if (!(L1 <= 3.0e38f) || (L1 == 0.0f && R1 + G1 + B1 > 0.0f)) L1 = luminance_rescaled(R1, G1, B1, be);
+}
+
 // 8-bit code of y in [0,1]: floor(255 y + 1/2), clamped.
 __device__ __forceinline__ uint32_t quant_u8(float y)
 {
@@ -210,9 +289,15 @@ __device__ __forceinline__ uint32_t quant_u8(float y)
 }
 
 // u8 sample -> float via the exponent-bias trick (2^23 + v, minus 2^23): exact.
-__device__ __forceinline__ float u8_at(const uint32_t (&w)[12], int idx)
+__device__ __forceinline__ float u8_biased(const uint32_t (&w)[12], int idx)
 {
-    return __uint_as_float(__byte_perm(w[idx >> 2], 0x4B00u, 0x5440u | (uint32_t)(idx & 3))) - 8388608.0f;
+    return __uint_as_float(__byte_perm(w[idx >> 2], 0x4B00u, 0x5440u | (uint32_t)(idx & 3)));
+}
+__device__ __forceinline__ float u8_at(const uint32_t (&w)[12], int idx) { return u8_biased(w, idx) - 8388608.0f; }
+// The same for the samples idx and idx + 3 (one channel of two neighbouring pixels).
+__device__ __forceinline__ F2 u8_pair(const uint32_t (&w)[12], int idx)
+{
+    return f2(u8_biased(w, idx), u8_biased(w, idx + 3)) - f2s(8388608.0f);
 }
 
 // ordered-uint encoding of floats (monotone), for exact atomic min/max
@@ -238,9 +323,11 @@ struct GroupIO {
     {
         if constexpr (IN_DT == DC_U8) {
 #pragma unroll
-            for (int k = 0; k < G; ++k)
-                Lv[k] = luminance_f32(u8_at(w, 3 * k), u8_at(w, 3 * k + 1), u8_at(w, 3 * k + 2), be) *
-                        (1.0f / 255.0f);
+            for (int k = 0; k < G; k += 2) {
+                float L0, L1;
+                luminance_x2(u8_pair(w, 3 * k), u8_pair(w, 3 * k + 1), u8_pair(w, 3 * k + 2), be, L0, L1);
+                f2split(f2(L0, L1) * f2s(1.0f / 255.0f), Lv[k], Lv[k + 1]);
+            }
         } else if constexpr (IN_DT == DC_F16) {
             float f[24];
 #pragma unroll
@@ -252,12 +339,15 @@ struct GroupIO {
                 f[2 * k + 1] = v.y;
             }
 #pragma unroll
-            for (int k = 0; k < G; ++k) Lv[k] = luminance_hdr(f[3 * k], f[3 * k + 1], f[3 * k + 2], be);
+            for (int k = 0; k < G; k += 2)
+                luminance_hdr_x2(f[3 * k], f[3 * k + 1], f[3 * k + 2], f[3 * k + 3], f[3 * k + 4], f[3 * k + 5], be,
+                                 Lv[k], Lv[k + 1]);
         } else {
 #pragma unroll
-            for (int k = 0; k < G; ++k)
-                Lv[k] = luminance_hdr(__uint_as_float(w[3 * k]), __uint_as_float(w[3 * k + 1]),
-                                               __uint_as_float(w[3 * k + 2]), be);
+            for (int k = 0; k < G; k += 2)
+                luminance_hdr_x2(__uint_as_float(w[3 * k]), __uint_as_float(w[3 * k + 1]), __uint_as_float(w[3 * k + 2]),
+                                 __uint_as_float(w[3 * k + 3]), __uint_as_float(w[3 * k + 4]),
+                                 __uint_as_float(w[3 * k + 5]), be, Lv[k], Lv[k + 1]);
         }
     }
 
@@ -439,8 +529,12 @@ struct SmemBlockH {
 struct SmemCdf {
     unsigned long long v[(kCdfChunk + 2 * kMaxRadius) * DC_MAX_BINS];
 };
+constexpr int kLocMaxCols = 1024;    // widest local tile
+constexpr int kLocMaxRows = 64;      // tallest local tile (block_s)
 struct SmemApplyL {
     float2 tab[3 * (kLocMaxBlocksX + 2) * (DC_MAX_BINS + 1)];  // per block and bin: (F at bin start, slope)
+    int2 col[kLocMaxCols + 16];  // per tile column: table slot offset of the left block, weight bits
+    int2 row[kLocMaxRows];  // per tile row: table slot offset of the upper block row, weight bits
 };
 
 template <int OPK>

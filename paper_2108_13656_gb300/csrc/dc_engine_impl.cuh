@@ -3,6 +3,8 @@
 // sample type.
 #pragma once
 
+#include <type_traits>
+
 #include "dc_engine.cuh"
 
 namespace dc {
@@ -25,11 +27,13 @@ struct Derived {
 __device__ __forceinline__ void cta_sync() { __syncthreads(); }
 
 // Groups a thread loads before computing any of them (memory-level parallelism):
-// the light plane-reading phases keep 64 bytes in flight per thread; the
-// compute-heavy RGB phases rely on the number of warps instead.
+// the light plane-reading phases keep 64 bytes in flight per thread, the f32 RGB
+// phases two 48-byte groups; the 8-bit and f16 RGB phases (more arithmetic per
+// byte) rely on the number of warps instead (measured: two groups there cost time
+// or registers).
 template <int IN_DT, bool PLANE>
 struct Unroll {
-    static constexpr int value = PLANE ? (InT<IN_DT>::G == 4 ? 4 : 2) : 1;
+    static constexpr int value = PLANE ? (InT<IN_DT>::G == 4 ? 4 : 2) : (IN_DT == DC_F32 ? 2 : 1);
 };
 
 // ------------------------------------------------------------ tile geometry ---
@@ -232,6 +236,44 @@ __device__ __forceinline__ void walk_tile(const DcImage& im, const TileRect& t, 
             for (int u = 0; u < U; ++u)
                 if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, rr[u], cc, n[u], vv, v[u], w[u], false);
         }
+    }
+}
+
+// Block-patch walk of a local-operator tile: each warp takes patches about one
+// block wide (lx lanes of G pixels across, lx the largest power of two <= s/G, and
+// 32/lx rows down), so that the lanes of a warp read the same block's tone curves -
+// mostly the same or neighbouring bins of them - instead of several blocks' (fewer
+// shared-memory bank conflicts).  Groups stay aligned to multiples of G.
+template <int IN_DT, bool PLANE, class F>
+__device__ __forceinline__ void walk_block_patches(const DcImage& im, const TileRect& t, int s, const Beta& be, F&& f)
+{
+    constexpr int G = InT<IN_DT>::G, U = Unroll<IN_DT, PLANE>::value;
+    constexpr int W = kThreads / 32;
+    const int lgx = min(5, 31 - __clz(max(1, s / G)));
+    const int lx = 1 << lgx, ly = 32 >> lgx, pw = lx * G;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gx = lane & (lx - 1), gy = lane >> lgx;
+    const int npx = (t.c1 - t.c0 + pw - 1) / pw;
+    const int items = npx * ((t.r1 - t.r0 + ly - 1) / ly);
+    const bool vec_img = (im.flags & IF_VEC) != 0;
+    int c[U], n[U], rr[U];
+    bool vec[U];
+    float v[U][G];
+    uint32_t w[U][PLANE ? 1 : 12];
+    for (int it = warp; it < items; it += U * W) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int item = it + u * W;
+            const int py = item / npx, px = item - py * npx;
+            rr[u] = t.r0 + py * ly + gy;
+            c[u] = t.c0 + px * pw + gx * G;
+            n[u] = (item < items && rr[u] < t.r1) ? max(0, min(G, t.c1 - c[u])) : 0;
+            vec[u] = vec_img && n[u] == G;
+            if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, rr[u], c[u], n[u], vec[u], v[u], w[u], true);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, rr[u], c[u], n[u], vec[u], v[u], w[u], false);
     }
 }
 
@@ -589,7 +631,8 @@ __device__ void tile_cdf(const DcBatch<CAP>& P, const DcImage& im, int I, const 
     for (int k = threadIdx.x; k < ncol * B; k += kThreads) {
         const int jj = lo + k / B, j = k % B;
         unsigned long long v = 0ull;
-        for (int I2 = i0; I2 <= i1; ++I2) v += ld_cg_u64(&H[((size_t)I2 * Wb + jj) * B + j]);
+#pragma unroll 5
+        for (int I2 = i0; I2 <= i1; ++I2) v += ld_cg_u64(&H[((size_t)I2 * Wb + jj) * B + j]);  // loads issued together
         S.v[k] = v;
     }
     cta_sync();
@@ -617,13 +660,15 @@ __device__ void tile_cdf(const DcBatch<CAP>& P, const DcImage& im, int I, const 
 // ------------------------------------------------------- phase: local apply --
 // The tile's block row and its neighbours' cumulative tables are staged as
 // (F at the start of bin j, F(j+1) - F(j)) pairs, so each of the four block curves
-// costs one 64-bit shared load and one FMA.  When block_s is a power of two and a
-// multiple of 2G, the bilinear column pair and weight step are fixed per group.
+// costs one 64-bit shared load and one FMA.  The bilinear geometry is tabulated
+// once per tile: per column the table slot of its left block and its weight, per
+// row the slot row of its upper block and its weight.
 template <int IN_DT, bool PLANE, int CAP>
 __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const TileRect& t, int I,
                                  const Beta& be, const Derived& d, unsigned char* smem)
 {
     constexpr int G = InT<IN_DT>::G;
+    constexpr bool ldr = IN_DT == DC_U8;  // u = L; otherwise the fixed-point log coordinate
     SmemApplyL& S = *reinterpret_cast<SmemApplyL*>(smem);
     const int s = P.block_s, B = P.bins, Hb = im.Hb, Wb = im.Wb;
     const int nbx = (t.c1 - t.c0 + s - 1) / s;
@@ -641,65 +686,74 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
         const float e0 = ld_cg_f(e), e1 = ld_cg_f(e + 1);
         S.tab[slot * SB + j] = make_float2(e0, e1 - e0);
     }
-    constexpr bool plane = PLANE;
-    const bool is_log = plane && (im.flags & IF_PLANE_LOG) != 0;
-    const bool ldr = P.ldr != 0;
-    const float delta = P.delta, Bf = (float)B, inv_s = 1.0f / (float)s, alpha = P.alpha;
-    const bool group_cols = (s & (s - 1)) == 0 && s % (2 * G) == 0;
-    cta_sync();
-    const float inv_B = 1.0f / Bf;
-    consume_tile<IN_DT, PLANE>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
-        const float fy = fmaf((float)r + 0.5f, inv_s, -0.5f);
+    // bilinear geometry: nominal block centres ((J + 1/2) s); a pixel at x + 1/2
+    // lies between the centres of blocks floor(x/s - 1/2) and the next
+    const float inv_s = 1.0f / (float)s;
+    // (a ragged group's lanes past the tile read the last column's entry)
+    for (int k = threadIdx.x; k < t.c1 - t.c0 + G; k += kThreads) {
+        const float fx = fmaf((float)(min(t.c0 + k, t.c1 - 1)) + 0.5f, inv_s, -0.5f);
+        const float flx = floorf(fx);
+        S.col[k] = make_int2(((int)flx - (J0 - 1)) * SB, __float_as_int(fx - flx));
+    }
+    for (int k = threadIdx.x; k < t.r1 - t.r0; k += kThreads) {
+        const float fy = fmaf((float)(t.r0 + k) + 0.5f, inv_s, -0.5f);
         const float fly = floorf(fy);
-        const float wy = fy - fly;
-        const float2* row0 = S.tab + ((int)fly - (I - 1)) * W2 * SB;
-        const float2* row1 = row0 + W2 * SB;
-        const float fx0 = fmaf((float)c + 0.5f, inv_s, -0.5f);
-        const float flx0 = floorf(fx0);
-        const int sc0g = (int)flx0 - (J0 - 1);
-        const float wx0 = fx0 - flx0;
+        S.row[k] = make_int2(((int)fly - (I - 1)) * W2 * SB, __float_as_int(fy - fly));
+    }
+    const float delta = P.delta, Bf = (float)B, alpha = P.alpha;
+    const int WSB = W2 * SB;
+    cta_sync();
+    auto body = [&](auto alpha_one) {
+        auto pixel_fn = [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+            const int2 ri = S.row[r - t.r0];
+            const float2* rowp = S.tab + ri.x;
+            const float wy = __int_as_float(ri.y);
+            const int2* colp = S.col + (c - t.c0);
 #pragma unroll
-        for (int k = 0; k < G; ++k) {
-            // bin j and position tt in it: from u = L (8-bit input) or exactly from
-            // the fixed-point log (HDR)
-            int j;
-            float tt, u;
-            if (ldr) {
-                u = fminf(fmaxf(Lv[k], 0.0f), 1.0f);
-                const float Bu = Bf * u;
-                j = min((int)Bu, B - 1);
-                tt = Bu - (float)j;
-            } else {
-                // bin coordinate: kept in the plane by the histogram pass, or
-                // computed from L recomputed from RGB
-                const uint32_t q = is_log ? __float_as_uint(Lv[k]) : coord_of<kLocTS>(Lv[k], false, delta, d, B);
-                const uint32_t jq = min(q >> kLocTS, (uint32_t)(B - 1));
-                j = (int)jq;
-                tt = (float)(q - (jq << kLocTS)) * (1.0f / (float)(1u << kLocTS));
-                u = (float)q * (inv_B / (float)(1u << kLocTS));
+            for (int k = 0; k < G; ++k) {
+                // bin j and position tt in it: from u = L (8-bit input) or exactly from
+                // the fixed-point log coordinate (HDR)
+                int j;
+                float tt, u = 0.0f;
+                if constexpr (ldr) {
+                    u = fminf(fmaxf(Lv[k], 0.0f), 1.0f);
+                    const float Bu = Bf * u;
+                    const float jf = fminf(__fadd_rd(Bu, 8388608.0f), 8388608.0f + (float)(B - 1));  // 2^23 + floor
+                    j = (int)(__float_as_uint(jf) - 0x4B000000u);
+                    tt = Bu - (jf - 8388608.0f);
+                } else {
+                    // the plane holds the coordinate the histogram pass kept; an
+                    // image without a plane recomputes it from L
+                    const uint32_t q = PLANE ? __float_as_uint(Lv[k]) : coord_of<kLocTS>(Lv[k], false, delta, d, B);
+                    const uint32_t jq = min(q >> kLocTS, (uint32_t)(B - 1));
+                    j = (int)jq;
+                    // (q - j 2^24) / 2^24 in [0, 1] through the float bit pattern of 1 + x
+                    tt = __uint_as_float(0x3F800000u + ((q - (jq << kLocTS)) >> (kLocTS - 23))) - 1.0f;
+                    if constexpr (!decltype(alpha_one)::value) u = (float)q * (1.0f / (Bf * (float)(1u << kLocTS)));
+                }
+                const int2 ci = colp[k];
+                const float wx = __int_as_float(ci.y);
+                const float2* p = rowp + ci.x + j;
+                const float2 a = p[0], b = p[SB], cc = p[WSB], dd = p[WSB + SB];
+                const float f00 = fmaf(tt, a.y, a.x), f01 = fmaf(tt, b.y, b.x);
+                const float f10 = fmaf(tt, cc.y, cc.x), f11 = fmaf(tt, dd.y, dd.x);
+                const float top = fmaf(wx, f01 - f00, f00);
+                const float bot = fmaf(wx, f11 - f10, f10);
+                const float F = fmaf(wy, bot - top, top);
+                if constexpr (decltype(alpha_one)::value) {
+                    Lv[k] = F;
+                } else {
+                    Lv[k] = fmaf(alpha, F - u, u);
+                }
             }
-            int sc0;
-            float wx;
-            if (group_cols) {
-                sc0 = sc0g;
-                wx = fmaf((float)k, inv_s, wx0);
-            } else {
-                const float fx = fmaf((float)(c + k) + 0.5f, inv_s, -0.5f);
-                const float flx = floorf(fx);
-                wx = fx - flx;
-                sc0 = (int)flx - (J0 - 1);
-            }
-            const float2 a = row0[sc0 * SB + j], b = row0[(sc0 + 1) * SB + j];
-            const float2 cc = row1[sc0 * SB + j], dd = row1[(sc0 + 1) * SB + j];
-            const float f00 = fmaf(tt, a.y, a.x), f01 = fmaf(tt, b.y, b.x);
-            const float f10 = fmaf(tt, cc.y, cc.x), f11 = fmaf(tt, dd.y, dd.x);
-            const float top = fmaf(wx, f01 - f00, f00);
-            const float bot = fmaf(wx, f11 - f10, f10);
-            const float F = fmaf(wy, bot - top, top);
-            Lv[k] = fmaf(alpha, F - u, u);
-        }
-        GroupIO<IN_DT>::store(im, r, c, n, vec, Lv);
-    });
+            GroupIO<IN_DT>::store(im, r, c, n, vec, Lv);
+        };
+        walk_block_patches<IN_DT, PLANE && IN_DT != DC_U8>(im, t, s, be, pixel_fn);
+    };
+    if (alpha == 1.0f)
+        body(std::true_type{});
+    else
+        body(std::false_type{});
 }
 
 // ------------------------------------------------------------ the engine -----
