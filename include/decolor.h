@@ -206,9 +206,18 @@ DC_API int dc_decolorize_tonemap_global_noalloc(const dc_image_in* in, const dc_
 /* Workspace bytes a call of `op` (DC_OP_*) needs for these inputs; op_params is
  * NULL (DC_OP_DECOLORIZE, DC_OP_GLOBAL) or a dc_local_params* (DC_OP_LOCAL).
  * Returns 0 when the arguments are invalid.  The workspace must be 256-byte
- * aligned; its contents need no initialisation (each call resets what it uses). */
+ * aligned; its contents need no initialisation (each call resets what it uses).
+ * For 8-bit input of up to 12 Mpx per call (per input sample type) the size
+ * includes an f32 luminance plane (4 bytes per pixel) that spares the later passes
+ * from recomputing Eq. 1-6; a call given less (down to dc_workspace_min_bytes)
+ * runs without it, with identical results. */
 DC_API size_t dc_workspace_bytes(int32_t op, const dc_image_in* in, int32_t n,
                                  const void* op_params);
+
+/* The least workspace a call of `op` accepts for these inputs (no optional plane);
+ * same arguments and 0 on invalid arguments.  The paper has no counterpart. */
+DC_API size_t dc_workspace_min_bytes(int32_t op, const dc_image_in* in, int32_t n,
+                                     const void* op_params);
 
 /* Synchronises `stream`, then reads the device-side error word of workspace `ws`
  * (reserved for device-detected errors; the current kernels never wait on each

@@ -74,6 +74,7 @@ _SIGS = {
                                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                             ctypes.c_void_p]),
     "dc_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "dc_workspace_min_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "dc_query_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "dc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "dc_set_tuning": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
@@ -188,16 +189,21 @@ def _stream_handle(stream):
 
 
 class Workspace:
-    """Device workspace owned by torch's allocator, grown on demand (256-byte aligned)."""
+    """Device workspace owned by torch's allocator (256-byte aligned): grown on demand
+    to what each call asks for, or, when created with `nbytes`, exactly that size and
+    never grown (a call then keeps its optional planes only if they fit)."""
 
-    def __init__(self, device=None):
+    def __init__(self, device=None, nbytes: int | None = None):
         self.device = device
         self.buf = None
+        self.fixed = nbytes is not None
+        if self.fixed:
+            self.buf = _torch().empty(max(int(nbytes), 256), dtype=_torch().uint8, device=device or "cuda")
 
     def get(self, nbytes: int):
         torch = _torch()
         nbytes = max(int(nbytes), 256)
-        if self.buf is None or self.buf.numel() < nbytes:
+        if not self.fixed and (self.buf is None or self.buf.numel() < nbytes):
             self.buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device or "cuda")
         ptr = self.buf.data_ptr()
         assert ptr % 256 == 0
@@ -308,10 +314,12 @@ def decolorize_tonemap_local(inputs, outputs, block_s: int = 32, radius_blocks: 
                         workspace=workspace)(stream)
 
 
-def workspace_bytes(op: int, inputs, lparams: dc_local_params | None = None) -> int:
+def workspace_bytes(op: int, inputs, lparams: dc_local_params | None = None, minimum: bool = False) -> int:
+    """dc_workspace_bytes (or dc_workspace_min_bytes with minimum=True) for these inputs."""
     inputs = _as_list(inputs)
     ins, _ = _arrays(inputs, None)
-    return int(load().dc_workspace_bytes(op, ins, len(inputs), ctypes.byref(lparams) if lparams else None))
+    fn = load().dc_workspace_min_bytes if minimum else load().dc_workspace_bytes
+    return int(fn(op, ins, len(inputs), ctypes.byref(lparams) if lparams else None))
 
 
 def query_status(workspace=None, stream=None) -> int:

@@ -21,6 +21,9 @@ constexpr int64_t kHeaderBytes = 256;
 constexpr int64_t kMaxPixels = int64_t(1) << 28;
 constexpr int kMaxLocalSide = 1 << 16;
 constexpr int kLocMaxBlocksX = 32;
+// 8-bit input keeps an f32 luminance plane in the workspace when the launch group
+// is small enough for the plane to stay in L2 between passes (12 Mpx = 48 MB).
+constexpr int64_t kU8PlaneMaxPixels = int64_t(12) << 20;
 constexpr int kLocMaxCols = 1024;
 constexpr int kCdfChunk = 16;
 
@@ -101,6 +104,7 @@ struct Geometry {
     DcImage im;
     int tiles[kMaxPhases];
     int64_t local_bytes;
+    int64_t plane_bytes;  // workspace plane (8-bit input)
 };
 
 struct LaunchPlan {
@@ -116,10 +120,11 @@ bool keeps_plane(const OpArgs& op, int in_dt, int out_dt)
     return op.opk != kOpkDecolor && in_dt != DC_U8 && out_dt == DC_F32;
 }
 
-// Passes that read the plane instead of recomputing L from RGB.
-bool reads_plane(int kind)
+// Passes that read the plane instead of recomputing L from RGB (an 8-bit local
+// call writes its plane in the block-histogram pass, the first one).
+bool reads_plane(int kind, int in_dt)
 {
-    return kind == PK_LOGHIST || kind == PK_APPLY_G || kind == PK_BLOCKH || kind == PK_APPLY_L;
+    return kind == PK_LOGHIST || kind == PK_APPLY_G || kind == PK_APPLY_L || (kind == PK_BLOCKH && in_dt != DC_U8);
 }
 
 // Phase chain of an operation for one input class.
@@ -149,7 +154,8 @@ int phase_list(const OpArgs& op, bool ldr, int32_t* kinds)
 }
 
 void make_geometry(const dc_image_in& in, const dc_image_out& out, const OpArgs& op, const dc_tuning& tu,
-                   int n_phase, const int32_t* kinds, Geometry& g, int tile_rows, int tile_cols, int loc_cols)
+                   int n_phase, const int32_t* kinds, Geometry& g, int tile_rows, int tile_cols, int loc_cols,
+                   bool u8_plane)
 {
     DcImage& im = g.im;
     std::memset(&im, 0, sizeof(im));
@@ -175,10 +181,17 @@ void make_geometry(const dc_image_in& in, const dc_image_out& out, const OpArgs&
     bool vec = al16(in.data) && al16(out.data);
     if (im.rows > 1) vec = vec && (in.stride_bytes % 16 == 0) && (out.stride_bytes % 16 == 0);
     im.flags = vec ? IF_VEC : 0u;
+    g.plane_bytes = 0;
     if (keeps_plane(op, in.dtype, out.dtype)) {
         im.flags |= IF_LPLANE;
+        im.plane = im.out;
+        im.plane_stride = im.out_stride;
         // the local operator and HDR histogram equalisation only need ln(L + delta)
         if (op.opk == kOpkLocal || (op.opk == kOpkGlobal && op.g->mode == DC_HISTEQ)) im.flags |= IF_PLANE_LOG;
+    } else if (u8_plane) {
+        im.flags |= IF_LPLANE;  // `plane` is set by the caller, in the workspace
+        im.plane_stride = align_up((int64_t)im.cols * 4, 16);
+        g.plane_bytes = align_up(im.plane_stride * im.rows, 256);
     }
     im.tiles_x = (im.cols + tile_cols - 1) / tile_cols;
     const int tiles_y = (im.rows + tile_rows - 1) / tile_rows;
@@ -203,12 +216,19 @@ void make_geometry(const dc_image_in& in, const dc_image_out& out, const OpArgs&
 
 template <int CAP>
 int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::vector<int>& idx, bool plane,
-                     const dc_decolor_params* p, const OpArgs& op, uint8_t* ws, bool first, int64_t* need,
-                     void* stream, bool launch)
+                     bool allow_u8_plane, const dc_decolor_params* p, const OpArgs& op, uint8_t* ws, bool first,
+                     int64_t* need, void* stream, bool launch)
 {
     const int n = (int)idx.size();
     const int in_dt = in[idx[0]].dtype;
     const bool ldr = in_dt == DC_U8;
+    bool u8_plane = false;
+    if (allow_u8_plane && ldr && op.opk != kOpkDecolor) {
+        int64_t px = 0;
+        for (int k = 0; k < n; ++k) px += (int64_t)in[idx[k]].width * in[idx[k]].height;
+        u8_plane = px <= kU8PlaneMaxPixels;
+    }
+    plane = plane || u8_plane;
     dc_tuning tu;
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -263,9 +283,13 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
     std::vector<Geometry> geo(n);
     for (int k = 0; k < n; ++k) {
         make_geometry(in[idx[k]], out[idx[k]], op, tu, b->n_phase, b->phase_kind, geo[k], b->tile_rows,
-                      b->tile_cols, b->loc_tile_cols);
+                      b->tile_cols, b->loc_tile_cols, u8_plane);
         geo[k].im.ws_hist = off;
         off += geo[k].local_bytes;
+        if (geo[k].plane_bytes > 0) {
+            geo[k].im.plane = ws ? ws + off : nullptr;
+            off += geo[k].plane_bytes;
+        }
         b->img[k] = geo[k].im;
         b->stats_index[k] = idx[k];
     }
@@ -316,7 +340,7 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
     int rc = DC_OK;
     for (int ph = 0; ph < b->n_phase && rc == DC_OK; ++ph) {
         const int kind = b->phase_kind[ph];
-        const bool pl = plane && reads_plane(kind);
+        const bool pl = plane && reads_plane(kind, in_dt);
         int occ = in_dt == DC_U8 ? occupancy_u8(CAP, op.opk, kind, pl)
                                  : (in_dt == DC_F16 ? occupancy_f16(CAP, op.opk, kind, pl) : occupancy_f32(CAP, op.opk, kind, pl));
         if (occ <= 0) occ = 1;
@@ -337,7 +361,7 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
 }
 
 int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_decolor_params* p, const OpArgs& op,
-        void* ws, size_t ws_bytes, void* stream, size_t* query)
+        void* ws, size_t ws_bytes, void* stream, size_t* query, bool min_query = false)
 {
     if (!in || n < 1) return DC_ERR_INVALID_ARG;
     if (n > DC_MAX_BATCH) return DC_ERR_TOO_MANY;
@@ -391,23 +415,31 @@ int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_deco
             if (!cur.idx.empty()) plans.push_back(cur);
         }
     }
-    int64_t need = kHeaderBytes;
-    for (const LaunchPlan& pl : plans) {
-        const int cnt = (int)pl.idx.size();
-        int r2;
-        if (cnt <= kCapSmall)
-            r2 = build_and_launch<kCapSmall>(in, outs, pl.idx, pl.plane, p, op, nullptr, false, &need, nullptr, false);
-        else if (cnt <= kCapMid)
-            r2 = build_and_launch<kCapMid>(in, outs, pl.idx, pl.plane, p, op, nullptr, false, &need, nullptr, false);
-        else
-            r2 = build_and_launch<kCapLarge>(in, outs, pl.idx, pl.plane, p, op, nullptr, false, &need, nullptr, false);
-        if (r2 != DC_OK) return r2;
+    // workspace: with the optional 8-bit planes (what dc_workspace_bytes reports) and
+    // without them (the least a call accepts); a call keeps the planes when its
+    // workspace holds them
+    int64_t need[2] = {kHeaderBytes, kHeaderBytes};
+    for (int with_plane = 0; with_plane < 2; ++with_plane) {
+        for (const LaunchPlan& pl : plans) {
+            const int cnt = (int)pl.idx.size();
+            const bool a = with_plane != 0;
+            int64_t* nd = &need[with_plane];
+            int r2;
+            if (cnt <= kCapSmall)
+                r2 = build_and_launch<kCapSmall>(in, outs, pl.idx, pl.plane, a, p, op, nullptr, false, nd, nullptr, false);
+            else if (cnt <= kCapMid)
+                r2 = build_and_launch<kCapMid>(in, outs, pl.idx, pl.plane, a, p, op, nullptr, false, nd, nullptr, false);
+            else
+                r2 = build_and_launch<kCapLarge>(in, outs, pl.idx, pl.plane, a, p, op, nullptr, false, nd, nullptr, false);
+            if (r2 != DC_OK) return r2;
+        }
     }
     if (query) {
-        *query = (size_t)need;
+        *query = (size_t)(min_query ? need[0] : need[1]);
         return DC_OK;
     }
-    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < (size_t)need) return DC_ERR_WORKSPACE;
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < (size_t)need[0]) return DC_ERR_WORKSPACE;
+    const bool use_planes = ws_bytes >= (size_t)need[1];
     g_call_launches = 0;
     bool first = true;
     for (const LaunchPlan& pl : plans) {
@@ -416,16 +448,40 @@ int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_deco
         uint8_t* w = static_cast<uint8_t*>(ws);
         int r2;
         if (cnt <= kCapSmall)
-            r2 = build_and_launch<kCapSmall>(in, out, pl.idx, pl.plane, p, op, w, first, &dummy, stream, true);
+            r2 = build_and_launch<kCapSmall>(in, out, pl.idx, pl.plane, use_planes, p, op, w, first, &dummy, stream, true);
         else if (cnt <= kCapMid)
-            r2 = build_and_launch<kCapMid>(in, out, pl.idx, pl.plane, p, op, w, first, &dummy, stream, true);
+            r2 = build_and_launch<kCapMid>(in, out, pl.idx, pl.plane, use_planes, p, op, w, first, &dummy, stream, true);
         else
-            r2 = build_and_launch<kCapLarge>(in, out, pl.idx, pl.plane, p, op, w, first, &dummy, stream, true);
+            r2 = build_and_launch<kCapLarge>(in, out, pl.idx, pl.plane, use_planes, p, op, w, first, &dummy, stream, true);
         if (r2 != DC_OK) return r2;
         first = false;
     }
     g_last_launches = g_call_launches;
     return DC_OK;
+}
+
+// Workspace a call needs: with the optional 8-bit planes (min_only false) or the
+// least it accepts.  0 on invalid arguments.
+size_t workspace_query(int32_t op, const dc_image_in* in, int32_t n, const void* op_params, bool min_only)
+{
+    static const dc_decolor_params kBeta = {0.55f, 0.8f};
+    static const dc_global_params kGlobal = {DC_SIGMOID, 1.0f, 1e-4f, 0};
+    OpArgs a{0, nullptr, nullptr, nullptr};
+    if (op == DC_OP_DECOLORIZE) {
+        a.opk = kOpkDecolor;
+    } else if (op == DC_OP_GLOBAL) {
+        a.opk = kOpkGlobal;
+        a.g = &kGlobal;
+    } else if (op == DC_OP_LOCAL) {
+        a.opk = kOpkLocal;
+        a.l = static_cast<const dc_local_params*>(op_params);
+        if (!a.l) return 0;
+    } else {
+        return 0;
+    }
+    size_t need = 0;
+    if (run(in, nullptr, n, &kBeta, a, nullptr, 0, nullptr, &need, min_only) != DC_OK) return 0;
+    return need;
 }
 
 }  // namespace
@@ -457,24 +513,12 @@ DC_API int dc_decolorize_tonemap_local(const dc_image_in* in, const dc_image_out
 
 DC_API size_t dc_workspace_bytes(int32_t op, const dc_image_in* in, int32_t n, const void* op_params)
 {
-    static const dc_decolor_params kBeta = {0.55f, 0.8f};
-    static const dc_global_params kGlobal = {DC_SIGMOID, 1.0f, 1e-4f, 0};
-    OpArgs a{0, nullptr, nullptr, nullptr};
-    if (op == DC_OP_DECOLORIZE) {
-        a.opk = kOpkDecolor;
-    } else if (op == DC_OP_GLOBAL) {
-        a.opk = kOpkGlobal;
-        a.g = &kGlobal;
-    } else if (op == DC_OP_LOCAL) {
-        a.opk = kOpkLocal;
-        a.l = static_cast<const dc_local_params*>(op_params);
-        if (!a.l) return 0;
-    } else {
-        return 0;
-    }
-    size_t need = 0;
-    if (run(in, nullptr, n, &kBeta, a, nullptr, 0, nullptr, &need) != DC_OK) return 0;
-    return need;
+    return workspace_query(op, in, n, op_params, false);
+}
+
+DC_API size_t dc_workspace_min_bytes(int32_t op, const dc_image_in* in, int32_t n, const void* op_params)
+{
+    return workspace_query(op, in, n, op_params, true);
 }
 
 DC_API int dc_query_status(const void* ws, void* stream)
@@ -556,3 +600,10 @@ DC_API int dc_last_launch_count(void) { return g_last_launches; }
 DC_API int dc_version(void) { return 100; }
 
 }  // extern "C"
+
+namespace dc {
+size_t workspace_min_bytes(int32_t op, const dc_image_in* in, int32_t n, const void* op_params)
+{
+    return workspace_query(op, in, n, op_params, true);
+}
+}  // namespace dc

@@ -405,10 +405,11 @@ struct GroupIO {
         }
     }
 
-    // Luminance from the f32 plane an earlier phase wrote into `out`.
+    // Luminance (or its fixed-point log or bin coordinate) from the f32 plane an
+    // earlier phase wrote.
     __device__ static void from_plane(const DcImage& im, int r, int c, int n, bool vec, float (&Lv)[G])
     {
-        const float* p = reinterpret_cast<const float*>(im.out + (int64_t)r * im.out_stride) + c;
+        const float* p = reinterpret_cast<const float*>(im.plane + (int64_t)r * im.plane_stride) + c;
         if (vec) {
 #pragma unroll
             for (int k = 0; k < G; k += 4) {
@@ -428,7 +429,7 @@ struct GroupIO {
     __device__ static __forceinline__ void store_plane(const DcImage& im, int r, int c, int n, bool vec,
                                                        const float (&y)[G])
     {
-        float* p = reinterpret_cast<float*>(im.out + (int64_t)r * im.out_stride) + c;
+        float* p = reinterpret_cast<float*>(im.plane + (int64_t)r * im.plane_stride) + c;
         if (vec) {
             const unsigned long long pol = policy_evict_last();
 #pragma unroll

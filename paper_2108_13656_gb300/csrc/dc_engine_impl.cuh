@@ -282,7 +282,7 @@ __device__ __forceinline__ void walk_block_patches(const DcImage& im, const Tile
 template <int IN_DT, bool PLANE, class F>
 __device__ __forceinline__ void consume_tile(const DcImage& im, const TileRect& t, const Beta& be, F&& f)
 {
-    walk_tile<IN_DT, PLANE && IN_DT != DC_U8>(im, t, be, f);  // 8-bit images never keep a plane
+    walk_tile<IN_DT, PLANE>(im, t, be, f);
 }
 
 // --------------------------------------------------------------- reductions --
@@ -551,6 +551,7 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
         S.fs[k] = 0u;
     }
     constexpr bool plane = PLANE;
+    const bool plane_out = !PLANE && (im.flags & IF_LPLANE) != 0;  // this pass writes the plane
     const bool is_log = plane && (im.flags & IF_PLANE_LOG) != 0;
     const bool ldr = P.ldr != 0;
     const float delta = P.delta, scale = (float)B * 1048576.0f;
@@ -600,8 +601,12 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
             atomicAdd(&S.cnt[cur], rc);
             atomicAdd(&S.fs[cur], rf);
         }
-        // the apply pass reads the coordinate instead of the logarithm
+        // the apply pass reads the coordinate instead of the logarithm (HDR), or the
+        // luminance instead of recomputing it (8-bit input with a workspace plane)
         if (is_log) GroupIO<IN_DT>::store_plane(im, r, c, n, vec, tq);
+        if constexpr (!PLANE) {
+            if (plane_out) GroupIO<IN_DT>::store_plane(im, r, c, n, vec, Lv);
+        }
     });
     cta_sync();
     unsigned long long* H = reinterpret_cast<unsigned long long*>(P.ws + im.ws_hist);
@@ -748,7 +753,7 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
             }
             GroupIO<IN_DT>::store(im, r, c, n, vec, Lv);
         };
-        walk_block_patches<IN_DT, PLANE && IN_DT != DC_U8>(im, t, s, be, pixel_fn);
+        walk_block_patches<IN_DT, PLANE>(im, t, s, be, pixel_fn);
     };
     if (alpha == 1.0f)
         body(std::true_type{});
@@ -873,7 +878,7 @@ int occupancy_one()
 }
 
 // Valid (operation, pass kind, reads a plane) triples, expanded for every batch
-// capacity.  Only f16/f32 input keeps a plane.
+// capacity.  8-bit input reads a plane only in the apply passes.
 #define DC_FOR_EACH_PASS(X)                                                                                  \
     X(OPK_DECOLOR, PK_DECOLOR, false) X(OPK_GLOBAL, PK_STATS, false) X(OPK_GLOBAL, PK_STATS_LOG, false)      \
         X(OPK_GLOBAL, PK_LOGHIST, false) X(OPK_GLOBAL, PK_LOGHIST, true) X(OPK_GLOBAL, PK_APPLY_G, false)    \
@@ -885,7 +890,7 @@ template <int IN_DT>
 int launch_dispatch(const void* batch, int cap, int opk, int kind, int ph, bool pl, LaunchShape ls, void* stream)
 {
 #define DC_CASE(OP, K, PL)                                                                               \
-    if constexpr (!PL || IN_DT != DC_U8) {                                                              \
+    if constexpr (!PL || IN_DT != DC_U8 || K == PK_APPLY_G || K == PK_APPLY_L) {                        \
         if (opk == OP && kind == K && pl == PL) {                                                       \
             if (cap == kCapSmall) return launch_one<IN_DT, OP, K, kCapSmall, PL>(batch, ph, ls, stream); \
             if (cap == kCapMid) return launch_one<IN_DT, OP, K, kCapMid, PL>(batch, ph, ls, stream);     \
@@ -901,7 +906,7 @@ template <int IN_DT>
 int occupancy_dispatch(int cap, int opk, int kind, bool pl)
 {
 #define DC_CASE(OP, K, PL)                                                                 \
-    if constexpr (!PL || IN_DT != DC_U8) {                                                \
+    if constexpr (!PL || IN_DT != DC_U8 || K == PK_APPLY_G || K == PK_APPLY_L) {          \
         if (opk == OP && kind == K && pl == PL) {                                         \
             if (cap == kCapSmall) return occupancy_one<IN_DT, OP, K, kCapSmall, PL>(); \
             if (cap == kCapMid) return occupancy_one<IN_DT, OP, K, kCapMid, PL>();     \

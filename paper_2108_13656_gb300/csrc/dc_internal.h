@@ -34,15 +34,17 @@ enum PhaseKind : int32_t {
 // per-image flags
 enum : uint32_t {
     IF_VEC = 1u,      // 16-byte aligned pointers and strides: vector path
-    IF_LPLANE = 2u,   // out is an f32 plane that holds L between phases
+    IF_LPLANE = 2u,   // the image keeps an f32 plane (`plane`) that holds L between phases
     IF_PLANE_LOG = 4u,  // ... and it holds round(ln(L + delta) 2^24) as int32 bits instead of L
 };
 
-struct DcImage {                 // 80 bytes
+struct DcImage {                 // 96 bytes
     const uint8_t* in;
     uint8_t* out;
     int64_t in_stride;           // bytes between (logical) rows
     int64_t out_stride;
+    uint8_t* plane;              // f32 plane kept between passes (the output, or workspace for 8-bit input)
+    int64_t plane_stride;
     int32_t rows, cols;          // logical geometry of pixelwise phases
     int32_t prow, pcol;          // physical geometry (local operator)
     int32_t out_dt;
@@ -146,5 +148,8 @@ int launch_engine_f32(const void* batch, int cap, int opk, int kind, int ph, boo
 int occupancy_u8(int cap, int opk, int kind, bool pl);
 int occupancy_f16(int cap, int opk, int kind, bool pl);
 int occupancy_f32(int cap, int opk, int kind, bool pl);
+
+// Smallest workspace a call accepts (without the optional 8-bit plane); 0 on error.
+size_t workspace_min_bytes(int32_t op, const dc_image_in* in, int32_t n, const void* op_params);
 
 }  // namespace dc

@@ -13,6 +13,7 @@
 #include <cstdint>
 
 #include "../../include/decolor.h"
+#include "dc_internal.h"
 
 namespace {
 
@@ -49,7 +50,7 @@ extern "C" DC_API int dc_decolorize_tonemap_global_noalloc(const dc_image_in* in
                                                            const dc_global_params* gparams,
                                                            dc_global_stats* stats, void* stream)
 {
-    const size_t need = dc_workspace_bytes(DC_OP_GLOBAL, in, n, nullptr);
+    const size_t need = dc::workspace_min_bytes(DC_OP_GLOBAL, in, n, nullptr);  // no optional plane
     if (need == 0) return DC_ERR_INVALID_ARG;
     if (need > kScratchBytes) return DC_ERR_WORKSPACE;  // batch too large for the fixed scratch
     void* ws = nullptr;

@@ -71,13 +71,25 @@ def _img(w, h, dt=0, stride=None, ptr=1 << 20):
 def test_workspace_bytes_sizes(abi):
     lib = abi.load()
     ins = (abi.dc_image_in * 1)(_img(3840, 2160))
-    g = lib.dc_workspace_bytes(abi.DC_OP_GLOBAL, ins, 1, None)
+    g = lib.dc_workspace_min_bytes(abi.DC_OP_GLOBAL, ins, 1, None)
     assert 256 < g < 1 << 20
+    # 8-bit input of this size: the optional f32 luminance plane on top
+    assert lib.dc_workspace_bytes(abi.DC_OP_GLOBAL, ins, 1, None) >= g + 3840 * 2160 * 4
     lp = abi.local_params()
-    loc = lib.dc_workspace_bytes(abi.DC_OP_LOCAL, ins, 1, ctypes.byref(lp))
+    loc = lib.dc_workspace_min_bytes(abi.DC_OP_LOCAL, ins, 1, ctypes.byref(lp))
     Hb, Wb = (2160 + 31) // 32, 3840 // 32
     assert loc >= g + Hb * Wb * 32 * 8 + Hb * Wb * 33 * 4
+    assert lib.dc_workspace_bytes(abi.DC_OP_LOCAL, ins, 1, ctypes.byref(lp)) >= loc + 3840 * 2160 * 4
     assert lib.dc_workspace_bytes(abi.DC_OP_LOCAL, ins, 1, None) == 0
+    assert lib.dc_workspace_min_bytes(abi.DC_OP_LOCAL, ins, 1, None) == 0
+    # decolorize never keeps a plane; HDR input keeps it in its f32 output
+    assert lib.dc_workspace_bytes(abi.DC_OP_DECOLORIZE, ins, 1, None) == \
+        lib.dc_workspace_min_bytes(abi.DC_OP_DECOLORIZE, ins, 1, None)
+    hdr = (abi.dc_image_in * 1)(_img(3840, 2160, dt=abi.DC_F32))
+    assert lib.dc_workspace_bytes(abi.DC_OP_GLOBAL, hdr, 1, None) == lib.dc_workspace_min_bytes(abi.DC_OP_GLOBAL, hdr, 1, None)
+    # above 12 Mpx per call the 8-bit plane is not kept
+    big = (abi.dc_image_in * 1)(_img(4096, 3200))
+    assert lib.dc_workspace_bytes(abi.DC_OP_GLOBAL, big, 1, None) == lib.dc_workspace_min_bytes(abi.DC_OP_GLOBAL, big, 1, None)
     assert lib.dc_workspace_bytes(7, ins, 1, None) == 0
     many = (abi.dc_image_in * 300)(*[_img(64 + i, 32) for i in range(300)])
     assert lib.dc_workspace_bytes(abi.DC_OP_GLOBAL, many, 300, None) > 0

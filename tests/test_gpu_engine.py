@@ -106,3 +106,32 @@ def test_cuda_graph_capture_matches_eager(dc):
     torch.cuda.synchronize()
     for e, o in zip(eager, outs):
         assert torch.equal(e, o)
+
+
+@pytest.mark.parametrize("op", ["global", "histeq", "local"])
+def test_u8_plane_changes_no_result(dc, op):
+    """8-bit input: a workspace with the optional luminance plane and the minimum
+    workspace (Eq. 1-6 recomputed in every pass) give the same bits."""
+    import torch
+    from paper_2108_13656_gb300 import synth
+    img = synth.s_ldr(1021, 347, 12)
+    x = to_dev(img)
+    code = dc.DC_OP_LOCAL if op == "local" else dc.DC_OP_GLOBAL
+    lp = dc.local_params() if op == "local" else None
+    full = dc.workspace_bytes(code, x, lp)
+    least = dc.workspace_bytes(code, x, lp, minimum=True)
+    assert full >= least + 1021 * 347 * 4
+    ys = []
+    for nbytes in (full, least):
+        ws = dc.Workspace(nbytes=nbytes)  # exactly this many bytes
+        y = torch.empty((347, 1021), dtype=torch.float32, device="cuda")
+        st = torch.zeros(dc.STATS_BYTES, dtype=torch.uint8, device="cuda")
+        if op == "local":
+            dc.decolorize_tonemap_local(x, y, workspace=ws)
+        else:
+            dc.decolorize_tonemap_global(x, y, mode="sigmoid" if op == "global" else "histeq", stats=st, workspace=ws)
+        torch.cuda.synchronize()
+        assert dc.query_status(ws) == 0
+        ys.append((y.cpu(), st.cpu()))
+    assert torch.equal(ys[0][0], ys[1][0])
+    assert torch.equal(ys[0][1], ys[1][1])
