@@ -307,6 +307,31 @@ def ragged_batch(dev, n_images: int, peak: float) -> dict:
             "l2": "inputs (%.2f GB) larger than L2" % (3 * px / 1e9)}
 
 
+# ----------------------------------------------------------- precision study ----
+def precision_8k(dev, peak: float) -> dict:
+    """7680x4320 linear HDR over 6 decades (seed 4) through decolorize + local tone
+    mapping with FP16 and with FP32 storage (FP32 arithmetic, f32 output): time per
+    call and algorithmic bandwidth (10 and 16 bytes per pixel).  The errors against
+    the FP64 oracle are measured by the test suite."""
+    import torch
+    import paper_2108_13656_gb300 as dc
+    from paper_2108_13656_gb300 import synth
+    W8, H8 = 7680, 4320
+    img32 = synth.s_hdr(W8, H8, seed=4, decades=6.0, sigma=2.76)
+    out = {}
+    for name, npdt, bpp in (("f16", np.float16, 6 + 4), ("f32", np.float32, 12 + 4)):
+        x = torch.from_numpy(img32.astype(npdt)).to(dev)
+        y = torch.empty((H8, W8), dtype=torch.float32, device=dev)
+        call = dc.PreparedCall("local", x, y, workspace=dc.Workspace(device=dev))
+        call()
+        ms = _event_ms(call, 10)
+        out[name] = {"ms": ms, "gpix_s": W8 * H8 / ms / 1e6, "GBps": bpp * W8 * H8 / ms / 1e6,
+                     "frac_of_measured_hbm": bpp * W8 * H8 / ms / 1e6 / peak, "bytes_per_px": bpp}
+        del x, y, call
+    out["l2"] = "inputs (199 / 398 MB) larger than L2"
+    return out
+
+
 # ------------------------------------------------------------------ serving ----
 def serving(dev, n_requests: int, rate: float) -> dict:
     """The serving trace (Poisson arrivals, sizes 720p..8K, 70% u8 / 30% f16, half
@@ -460,6 +485,8 @@ def run_native(args):
         line["cpu_baseline"] = cpu_baseline(imgs)
     if not args.no_extras:
         line["ragged_batch"] = ragged_batch(dev, args.ragged_images, peak)
+        torch.cuda.empty_cache()
+        line["precision_8k_local"] = precision_8k(dev, peak)
         torch.cuda.empty_cache()
         line["serving"] = serving(dev, args.serve_requests, args.serve_rate)
     print(json.dumps(line))

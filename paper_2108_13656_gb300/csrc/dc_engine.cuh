@@ -245,12 +245,13 @@ __device__ __forceinline__ float luminance_hdr(float R, float G, float B, const 
 
 // ------------------------------------------------------ fixed-point log ------
 // ln x in units of 2^-24, for x >= FLT_MIN: x = 2^e m with m in (1/sqrt 2, sqrt 2],
-// ln x = e ln 2 + ln m, the first term exact in 2^-40 units, ln m (|ln m| < 0.35)
-// from the hardware base-2 logarithm (absolute error about 2^-22 on [1/2, 2]), one
-// rounding at the end.  Absolute error about 2e-7 whatever the magnitude of ln x,
-// where a binary32 ln x near 7 is only good to 5e-7 and its normalisation by the
-// log range adds as much again: the histogram forms need the absolute error.
-constexpr long long kLn2Q40 = 762123384786LL;  // round(ln 2 * 2^40)
+// ln x = e ln 2 + ln m, the first term from ln 2 in 2^-32 units (error below 2^-30
+// for any e) rounded to 2^-24, ln m (|ln m| < 0.35) from the hardware base-2
+// logarithm (absolute error about 2^-22 on [1/2, 2]) rounded to 2^-24.  Absolute
+// error about 2e-7 whatever the magnitude of ln x, where a binary32 ln x near 7 is
+// only good to 5e-7 and its normalisation by the log range adds as much again: the
+// histogram forms need the absolute error.
+constexpr long long kLn2Q32 = 2977044472LL;  // round(ln 2 * 2^32)
 __device__ __forceinline__ int ln_q24(float x)
 {
     const uint32_t bits = __float_as_uint(x);
@@ -261,8 +262,8 @@ __device__ __forceinline__ int ln_q24(float x)
         ++e;
     }
     const float lm = __log2f(__uint_as_float(mb)) * 0.693147180559945309f;
-    const long long q = (long long)e * kLn2Q40 + __float2ll_rn(lm * 1099511627776.0f);  // 2^-40 units
-    return (int)((q + (1ll << 15)) >> 16);
+    const int ep = (int)(((long long)e * kLn2Q32 + 128) >> 8);
+    return ep + __float2int_rn(lm * 16777216.0f);
 }
 
 // Two linear pixels: negatives (and NaN) to 0, the paired Eq. 1-6, and the scaled

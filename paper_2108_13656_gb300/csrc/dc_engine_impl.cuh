@@ -15,14 +15,20 @@ struct TileRect {
 
 // Values a tile derives from an image's finished statistics pass.  For the
 // fixed-point log forms: vmin, vmax of v = round(ln(L + delta) 2^24), the range
-// R = vmax - vmin shifted right by sh until it is below 2^30 (Rs), and 1/Rs.  A
-// constant image gets the range [v - 1, v + 1], which puts every pixel at u = 1/2.
+// R = vmax - vmin shifted right by sh until it is below 2^30 (Rs), and the
+// fixed-point reciprocals m_loc = floor(bins 2^56 / Rs), m_glob = floor(256 2^54 / Rs)
+// that turn v into bin coordinates.  A constant image gets the range [v - 1, v + 1],
+// which puts every pixel at u = 1/2.
 struct Derived {
     float mu, exp_mu, lmin, lmax;
     int vmin, vmax, sh;
     uint32_t Rs;
-    float invRs;
+    unsigned long long m_loc, m_glob;
 };
+
+// Coordinate shifts: 2^-24 of a bin for the local operator (bins <= 64), 2^-22 of
+// a bin for the 256-bin global histogram, so that nb 2^S stays below 2^31.
+constexpr int kLocTS = 24, kGlobTS = 22;
 
 __device__ __forceinline__ void cta_sync() { __syncthreads(); }
 
@@ -89,7 +95,7 @@ __device__ __forceinline__ TileRect tile_rect(const DcBatch<CAP>& P, const DcIma
 
 // mu, lmin, lmax from the exact integer accumulators of a finished stats pass
 // (fixed_log: the min and max are of the 2^-24 fixed-point logarithms).
-__device__ __forceinline__ Derived derive(const DcImgCtrl* ic, long long N, bool fixed_log)
+__device__ __forceinline__ Derived derive(const DcImgCtrl* ic, long long N, bool fixed_log, int bins)
 {
     Derived d;
     const long long sum = (long long)ld_cg_u64(&ic->logsum);
@@ -99,7 +105,6 @@ __device__ __forceinline__ Derived derive(const DcImgCtrl* ic, long long N, bool
     d.exp_mu = expf(d.mu);
     d.vmin = d.vmax = d.sh = 0;
     d.Rs = 2u;
-    d.invRs = 0.5f;
     if (fixed_log) {
         const int vmax = (int)(ld_cg_u32(&ic->lmax_ord) ^ 0x80000000u);
         const int vmin = (int)(~ld_cg_u32(&ic->lmin_nord) ^ 0x80000000u);
@@ -114,7 +119,6 @@ __device__ __forceinline__ Derived derive(const DcImgCtrl* ic, long long N, bool
                 ++d.sh;
             }
             d.Rs = R;
-            d.invRs = 1.0f / (float)R;
         } else {
             d.vmin = vmin - 1;
             d.vmax = vmin + 1;
@@ -123,42 +127,31 @@ __device__ __forceinline__ Derived derive(const DcImgCtrl* ic, long long N, bool
         d.lmin = ord_dec(~ld_cg_u32(&ic->lmin_nord));
         d.lmax = ord_dec(ld_cg_u32(&ic->lmax_ord));
     }
+    d.m_loc = (unsigned long long)(((unsigned __int128)(unsigned)max(bins, 1) << (32 + kLocTS)) / d.Rs);
+    d.m_glob = (unsigned long long)(((unsigned __int128)256u << (32 + kGlobTS)) / d.Rs);
     return d;
 }
 
 // Bin coordinate t = nb u = nb (v - vmin) / R of a fixed-point log value, in units
-// of 2^-S (0 <= t <= nb).  The integer part comes out exact: a float quotient
-// estimates it to within one and the exact 32-bit remainder (|rem| < 2^31 because
-// Rs < 2^30) corrects it; the one rounding left is that of the fraction to 2^-S.
+// of 2^-S (0 <= t <= nb): the high half of (v - vmin) 2^32 times the fixed-point
+// reciprocal m = floor(nb 2^(32+S) / Rs), i.e. floor(t 2^S) or one unit below it
+// (the reciprocal's truncation is below 2^-32 of it and v - vmin < 2^30).
 template <int S>
-__device__ __forceinline__ uint32_t bin_coord(int v, const Derived& d, int nb)
+__device__ __forceinline__ uint32_t bin_coord(int v, const Derived& d)
 {
     v = min(max(v, d.vmin), d.vmax);
     const uint32_t dv = ((uint32_t)v - (uint32_t)d.vmin) >> d.sh;
-    int j = (int)((float)dv * ((float)nb * d.invRs));
-    int rem = (int)(dv * (uint32_t)nb - (uint32_t)j * d.Rs);
-    if (rem < 0) {
-        --j;
-        rem += (int)d.Rs;
-    } else if (rem >= (int)d.Rs) {
-        ++j;
-        rem -= (int)d.Rs;
-    }
-    const uint32_t f = __float2uint_rn((float)rem * (d.invRs * (float)(1u << S)));
-    return ((uint32_t)j << S) + f;
+    const unsigned long long m = S == kLocTS ? d.m_loc : d.m_glob;
+    return (uint32_t)__umul64hi((unsigned long long)dv << 32, m);
 }
-
-// Coordinate shifts: 2^-24 of a bin for the local operator (bins <= 64), 2^-22 of
-// a bin for the 256-bin global histogram, so that nb 2^S stays below 2^31.
-constexpr int kLocTS = 24, kGlobTS = 22;
 
 // Bin coordinate of a value a histogram pass sees: from the plane's fixed-point
 // log (a histogram pass then keeps the coordinate in the plane for the apply
 // pass), or from L recomputed from RGB.
 template <int S>
-__device__ __forceinline__ uint32_t coord_of(float val, bool is_log_plane, float delta, const Derived& d, int nb)
+__device__ __forceinline__ uint32_t coord_of(float val, bool is_log_plane, float delta, const Derived& d)
 {
-    return bin_coord<S>(is_log_plane ? __float_as_int(val) : ln_q24(val + delta), d, nb);
+    return bin_coord<S>(is_log_plane ? __float_as_int(val) : ln_q24(val + delta), d);
 }
 
 // ------------------------------------------------------------- group walk ---
@@ -444,7 +437,7 @@ __device__ void tile_loghist(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl
         float tq[G] = {};
 #pragma unroll
         for (int k = 0; k < G; ++k) {
-            const uint32_t q = k < n ? coord_of<kGlobTS>(Lv[k], is_log, delta, d, 256) : 0u;
+            const uint32_t q = k < n ? coord_of<kGlobTS>(Lv[k], is_log, delta, d) : 0u;
             tq[k] = __uint_as_float(q);
             if (k < n) atomicAdd(&S.hist[min(q >> kGlobTS, 255u)], 1u);
         }
@@ -520,7 +513,7 @@ __device__ void tile_apply_global(const DcBatch<CAP>& P, const DcImage& im,
                 } else {
                     // bin coordinate: kept in the plane by the histogram pass, or
                     // computed from L recomputed from RGB
-                    const uint32_t q = is_log ? __float_as_uint(Lv[j]) : coord_of<kGlobTS>(Lv[j], false, delta, d, 256);
+                    const uint32_t q = is_log ? __float_as_uint(Lv[j]) : coord_of<kGlobTS>(Lv[j], false, delta, d);
                     const uint32_t b = min(q >> kGlobTS, 255u);
                     const float frac = (float)(q - (b << kGlobTS)) * (1.0f / (float)(1u << kGlobTS));
                     const float e0 = S.lut[b], e1 = S.lut[b + 1];
@@ -572,7 +565,7 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
                     x = min(max(__float2int_rn(fmaf(fminf(fmaxf(Lv[k], 0.0f), 1.0f), scale, -524288.0f)), 0), xmax);
                 } else {
                     // t - 1/2 from 2^-24 to 2^-20 units, rounded
-                    const uint32_t q = coord_of<kLocTS>(Lv[k], is_log, delta, d, B);
+                    const uint32_t q = coord_of<kLocTS>(Lv[k], is_log, delta, d);
                     tq[k] = __uint_as_float(q);
                     x = min(max(((int)q - (1 << (kLocTS - 1)) + 8) >> (kLocTS - 20), 0), xmax);
                 }
@@ -729,7 +722,7 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
                 } else {
                     // the plane holds the coordinate the histogram pass kept; an
                     // image without a plane recomputes it from L
-                    const uint32_t q = PLANE ? __float_as_uint(Lv[k]) : coord_of<kLocTS>(Lv[k], false, delta, d, B);
+                    const uint32_t q = PLANE ? __float_as_uint(Lv[k]) : coord_of<kLocTS>(Lv[k], false, delta, d);
                     const uint32_t jq = min(q >> kLocTS, (uint32_t)(B - 1));
                     j = (int)jq;
                     // (q - j 2^24) / 2^24 in [0, 1] through the float bit pattern of 1 + x
@@ -812,7 +805,7 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
         const DcImage& im = P.img[img];
         DcImgCtrl* ic = img_ctrl(P.ctrl, img);
         if (need_d && img != cached) {
-            if (threadIdx.x == 0) s_d = derive(ic, (long long)im.prow * (long long)im.pcol, fixed_log);
+            if (threadIdx.x == 0) s_d = derive(ic, (long long)im.prow * (long long)im.pcol, fixed_log, P.bins);
             cta_sync();
             cached = img;
         }
