@@ -176,12 +176,13 @@ def ncu_traffic(op_name: str):
 
 
 # ----------------------------------------------------------------- CPU oracle ----
-def oracle_step(imgs, rows: int):
-    """The FP64 oracle on a band of `rows` rows of each variant, all four operations."""
+def oracle_step(imgs, rows: int, r0: int = 0):
+    """The FP64 oracle on the band of `rows` rows from row r0 of each variant, all four
+    operations."""
     import oracle
     n = 0
     for name, var, op, _, _ in OPS:
-        img = imgs[var][:rows]
+        img = imgs[var][r0:r0 + rows]
         if op == "global":
             oracle.tonemap_global(img)
         else:
@@ -204,9 +205,30 @@ def cpu_baseline(imgs, budget_s: float = 12.0):
     for _ in range(reps):
         tot += oracle_step(imgs, rows)
     dt = time.perf_counter() - t0
-    return {"value": tot / dt / 1e9, "unit": "Gpix/s", "cores": 1, "kind": "oracle",
-            "sample": "%d repetitions of a %d-row band (%d px) of both 3840-wide variants through all "
-                      "four operations, FP64 C oracle, single thread" % (reps, rows, rows * W)}
+    out = {"value": tot / dt / 1e9, "unit": "Gpix/s", "cores": 1, "kind": "oracle",
+           "sample": "%d repetitions of a %d-row band (%d px) of both 3840-wide variants through all "
+                     "four operations, FP64 C oracle, single thread" % (reps, rows, rows * W)}
+    # the same oracle on every host core: one thread per core, each on its own band
+    # (the C calls release the interpreter lock)
+    try:
+        ncores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        ncores = os.cpu_count() or 1
+    counts = [0] * ncores
+
+    def worker(k):
+        for _ in range(max(1, reps // 2)):
+            counts[k] += oracle_step(imgs, rows, (k % (H // rows)) * rows)
+    t0 = time.perf_counter()
+    ths = [threading.Thread(target=worker, args=(k,)) for k in range(ncores)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    dt = time.perf_counter() - t0
+    out["all_cores"] = {"value": sum(counts) / dt / 1e9, "unit": "Gpix/s", "cores": ncores,
+                        "sample": "%d threads, each %d repetitions of its own %d-row band" % (ncores, max(1, reps // 2), rows)}
+    return out
 
 
 def run_reference(args):
@@ -307,6 +329,21 @@ def ragged_batch(dev, n_images: int, peak: float) -> dict:
             "l2": "inputs (%.2f GB) larger than L2" % (3 * px / 1e9)}
 
 
+# ------------------------------------------------------------ small decolorize ----
+def decolorize_512(dev) -> dict:
+    """512x512 8-bit S-LDR (seed 0), decolorize only, u8 output: one launch."""
+    import torch
+    import paper_2108_13656_gb300 as dc
+    from paper_2108_13656_gb300 import synth
+    x = torch.from_numpy(synth.s_ldr(512, 512, seed=0)).to(dev)
+    y = torch.empty((512, 512), dtype=torch.uint8, device=dev)
+    call = dc.PreparedCall("decolorize", x, y, workspace=dc.Workspace(device=dev))
+    call()
+    ms = _event_ms(call, 50)
+    return {"us": ms * 1e3, "gpix_s": 512 * 512 / ms / 1e6, "launches": 1,
+            "note": "launch-bound: 1 MB of traffic, below L2 size; L2 not flushed"}
+
+
 # ----------------------------------------------------------- precision study ----
 def precision_8k(dev, peak: float) -> dict:
     """7680x4320 linear HDR over 6 decades (seed 4) through decolorize + local tone
@@ -339,7 +376,7 @@ def serving(dev, n_requests: int, rate: float) -> dict:
     serial single-image calls."""
     from paper_2108_13656_gb300 import serve
     trace = serve.make_trace(n_requests, rate, seed=5)
-    pool = serve.HostPool(trace)
+    pool = serve.HostPool(trace, device=dev)
     warm = serve.make_trace(min(200, n_requests), rate, seed=6)
     serve.serve_batched(warm, pool, device=dev)
     serve.serve_serial(warm, pool, device=dev)
@@ -484,6 +521,7 @@ def run_native(args):
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(imgs)
     if not args.no_extras:
+        line["decolorize_512"] = decolorize_512(dev)
         line["ragged_batch"] = ragged_batch(dev, args.ragged_images, peak)
         torch.cuda.empty_cache()
         line["precision_8k_local"] = precision_8k(dev, peak)

@@ -19,6 +19,7 @@ from __future__ import annotations
 
 import collections
 import dataclasses
+import gc
 import time
 
 import numpy as np
@@ -51,16 +52,24 @@ def make_trace(n: int, rate: float, seed: int, sizes=SERVE_SIZES, p_u8: float = 
                     tuple(sizes[int(size_idx[i])]), int(var[i])) for i in range(n)]
 
 
-class _OutPool:
-    """Recycled pinned host output buffers per (size, dtype)."""
+class _BufPool:
+    """Recycled buffers per (shape, dtype): pinned host memory, or device memory
+    (allocating and pinning are slow and may synchronise the device, so the loop
+    reuses what it allocated; a buffer goes back only after its batch completed)."""
 
-    def __init__(self):
+    def __init__(self, device=None):
+        self.device = device  # None: pinned host memory
         self.free = collections.defaultdict(list)
 
-    def get(self, shape, dtype):
+    def new(self, shape, dtype):
         import torch
-        lst = self.free[(shape, dtype)]
-        return lst.pop() if lst else torch.empty(shape, dtype=dtype).pin_memory()
+        if self.device is None:
+            return torch.empty(shape, dtype=dtype).pin_memory()
+        return torch.empty(shape, dtype=dtype, device=self.device)
+
+    def get(self, shape, dtype):
+        lst = self.free[(tuple(shape), dtype)]
+        return lst.pop() if lst else self.new(tuple(shape), dtype)
 
     def put(self, t):
         self.free[(tuple(t.shape), t.dtype)].append(t)
@@ -69,13 +78,15 @@ class _OutPool:
 class HostPool:
     """Pinned host images, one per (size, sample type, variant) of a trace: S-LDR for
     u8, S-HDR (5 decades) stored as binary16 for f16; variants are cyclic shifts.
-    Also the pinned output buffers, `outputs_per_class` per (size, output type)
-    allocated up front (pinning is slow; more are added on demand)."""
+    Also the reusable buffers: pinned host outputs and device inputs and outputs,
+    `buffers_per_class` of each per (size, sample type) allocated up front (more
+    are added on demand)."""
 
-    def __init__(self, trace, seed: int = 5, outputs_per_class: int = 4):
+    def __init__(self, trace, seed: int = 5, buffers_per_class: int = 12, device=None):
         import torch
         self.images = {}
-        self.outpool = _OutPool()
+        self.outpool = _BufPool()
+        self.devpool = _BufPool(torch.device(device or "cuda"))
         keys = sorted({(r.size, r.dtype, r.variant) for r in trace})
         bases = {}
         for size, dt, var in keys:
@@ -88,8 +99,11 @@ class HostPool:
             self.images[(size, dt, var)] = torch.from_numpy(np.ascontiguousarray(img)).pin_memory()
         for size, dt in sorted({(r.size, r.dtype) for r in trace}):
             odt = torch.uint8 if dt == "u8" else torch.float32
-            for _ in range(outputs_per_class):
-                self.outpool.put(torch.empty((size[1], size[0]), dtype=odt).pin_memory())
+            idt = torch.uint8 if dt == "u8" else torch.float16
+            for _ in range(buffers_per_class):
+                self.outpool.put(self.outpool.new((size[1], size[0]), odt))
+                self.devpool.put(self.devpool.new((size[1], size[0]), odt))
+                self.devpool.put(self.devpool.new((size[1], size[0], 3), idt))
 
     def host_input(self, r: Request):
         return self.images[(r.size, r.dtype, r.variant)]
@@ -120,6 +134,7 @@ class ServeResult:
     max_inflight_bytes: int
     outputs: dict | None       # rid -> host tensor, when kept
     sizes: list | None = None  # per request (width, height), in request order
+    queue_s: np.ndarray | None = None  # per request: arrival to launch of its batch
 
     def summary(self) -> dict:
         lat = self.latency_s * 1e3
@@ -127,6 +142,12 @@ class ServeResult:
                "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
                "gpix_s": self.pixels / self.makespan_s / 1e9, "makespan_s": self.makespan_s,
                "batches": self.batches, "max_inflight_gb": self.max_inflight_bytes / 1e9}
+        if self.queue_s is not None:
+            q = self.queue_s * 1e3
+            out["queue_p50_ms"] = float(np.percentile(q, 50))
+            out["queue_p99_ms"] = float(np.percentile(q, 99))
+        out["p999_ms"] = float(np.percentile(lat, 99.9))
+        out["max_ms"] = float(lat.max())
         if self.sizes:
             per = {}
             for sz in sorted(set(self.sizes)):
@@ -153,8 +174,10 @@ def serve_batched(trace, pool: HostPool, budget_bytes: int = 16 << 30, n_streams
     dev = torch.device(device or "cuda")
     streams = [torch.cuda.Stream(device=dev) for _ in range(n_streams)]
     wss = [_abi.Workspace(device=dev) for _ in range(n_streams)]
+    for w in wss:
+        w.get(128 << 20)  # sized up front: growing it inside the loop would allocate
     inflight_per_stream = [0] * n_streams
-    outpool = pool.outpool
+    outpool, devpool = pool.outpool, pool.devpool
     pending = collections.deque(sorted(trace, key=lambda r: r.t_arrive))
     waiting = collections.deque()
     inflight = []  # (event, stream index, [(req, x, y, host_out)], bytes)
@@ -162,7 +185,11 @@ def serve_batched(trace, pool: HostPool, budget_bytes: int = 16 << 30, n_streams
     outputs = {} if keep_outputs else None
     used = peak = 0
     batches = 0
+    queued = {}
     torch.cuda.synchronize(dev)
+    gc_was = gc.isenabled()
+    gc.collect()
+    gc.disable()  # a collection pause would stall every request in flight
     t0 = time.perf_counter()
     while pending or waiting or inflight:
         now = time.perf_counter() - t0
@@ -178,6 +205,8 @@ def serve_batched(trace, pool: HostPool, budget_bytes: int = 16 << 30, n_streams
                     if keep_outputs:
                         outputs[r.rid] = ho.clone()
                     outpool.put(ho)
+                    devpool.put(x)
+                    devpool.put(y)
                 used -= nbytes
                 inflight_per_stream[si] -= 1
             else:
@@ -193,15 +222,18 @@ def serve_batched(trace, pool: HostPool, budget_bytes: int = 16 << 30, n_streams
             admitted.append((waiting.popleft(), need))
         peak = max(peak, used)
         if admitted:
+            t_launch = time.perf_counter() - t0
+            for r, _ in admitted:
+                queued[r.rid] = t_launch - r.t_arrive
             si = min(range(n_streams), key=lambda k: inflight_per_stream[k])
             s = streams[si]
             with torch.cuda.stream(s):
                 items = []
                 for r, _ in admitted:
                     hx = pool.host_input(r)
-                    x = torch.empty(hx.shape, dtype=hx.dtype, device=dev)
+                    x = devpool.get(hx.shape, hx.dtype)
                     x.copy_(hx, non_blocking=True)
-                    y = torch.empty(hx.shape[:2], dtype=out_dtype(r), device=dev)
+                    y = devpool.get(hx.shape[:2], out_dtype(r))
                     items.append((r, x, y, outpool.get(tuple(hx.shape[:2]), out_dtype(r))))
                 for op in ("global", "local"):
                     sel = [(x, y) for r, x, y, _ in items if r.op == op]
@@ -220,10 +252,13 @@ def serve_batched(trace, pool: HostPool, budget_bytes: int = 16 << 30, n_streams
             _wait_until(t0 + pending[0].t_arrive)
         else:
             time.sleep(2e-5)
+    if gc_was:
+        gc.enable()
     makespan = max(r.t_arrive + lat[r.rid] for r in trace) - min(r.t_arrive for r in trace)
     order = sorted(trace, key=lambda r: r.rid)
     return ServeResult(np.array([lat[r.rid] for r in order]), makespan,
-                       sum(r.size[0] * r.size[1] for r in trace), batches, peak, outputs, [r.size for r in order])
+                       sum(r.size[0] * r.size[1] for r in trace), batches, peak, outputs, [r.size for r in order],
+                       np.array([queued[r.rid] for r in order]))
 
 
 def serve_serial(trace, pool: HostPool, keep_outputs: bool = False, device=None) -> ServeResult:
@@ -232,26 +267,37 @@ def serve_serial(trace, pool: HostPool, keep_outputs: bool = False, device=None)
     import torch
     dev = torch.device(device or "cuda")
     ws = _abi.Workspace(device=dev)
-    outpool = pool.outpool
+    ws.get(128 << 20)
+    outpool, devpool = pool.outpool, pool.devpool
     lat = {}
     outputs = {} if keep_outputs else None
     torch.cuda.synchronize(dev)
+    gc_was = gc.isenabled()
+    gc.collect()
+    gc.disable()
+    queued = {}
     t0 = time.perf_counter()
     for r in sorted(trace, key=lambda q: q.t_arrive):
         _wait_until(t0 + r.t_arrive)
+        queued[r.rid] = time.perf_counter() - t0 - r.t_arrive
         hx = pool.host_input(r)
-        x = torch.empty(hx.shape, dtype=hx.dtype, device=dev)
+        x = devpool.get(hx.shape, hx.dtype)
         x.copy_(hx, non_blocking=True)
-        y = torch.empty(hx.shape[:2], dtype=out_dtype(r), device=dev)
+        y = devpool.get(hx.shape[:2], out_dtype(r))
         _abi.PreparedCall(r.op, x, y, workspace=ws)()
         ho = outpool.get(tuple(hx.shape[:2]), out_dtype(r))
         ho.copy_(y, non_blocking=True)
         torch.cuda.current_stream(dev).synchronize()
+        devpool.put(x)
+        devpool.put(y)
         lat[r.rid] = time.perf_counter() - t0 - r.t_arrive
         if keep_outputs:
             outputs[r.rid] = ho.clone()
         outpool.put(ho)
+    if gc_was:
+        gc.enable()
     makespan = max(r.t_arrive + lat[r.rid] for r in trace) - min(r.t_arrive for r in trace)
     order = sorted(trace, key=lambda r: r.rid)
     return ServeResult(np.array([lat[r.rid] for r in order]), makespan,
-                       sum(r.size[0] * r.size[1] for r in trace), len(trace), 0, outputs, [r.size for r in order])
+                       sum(r.size[0] * r.size[1] for r in trace), len(trace), 0, outputs, [r.size for r in order],
+                       np.array([queued[r.rid] for r in order]))
