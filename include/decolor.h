@@ -247,6 +247,13 @@ DC_API int dc_debug_read_profile(const void* ws, int32_t n_img, uint64_t* out, v
 /* Number of kernels the last successful call on this thread enqueued. */
 DC_API int dc_last_launch_count(void);
 
+/* Bounds-checked build (compiled with -DDC_BOUNDS_CHECK): *checked = 1 and *flags =
+ * the OR of the buffers some kernel tried to access outside (1 input, 2 output,
+ * 4 plane, 8 workspace) since the last read, which clears them; such accesses were
+ * skipped.  Other builds: *checked = 0, *flags = 0.  Synchronous (reads device
+ * memory).  The paper has no counterpart. */
+DC_API int dc_debug_bounds(uint32_t* flags, int32_t* checked);
+
 /* ABI version (major * 100 + minor). */
 DC_API int dc_version(void);
 

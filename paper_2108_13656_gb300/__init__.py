@@ -22,6 +22,7 @@ from ._abi import (  # noqa: F401
     DcError,
     PreparedCall,
     Workspace,
+    debug_bounds,
     debug_profile,
     decolorize,
     decolorize_tonemap_global,

@@ -82,6 +82,7 @@ _SIGS = {
     "dc_debug_profile": (ctypes.c_int, [ctypes.c_int32]),
     "dc_debug_read_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "dc_last_launch_count": (ctypes.c_int, []),
+    "dc_debug_bounds": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "dc_version": (ctypes.c_int, []),
 }
 
@@ -369,6 +370,16 @@ def read_profile(workspace, n_img: int = 1, stream=None) -> dict:
 
 def last_launch_count() -> int:
     return int(load().dc_last_launch_count())
+
+
+def debug_bounds() -> tuple[bool, int]:
+    """(built with bounds checks, flags of buffers accessed out of bounds since the last read)."""
+    flags = ctypes.c_uint32(0)
+    checked = ctypes.c_int32(0)
+    rc = load().dc_debug_bounds(ctypes.byref(flags), ctypes.byref(checked))
+    if rc != DC_OK:
+        raise DcError(rc, "dc_debug_bounds")
+    return bool(checked.value), int(flags.value)
 
 
 def parse_stats(buf, n: int) -> list[dict]:

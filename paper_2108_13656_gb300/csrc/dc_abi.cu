@@ -216,8 +216,8 @@ void make_geometry(const dc_image_in& in, const dc_image_out& out, const OpArgs&
 
 template <int CAP>
 int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::vector<int>& idx, bool plane,
-                     bool allow_u8_plane, const dc_decolor_params* p, const OpArgs& op, uint8_t* ws, bool first,
-                     int64_t* need, void* stream, bool launch)
+                     bool allow_u8_plane, const dc_decolor_params* p, const OpArgs& op, uint8_t* ws,
+                     int64_t ws_bytes_total, bool first, int64_t* need, void* stream, bool launch)
 {
     const int n = (int)idx.size();
     const int in_dt = in[idx[0]].dtype;
@@ -323,6 +323,7 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
         return DC_OK;
     }
     b->ws = ws;
+    b->ws_bytes = ws_bytes_total;
     b->err = reinterpret_cast<uint32_t*>(ws);
     b->ctrl = reinterpret_cast<DcCtrl*>(ws + kHeaderBytes);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -426,11 +427,11 @@ int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_deco
             int64_t* nd = &need[with_plane];
             int r2;
             if (cnt <= kCapSmall)
-                r2 = build_and_launch<kCapSmall>(in, outs, pl.idx, pl.plane, a, p, op, nullptr, false, nd, nullptr, false);
+                r2 = build_and_launch<kCapSmall>(in, outs, pl.idx, pl.plane, a, p, op, nullptr, 0, false, nd, nullptr, false);
             else if (cnt <= kCapMid)
-                r2 = build_and_launch<kCapMid>(in, outs, pl.idx, pl.plane, a, p, op, nullptr, false, nd, nullptr, false);
+                r2 = build_and_launch<kCapMid>(in, outs, pl.idx, pl.plane, a, p, op, nullptr, 0, false, nd, nullptr, false);
             else
-                r2 = build_and_launch<kCapLarge>(in, outs, pl.idx, pl.plane, a, p, op, nullptr, false, nd, nullptr, false);
+                r2 = build_and_launch<kCapLarge>(in, outs, pl.idx, pl.plane, a, p, op, nullptr, 0, false, nd, nullptr, false);
             if (r2 != DC_OK) return r2;
         }
     }
@@ -448,11 +449,11 @@ int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_deco
         uint8_t* w = static_cast<uint8_t*>(ws);
         int r2;
         if (cnt <= kCapSmall)
-            r2 = build_and_launch<kCapSmall>(in, out, pl.idx, pl.plane, use_planes, p, op, w, first, &dummy, stream, true);
+            r2 = build_and_launch<kCapSmall>(in, out, pl.idx, pl.plane, use_planes, p, op, w, (int64_t)ws_bytes, first, &dummy, stream, true);
         else if (cnt <= kCapMid)
-            r2 = build_and_launch<kCapMid>(in, out, pl.idx, pl.plane, use_planes, p, op, w, first, &dummy, stream, true);
+            r2 = build_and_launch<kCapMid>(in, out, pl.idx, pl.plane, use_planes, p, op, w, (int64_t)ws_bytes, first, &dummy, stream, true);
         else
-            r2 = build_and_launch<kCapLarge>(in, out, pl.idx, pl.plane, use_planes, p, op, w, first, &dummy, stream, true);
+            r2 = build_and_launch<kCapLarge>(in, out, pl.idx, pl.plane, use_planes, p, op, w, (int64_t)ws_bytes, first, &dummy, stream, true);
         if (r2 != DC_OK) return r2;
         first = false;
     }
@@ -596,6 +597,17 @@ DC_API int dc_debug_read_profile(const void* ws, int32_t n_img, uint64_t* out, v
 }
 
 DC_API int dc_last_launch_count(void) { return g_last_launches; }
+
+DC_API int dc_debug_bounds(uint32_t* flags, int32_t* checked)
+{
+    if (!flags || !checked) return DC_ERR_INVALID_ARG;
+    uint32_t f[3] = {0u, 0u, 0u};
+    const int r0 = bounds_u8(&f[0]), r1 = bounds_f16(&f[1]), r2 = bounds_f32(&f[2]);
+    if (r0 == DC_ERR_CUDA || r1 == DC_ERR_CUDA || r2 == DC_ERR_CUDA) return DC_ERR_CUDA;
+    *checked = r0 == DC_OK ? 1 : 0;
+    *flags = f[0] | f[1] | f[2];
+    return DC_OK;
+}
 
 DC_API int dc_version(void) { return 100; }
 

@@ -34,6 +34,26 @@ template <> struct InT<DC_F32> { static constexpr int G = 4; static constexpr in
 
 enum OpKind { OPK_DECOLOR = 0, OPK_GLOBAL = 1, OPK_LOCAL = 2 };
 
+// ---------------------------------------------------- bounds-checked build ---
+// Built with -DDC_BOUNDS_CHECK, every global access of the pass kernels is checked
+// against the extent of the buffer it targets (input, output, plane, workspace); an
+// access outside is skipped (a load gives 0) and a bit is set in a per-library flag
+// word that dc_debug_bounds reads.  It stands in for a memory checker: tests run the
+// odd shapes, strides and batches through such a build and expect no flag.
+enum : uint32_t { BC_IN = 1u, BC_OUT = 2u, BC_PLANE = 4u, BC_WS = 8u };
+#ifdef DC_BOUNDS_CHECK
+static __device__ unsigned int g_bounds_flags;
+__device__ __forceinline__ bool bc_ok(const void* p, int64_t bytes, const void* base, int64_t extent, uint32_t bit)
+{
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p), b0 = reinterpret_cast<uintptr_t>(base);
+    const bool ok = a >= b0 && bytes >= 0 && a + (uintptr_t)bytes <= b0 + (uintptr_t)extent;
+    if (!ok) atomicOr(&g_bounds_flags, bit);
+    return ok;
+}
+#else
+__device__ __forceinline__ bool bc_ok(const void*, int64_t, const void*, int64_t, uint32_t) { return true; }
+#endif
+
 // ------------------------------------------------------------ memory access ---
 // Input pixels: read-only for the whole launch, so the loads may be scheduled
 // freely (not volatile); no L1 allocation, normal L2 caching.
@@ -352,6 +372,21 @@ struct GroupIO {
         }
     }
 
+    // Bytes each buffer of an image spans (for the bounds-checked build).
+    __device__ static __forceinline__ int64_t in_extent(const DcImage& im)
+    {
+        return (int64_t)(im.rows - 1) * im.in_stride + (int64_t)im.cols * 3 * ESZ;
+    }
+    __device__ static __forceinline__ int64_t plane_extent(const DcImage& im)
+    {
+        return (int64_t)(im.rows - 1) * im.plane_stride + (int64_t)im.cols * 4;
+    }
+    __device__ static __forceinline__ int64_t out_extent(const DcImage& im)
+    {
+        const int oe = im.out_dt == DC_U8 ? 1 : (im.out_dt == DC_F16 ? 2 : 4);
+        return (int64_t)(im.rows - 1) * im.out_stride + (int64_t)im.cols * oe;
+    }
+
     // The raw bytes of a full, aligned group: 24 (u8, three 8-byte loads) or 48
     // (f16, f32, three 16-byte loads).
     // With a plane kept for later passes (f16/f32 input), the input is read only
@@ -359,6 +394,11 @@ struct GroupIO {
     __device__ static __forceinline__ void load_raw(const DcImage& im, int r, int c, uint32_t (&w)[12])
     {
         const uint8_t* p = im.in + (int64_t)r * im.in_stride + (int64_t)c * 3 * ESZ;
+        if (!bc_ok(p, 3 * G * ESZ, im.in, in_extent(im), BC_IN)) {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) w[k] = 0u;
+            return;
+        }
         if constexpr (IN_DT == DC_U8) {
             const uint2 a = ld_stream8(p), b = ld_stream8(p + 8), d = ld_stream8(p + 16);
             w[0] = a.x; w[1] = a.y; w[2] = b.x; w[3] = b.y; w[4] = d.x; w[5] = d.y;
@@ -387,8 +427,9 @@ struct GroupIO {
             load_raw(im, r, c, w);
             decode(w, be, Lv);
         } else {
+            const bool ok = bc_ok(p, (int64_t)n * 3 * ESZ, im.in, in_extent(im), BC_IN);
 #pragma unroll
-            for (int k = 0; k < G; ++k) Lv[k] = (k < n) ? scalar_luminance(p + k * 3 * ESZ, be) : 0.0f;
+            for (int k = 0; k < G; ++k) Lv[k] = (ok && k < n) ? scalar_luminance(p + k * 3 * ESZ, be) : 0.0f;
         }
     }
 
@@ -411,6 +452,11 @@ struct GroupIO {
     __device__ static void from_plane(const DcImage& im, int r, int c, int n, bool vec, float (&Lv)[G])
     {
         const float* p = reinterpret_cast<const float*>(im.plane + (int64_t)r * im.plane_stride) + c;
+        if (!bc_ok(p, (int64_t)(vec ? G : n) * 4, im.plane, plane_extent(im), BC_PLANE)) {
+#pragma unroll
+            for (int k = 0; k < G; ++k) Lv[k] = 0.0f;
+            return;
+        }
         if (vec) {
 #pragma unroll
             for (int k = 0; k < G; k += 4) {
@@ -431,6 +477,7 @@ struct GroupIO {
                                                        const float (&y)[G])
     {
         float* p = reinterpret_cast<float*>(im.plane + (int64_t)r * im.plane_stride) + c;
+        if (!bc_ok(p, (int64_t)(vec ? G : n) * 4, im.plane, plane_extent(im), BC_PLANE)) return;
         if (vec) {
             const unsigned long long pol = policy_evict_last();
 #pragma unroll
@@ -446,6 +493,10 @@ struct GroupIO {
     __device__ static void store(const DcImage& im, int r, int c, int n, bool vec, const float (&y)[G])
     {
         uint8_t* base = im.out + (int64_t)r * im.out_stride;
+        {
+            const int oe = im.out_dt == DC_U8 ? 1 : (im.out_dt == DC_F16 ? 2 : 4);
+            if (!bc_ok(base + (int64_t)c * oe, (int64_t)(vec ? G : n) * oe, im.out, out_extent(im), BC_OUT)) return;
+        }
         if (im.out_dt == DC_U8) {
             uint8_t* p = base + c;
             if (vec) {

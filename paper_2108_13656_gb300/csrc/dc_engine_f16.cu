@@ -13,4 +13,9 @@ int occupancy_f16(int cap, int opk, int kind, bool pl)
     return occupancy_dispatch<DC_F16>(cap, opk, kind, pl);
 }
 
+int bounds_f16(uint32_t* flags)
+{
+    return bounds_take<DC_F16>(flags);
+}
+
 }  // namespace dc

@@ -13,4 +13,9 @@ int occupancy_f32(int cap, int opk, int kind, bool pl)
     return occupancy_dispatch<DC_F32>(cap, opk, kind, pl);
 }
 
+int bounds_f32(uint32_t* flags)
+{
+    return bounds_take<DC_F32>(flags);
+}
+
 }  // namespace dc

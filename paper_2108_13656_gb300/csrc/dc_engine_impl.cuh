@@ -608,7 +608,8 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
         const int blk = k / B, j = k - blk * B;
         const unsigned long long fprev = j > 0 ? S.fs[k - 1] : 0u;
         const unsigned long long h = ((unsigned long long)S.cnt[k] << 20) - S.fs[k] + fprev;
-        H[((size_t)I * im.Wb + (J0 + blk)) * B + j] = h;
+        unsigned long long* q = &H[((size_t)I * im.Wb + (J0 + blk)) * B + j];
+        if (bc_ok(q, 8, P.ws, P.ws_bytes, BC_WS)) *q = h;
     }
 }
 
@@ -630,7 +631,10 @@ __device__ void tile_cdf(const DcBatch<CAP>& P, const DcImage& im, int I, const 
         const int jj = lo + k / B, j = k % B;
         unsigned long long v = 0ull;
 #pragma unroll 5
-        for (int I2 = i0; I2 <= i1; ++I2) v += ld_cg_u64(&H[((size_t)I2 * Wb + jj) * B + j]);  // loads issued together
+        for (int I2 = i0; I2 <= i1; ++I2) {  // loads issued together
+            const unsigned long long* q = &H[((size_t)I2 * Wb + jj) * B + j];
+            v += bc_ok(q, 8, P.ws, P.ws_bytes, BC_WS) ? ld_cg_u64(q) : 0ull;
+        }
         S.v[k] = v;
     }
     cta_sync();
@@ -650,6 +654,7 @@ __device__ void tile_cdf(const DcBatch<CAP>& P, const DcImage& im, int I, const 
         }
         const unsigned long long total = __shfl_sync(0xffffffffu, w, 31);
         float* e = E + ((size_t)I * Wb + J) * (B + 1);
+        if (!bc_ok(e, (int64_t)(B + 1) * 4, P.ws, P.ws_bytes, BC_WS)) continue;
         if (lane < B) e[lane + 1] = __ull2float_rn(w) / __ull2float_rn(total);
         if (lane == 0) e[0] = 0.0f;
     }
@@ -681,7 +686,8 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
         const int I2 = min(max(I - 1 + sr, 0), Hb - 1);
         const int J2 = min(max(J0 - 1 + sc, 0), Wb - 1);
         const float* e = E + ((size_t)I2 * Wb + J2) * B1 + j;
-        const float e0 = ld_cg_f(e), e1 = ld_cg_f(e + 1);
+        const bool ok = bc_ok(e, 8, P.ws, P.ws_bytes, BC_WS);
+        const float e0 = ok ? ld_cg_f(e) : 0.0f, e1 = ok ? ld_cg_f(e + 1) : 0.0f;
         S.tab[slot * SB + j] = make_float2(e0, e1 - e0);
     }
     // bilinear geometry: nominal block centres ((J + 1/2) s); a pixel at x + 1/2
@@ -909,6 +915,24 @@ int occupancy_dispatch(int cap, int opk, int kind, bool pl)
     DC_FOR_EACH_PASS(DC_CASE)
 #undef DC_CASE
     return 0;
+}
+
+// Bounds-check flags of this translation unit's kernels (read and cleared); -1 when
+// the library was built without checks.
+template <int IN_DT>
+int bounds_take(uint32_t* flags)
+{
+#ifdef DC_BOUNDS_CHECK
+    unsigned int v = 0u, z = 0u;
+    if (cudaMemcpyFromSymbol(&v, g_bounds_flags, sizeof(v)) != cudaSuccess ||
+        cudaMemcpyToSymbol(g_bounds_flags, &z, sizeof(z)) != cudaSuccess)
+        return DC_ERR_CUDA;
+    *flags = v;
+    return DC_OK;
+#else
+    *flags = 0u;
+    return -1;
+#endif
 }
 
 // The batch descriptor travels in kernel parameter space (limit 32764 bytes).

@@ -13,4 +13,9 @@ int occupancy_u8(int cap, int opk, int kind, bool pl)
     return occupancy_dispatch<DC_U8>(cap, opk, kind, pl);
 }
 
+int bounds_u8(uint32_t* flags)
+{
+    return bounds_take<DC_U8>(flags);
+}
+
 }  // namespace dc

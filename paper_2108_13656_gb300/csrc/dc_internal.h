@@ -123,6 +123,7 @@ struct DcBatch {
     uint32_t* err;                     // call-level error word (workspace header)
     dc_global_stats* stats;            // nullable; indexed by img_stats_index
     uint8_t* ws;
+    int64_t ws_bytes;                  // workspace size (bounds-checked build)
     int32_t stats_index[CAP];
     DcImage img[CAP];
     int32_t reverse[kMaxPhases];         // hand a pass's tiles out last-first (L2 reuse)
@@ -148,6 +149,9 @@ int launch_engine_f32(const void* batch, int cap, int opk, int kind, int ph, boo
 int occupancy_u8(int cap, int opk, int kind, bool pl);
 int occupancy_f16(int cap, int opk, int kind, bool pl);
 int occupancy_f32(int cap, int opk, int kind, bool pl);
+int bounds_u8(uint32_t* flags);   // bounds-check flags per translation unit (-1: not built with checks)
+int bounds_f16(uint32_t* flags);
+int bounds_f32(uint32_t* flags);
 
 // Smallest workspace a call accepts (without the optional 8-bit plane); 0 on error.
 size_t workspace_min_bytes(int32_t op, const dc_image_in* in, int32_t n, const void* op_params);
