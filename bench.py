@@ -6,8 +6,10 @@ Workload (one "step"): the 3840x2160 image in its two variants - 8-bit sRGB
 (S-HDR, mu = 0, sigma = 2.5, seed 2) - each through decolorize -> global
 centred-sigmoid tone map and decolorize -> local smoothed-LHE tone map, i.e. four
 C-ABI calls per step and every step of the hot path.  Inputs are synthetic and
-resident in HBM before timing; L2 is flushed (a 256 MiB write) before every timed
-call and each call is timed with CUDA events on its stream.
+resident in HBM before timing.  `value` times K steps back to back between two CUDA
+events, rotating through 8 copies of every input and output so that no step finds
+its data in L2; the per-call breakdown and the roofline time each call alone
+between two events after a 256 MiB L2-flushing write.
 
 Prints ONE JSON line (rank 0).  `value` is whole-job Gpix/s (output pixels of all
 four calls, all ranks) over device time; `e2e` repeats the step through the public
@@ -34,6 +36,7 @@ W, H = 3840, 2160
 NPIX = W * H
 METRIC = "Gpix/s and % of HBM roofline"
 L2_FLUSH_BYTES = 256 << 20
+ROT = 8  # input / output sets the steady-state loop rotates through
 OPS = [  # (name, input variant, operation, output dtype, algorithmic bytes per pixel)
     ("u8_global", "u8", "global", "u8", 3 + 1),
     ("f32_global", "f32", "global", "f32", 12 + 4),
@@ -402,19 +405,26 @@ def run_native(args):
     dev = torch.device("cuda", local)
     dc.load()
     imgs = make_inputs()
-    x = {k: torch.from_numpy(v).to(dev) for k, v in imgs.items()}
-    outs = {}
+    # ROT copies of every input and output: consecutive steps of the steady-state loop
+    # touch different buffers (8 x 166 MB, far above L2), so no step finds the previous
+    # one's data in L2 and no flush is needed between them
+    xs = {k: [torch.from_numpy(v).to(dev) for _ in range(ROT)] for k, v in imgs.items()}
+    x = {k: v[0] for k, v in xs.items()}
+    outs_r = {}
     for name, var, op, odt, _ in OPS:
-        outs[name] = torch.empty((H, W), dtype=torch.uint8 if odt == "u8" else torch.float32, device=dev)
-    ws = dc.Workspace(device=dev)
+        outs_r[name] = [torch.empty((H, W), dtype=torch.uint8 if odt == "u8" else torch.float32, device=dev)
+                        for _ in range(ROT)]
+    outs = {name: v[0] for name, v in outs_r.items()}
+    wss = {name: dc.Workspace(device=dev) for name, *_ in OPS}
+    ws = wss[OPS[0][0]]
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    calls = {}
+    calls_r = {}
     for name, var, op, _, _ in OPS:
-        if op == "global":
-            calls[name] = dc.PreparedCall("global", x[var], outs[name], mode="sigmoid", workspace=ws)
-        else:
-            calls[name] = dc.PreparedCall("local", x[var], outs[name], workspace=ws)
+        kw = {"mode": "sigmoid"} if op == "global" else {}
+        calls_r[name] = [dc.PreparedCall(op, xs[var][r], outs_r[name][r], workspace=wss[name], **kw)
+                         for r in range(ROT)]
+    calls = {name: v[0] for name, v in calls_r.items()}
 
     def call(name, var, op, out):
         calls[name]()
@@ -422,10 +432,11 @@ def run_native(args):
     clocks = ClockSampler(local)
     clocks.start()
     for _ in range(max(3, args.warmup)):
-        for name, var, op, _, _ in OPS:
-            call(name, var, op, outs[name])
+        for r in range(ROT):
+            for name, *_ in OPS:
+                calls_r[name][r]()
     torch.cuda.synchronize()
-    assert dc.query_status(ws) == 0
+    assert all(dc.query_status(w) == 0 for w in wss.values())
     # keep the device busy while the samplers start
     t_end = time.perf_counter() + args.busy_s
     while time.perf_counter() < t_end:
@@ -433,29 +444,44 @@ def run_native(args):
             call(name, var, op, outs[name])
         torch.cuda.synchronize()
 
+    # steady state: K steps back to back on rotating buffers, one pair of events
     K = args.steps
-    ev = {name: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-          for name, *_ in OPS}
     launches = 0
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     torch.cuda._sleep(20_000_000)  # let the host queue run ahead of the device
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
     for k in range(K):
-        for name, var, op, _, _ in OPS:
-            flush.fill_(k & 0xFF)  # evict L2 (256 MiB write), outside the timed pair
-            s, e = ev[name][k]
-            s.record(stream)
-            call(name, var, op, outs[name])
-            e.record(stream)
+        r = k % ROT
+        for name, *_ in OPS:
+            calls_r[name][r]()
             launches += dc.last_launch_count()
+    e1.record(stream)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
+    step_ms = e0.elapsed_time(e1) / K
+
+    # per call, for the roofline and the breakdown: L2 flushed (256 MiB write) before
+    # each call, the call alone between two events
+    KC = min(K, 200)
+    ev = {name: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(KC)]
+          for name, *_ in OPS}
+    torch.cuda._sleep(20_000_000)
+    for k in range(KC):
+        for name, var, op, _, _ in OPS:
+            flush.fill_(k & 0xFF)
+            s0, s1 = ev[name][k]
+            s0.record(stream)
+            call(name, var, op, outs[name])
+            s1.record(stream)
+    torch.cuda.synchronize()
     clk = clocks.stop()
-    op_ms = {name: float(np.mean([s.elapsed_time(e) for s, e in ev[name]])) for name, *_ in OPS}
-    step_ms = sum(op_ms.values())
-    assert dc.query_status(ws) == 0
+    op_ms = {name: float(np.mean([a.elapsed_time(b) for a, b in ev[name]])) for name, *_ in OPS}
+    assert all(dc.query_status(w) == 0 for w in wss.values())
 
     def reduce_max(v):
         if world == 1:
@@ -508,7 +534,12 @@ def run_native(args):
         "metric": METRIC, "value": gpix, "unit": "Gpix/s", "n_gpus": world, "steps": K,
         "warmup": max(3, args.warmup), "ms_per_step": t_max, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "pixels_per_step": 4 * NPIX, "l2": "flushed (256 MiB write) before every timed call",
+        "config": {"workload": WORKLOAD, "pixels_per_step": 4 * NPIX,
+                   "l2": "value: steps back to back over %d rotating input/output sets (%.2f GB, far above L2); "
+                         "per_op and roofline: each call alone after a 256 MiB L2-flushing write" % (
+                             ROT, ROT * (sum(v.nbytes for v in imgs.values()) +
+                                         sum(t.numel() * t.element_size() for t in outs.values())) / 1e9),
+                   "per_op_sum_ms": sum(op_ms.values()),
                    "parallelism": "replicas" if world > 1 else "single GPU", "per_op": per_op},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,

@@ -219,6 +219,19 @@ DC_API size_t dc_workspace_bytes(int32_t op, const dc_image_in* in, int32_t n,
 DC_API size_t dc_workspace_min_bytes(int32_t op, const dc_image_in* in, int32_t n,
                                      const void* op_params);
 
+/* Registers a workspace kept for calls of this library only: zeroes its ws_bytes
+ * (on `stream`, then synchronises it, once) and remembers the address.  Calls on a
+ * registered workspace clear their control block at the end of their last pass, so
+ * a call whose control block is no larger than the previous call's needs no
+ * clearing memset before its first pass (one stream operation fewer per call).
+ * Until dc_workspace_release the caller must neither write to that memory nor free
+ * it, and only one call at a time may use it.  Returns DC_ERR_WORKSPACE for a NULL
+ * or misaligned pointer or fewer than 256 bytes.  The paper has no counterpart. */
+DC_API int dc_workspace_prepare(void* ws, size_t ws_bytes, void* stream);
+
+/* Forgets a registered workspace (before its memory is freed or reused). */
+DC_API int dc_workspace_release(void* ws);
+
 /* Synchronises `stream`, then reads the device-side error word of workspace `ws`
  * (reserved for device-detected errors; the current kernels never wait on each
  * other and report DC_OK).  Returns DC_ERR_CUDA if the copy fails. */

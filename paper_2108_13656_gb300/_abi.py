@@ -75,6 +75,8 @@ _SIGS = {
                                                             ctypes.c_void_p]),
     "dc_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "dc_workspace_min_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "dc_workspace_prepare": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
+    "dc_workspace_release": (ctypes.c_int, [ctypes.c_void_p]),
     "dc_query_status": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "dc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "dc_set_tuning": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
@@ -192,23 +194,43 @@ def _stream_handle(stream):
 class Workspace:
     """Device workspace owned by torch's allocator (256-byte aligned): grown on demand
     to what each call asks for, or, when created with `nbytes`, exactly that size and
-    never grown (a call then keeps its optional planes only if they fit)."""
+    never grown (a call then keeps its optional planes only if they fit).  Each buffer
+    is registered with dc_workspace_prepare (calls keep its control block clean, no
+    per-call clearing memset) and released before it is dropped."""
 
     def __init__(self, device=None, nbytes: int | None = None):
         self.device = device
         self.buf = None
         self.fixed = nbytes is not None
         if self.fixed:
-            self.buf = _torch().empty(max(int(nbytes), 256), dtype=_torch().uint8, device=device or "cuda")
+            self._set(_torch().empty(max(int(nbytes), 256), dtype=_torch().uint8, device=device or "cuda"))
+
+    def _set(self, buf):
+        lib = load()
+        if self.buf is not None:
+            _torch().cuda.synchronize(self.buf.device)  # calls on the old buffer end first
+            lib.dc_workspace_release(ctypes.c_void_p(self.buf.data_ptr()))
+        self.buf = buf
+        with _torch().cuda.device(buf.device):
+            rc = lib.dc_workspace_prepare(ctypes.c_void_p(buf.data_ptr()), buf.numel(), _stream_handle(None))
+        if rc != DC_OK:
+            raise DcError(rc, "dc_workspace_prepare")
 
     def get(self, nbytes: int):
         torch = _torch()
         nbytes = max(int(nbytes), 256)
         if not self.fixed and (self.buf is None or self.buf.numel() < nbytes):
-            self.buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device or "cuda")
+            self._set(torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device or "cuda"))
         ptr = self.buf.data_ptr()
         assert ptr % 256 == 0
         return ptr, self.buf.numel()
+
+    def __del__(self):
+        try:
+            if self.buf is not None and _lib is not None:
+                _lib.dc_workspace_release(ctypes.c_void_p(self.buf.data_ptr()))
+        except Exception:
+            pass
 
 
 _default_ws: dict = {}

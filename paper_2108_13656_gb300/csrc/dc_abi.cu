@@ -8,6 +8,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "dc_internal.h"
@@ -35,6 +36,38 @@ dc_tuning g_tune[3][3] = {
     {{256, 32, 512, 0}, {256, 32, 512, 0}, {256, 32, 512, 0}},
 };
 constexpr int kAutoCtasPerSm = 4;  // resident CTAs of a pass kernel (launch bounds)
+
+// Workspaces registered with dc_workspace_prepare.  A call's control block (header
+// and per-launch / per-image records at the start of the workspace) must be zero
+// when its first pass starts.  For each registered workspace the host tracks how
+// many leading bytes are zero between calls: a call whose control block lies inside
+// that prefix needs no clearing memset, and its last pass clears the block again.
+// The bytes after a call's control block (histograms, curves, planes) are left
+// dirty, so afterwards the clean prefix ends with the block; a profiled call leaves
+// its counters for reading (prefix 0 until a later call clears it).
+struct CleanWs {
+    size_t bytes;  // registered size
+    size_t clean;  // leading bytes known to be zero between calls
+};
+std::unordered_map<uintptr_t, CleanWs> g_clean;  // guarded by g_mu
+
+// For a call whose control block ends at `need` bytes: whether it can skip the
+// clearing memset and whether its last pass must clear the block (registered
+// workspace).  Records what the call leaves.
+void plan_clear(const void* ws, size_t need, bool profiling, bool* skip_memset, bool* clear_at_end)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_clean.find(reinterpret_cast<uintptr_t>(ws));
+    if (it == g_clean.end() || it->second.bytes < need) {
+        *skip_memset = false;
+        *clear_at_end = false;
+        if (it != g_clean.end()) it->second.clean = 0;
+        return;
+    }
+    *skip_memset = !profiling && it->second.clean >= need;
+    *clear_at_end = !profiling;
+    it->second.clean = profiling ? 0 : need;
+}
 int g_profile = 0;
 thread_local int g_last_launches = 0;
 thread_local int g_call_launches = 0;
@@ -327,11 +360,16 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
     b->err = reinterpret_cast<uint32_t*>(ws);
     b->ctrl = reinterpret_cast<DcCtrl*>(ws + kHeaderBytes);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const size_t clear_bytes = first ? (size_t)(kHeaderBytes + ctrl_bytes) : (size_t)ctrl_bytes;
-    uint8_t* clear_ptr = first ? ws : ws + kHeaderBytes;
-    if (cudaMemsetAsync(clear_ptr, 0, clear_bytes, st) != cudaSuccess) {
-        delete b;
-        return DC_ERR_CUDA;
+    bool skip_memset = false, clear_at_end = false;
+    plan_clear(ws, (size_t)(kHeaderBytes + ctrl_bytes), b->profile != 0, &skip_memset, &clear_at_end);
+    b->reset_bytes = clear_at_end ? (int32_t)ctrl_bytes : 0;
+    if (!skip_memset) {
+        const size_t clear_bytes = first ? (size_t)(kHeaderBytes + ctrl_bytes) : (size_t)ctrl_bytes;
+        uint8_t* clear_ptr = first ? ws : ws + kHeaderBytes;
+        if (cudaMemsetAsync(clear_ptr, 0, clear_bytes, st) != cudaSuccess) {
+            delete b;
+            return DC_ERR_CUDA;
+        }
     }
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
@@ -520,6 +558,24 @@ DC_API size_t dc_workspace_bytes(int32_t op, const dc_image_in* in, int32_t n, c
 DC_API size_t dc_workspace_min_bytes(int32_t op, const dc_image_in* in, int32_t n, const void* op_params)
 {
     return workspace_query(op, in, n, op_params, true);
+}
+
+DC_API int dc_workspace_prepare(void* ws, size_t ws_bytes, void* stream)
+{
+    if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255u) != 0 || ws_bytes < (size_t)kHeaderBytes) return DC_ERR_WORKSPACE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (cudaMemsetAsync(ws, 0, ws_bytes, st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+        return DC_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_clean[reinterpret_cast<uintptr_t>(ws)] = CleanWs{ws_bytes, ws_bytes};
+    return DC_OK;
+}
+
+DC_API int dc_workspace_release(void* ws)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_clean.erase(reinterpret_cast<uintptr_t>(ws));
+    return DC_OK;
 }
 
 DC_API int dc_query_status(const void* ws, void* stream)

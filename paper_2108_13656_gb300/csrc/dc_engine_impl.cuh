@@ -846,6 +846,24 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
         }
     }
     if (P.profile && threadIdx.x == 0) atomicMax(&P.ctrl->prof[PROF_KEND], globaltimer_ns());
+    // Self-clearing call: after the last pass the control block is zero again for the
+    // next call on this workspace.  Every CTA fences its work on the block and counts
+    // itself; the one that counts last clears the block, counter included.  No CTA
+    // waits for another.
+    if (P.reset_bytes > 0 && ph == P.n_phase - 1) {
+        __shared__ uint32_t s_last;
+        cta_sync();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_last = atomicAdd(&P.ctrl->done_ctas, 1u) == gridDim.x - 1 ? 1u : 0u;
+        }
+        cta_sync();
+        if (s_last) {
+            __threadfence();
+            uint4* c = reinterpret_cast<uint4*>(P.ctrl);
+            for (int i = threadIdx.x; i < P.reset_bytes / 16; i += kThreads) c[i] = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
 }
 
 template <int IN_DT, int OPK, int KIND, int CAP, bool PL>

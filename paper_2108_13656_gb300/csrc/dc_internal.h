@@ -90,7 +90,7 @@ enum ProfSlot {
 
 // Per-launch control block, cleared by the host before the launch.
 struct DcCtrl {
-    uint32_t next_tile;          // unused by the pass kernels (static schedule)
+    uint32_t done_ctas;          // CTAs of the last pass that finished (self-clearing calls)
     uint32_t pad[15];
     unsigned long long prof[PROF_SLOTS];
     uint32_t pad2[32];
@@ -119,6 +119,8 @@ struct DcBatch {
     uint32_t s_magic;                  // ceil(2^32 / block_s), 0 for block_s = 1: exact division of offsets < 2^16
     float alpha;
     uint32_t profile;                  // record phase timestamps
+    int32_t reset_bytes;               // > 0: the last pass's last CTA clears this many bytes of the
+                                       // control block (from ctrl), leaving it zero for the next call
     DcCtrl* ctrl;
     uint32_t* err;                     // call-level error word (workspace header)
     dc_global_stats* stats;            // nullable; indexed by img_stats_index

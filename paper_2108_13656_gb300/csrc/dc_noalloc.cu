@@ -30,13 +30,15 @@ std::atomic<void*> g_scratch_addr[kMaxDevices];
 
 // Device address of the scratch array on the current device (looked up once per
 // device, with that device current).
-int scratch_address(void** out)
+int scratch_address(void** out, void* stream)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return DC_ERR_CUDA;
     void* p = g_scratch_addr[dev].load(std::memory_order_acquire);
     if (p == nullptr) {
         if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) return DC_ERR_CUDA;
+        // zeroed once and registered: the calls keep their control block clean
+        if (dc_workspace_prepare(p, kScratchBytes, stream) != DC_OK) return DC_ERR_CUDA;
         g_scratch_addr[dev].store(p, std::memory_order_release);
     }
     *out = p;
@@ -54,7 +56,7 @@ extern "C" DC_API int dc_decolorize_tonemap_global_noalloc(const dc_image_in* in
     if (need == 0) return DC_ERR_INVALID_ARG;
     if (need > kScratchBytes) return DC_ERR_WORKSPACE;  // batch too large for the fixed scratch
     void* ws = nullptr;
-    const int rc = scratch_address(&ws);
+    const int rc = scratch_address(&ws, stream);
     if (rc != DC_OK) return rc;
     // the call clears the counters it uses before its first pass
     return dc_decolorize_tonemap_global(in, out, n, params, gparams, stats, ws, kScratchBytes, stream);

@@ -135,3 +135,59 @@ def test_u8_plane_changes_no_result(dc, op):
         ys.append((y.cpu(), st.cpu()))
     assert torch.equal(ys[0][0], ys[1][0])
     assert torch.equal(ys[0][1], ys[1][1])
+
+
+class _RawWorkspace:
+    """A plain device buffer that is not registered with dc_workspace_prepare (every
+    call clears its control block with a memset first)."""
+
+    def __init__(self, nbytes):
+        import torch
+        self.buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+
+    def get(self, nbytes):
+        assert nbytes <= self.buf.numel()
+        return self.buf.data_ptr(), self.buf.numel()
+
+
+def test_registered_workspace_stays_clean(dc):
+    """Calls on a registered workspace skip the clearing memset when the previous call
+    left their control block zero, and clear it again at the end.  A sequence that
+    changes sizes, batch sizes (a larger control block over a previous call's planes
+    and histograms), operations, sample types, and has a profiled call in between
+    gives the same bits and statistics as the same calls on an unregistered buffer."""
+    import torch
+    from paper_2108_13656_gb300 import synth
+    small = [synth.s_ldr(64 + 7 * i, 40 + 3 * i, 60 + i) for i in range(20)]
+    seq = [("local", [synth.s_ldr(700, 300, 6)], None),          # planes and histograms after a small block
+           ("global", small, "sigmoid"),                           # 20 images: a larger control block
+           ("global", [synth.s_ldr(640, 480, 1)], "sigmoid"),
+           ("local", [synth.s_hdr(500, 300, 2)], None),
+           ("global", [synth.s_hdr(333, 222, 3).astype(np.float16)], "histeq"),
+           ("global", [synth.s_ldr(97, 61, 4)], "histeq"),          # profiled on the registered workspace
+           ("decolorize", [synth.s_ldr(128, 64, 5)], None),
+           ("global", small[:5] + [synth.s_hdr(90, 70, 7)], "histeq"),
+           ("global", [synth.s_ldr(640, 480, 1)], "sigmoid")]
+    reg = dc.Workspace()
+    raw = _RawWorkspace(96 << 20)
+    for i, (op, imgs, mode) in enumerate(seq):
+        xs = [to_dev(im) for im in imgs]
+        res = []
+        for ws in (reg, raw):
+            ys = [torch.empty(im.shape[:2], dtype=torch.float32, device="cuda") for im in imgs]
+            st = torch.zeros(dc.STATS_BYTES * len(imgs), dtype=torch.uint8, device="cuda")
+            if i == 5 and ws is reg:
+                dc.debug_profile(True)  # this call leaves its counters for reading
+            try:
+                if op == "global":
+                    dc.PreparedCall(op, xs, ys, mode=mode, stats=st, workspace=ws)()
+                else:
+                    dc.PreparedCall(op, xs, ys, workspace=ws)()
+            finally:
+                dc.debug_profile(False)
+            torch.cuda.synchronize()
+            res.append(([y.cpu() for y in ys], st.cpu()))
+        for a, b in zip(res[0][0], res[1][0]):
+            assert torch.equal(a, b), "call %d (%s) differs" % (i, op)
+        assert torch.equal(res[0][1], res[1][1]), "call %d (%s) statistics differ" % (i, op)
+    assert dc.query_status(reg) == 0
