@@ -583,9 +583,12 @@ struct SmemCdf {
     unsigned long long v[(kCdfChunk + 2 * kMaxRadius) * DC_MAX_BINS];
 };
 constexpr int kLocMaxCols = 1024;    // widest local tile
+// Slot stride of the apply pass's curve table in (value, slope) pairs: at least B
+// and 8 (mod 16), i.e. 16 banks between neighbouring slots; at most DC_MAX_BINS + 8.
+__host__ __device__ constexpr int apply_slot_stride(int bins) { return bins + ((24 - bins % 16) % 16); }
 constexpr int kLocMaxRows = 64;      // tallest local tile (block_s)
 struct SmemApplyL {
-    float2 tab[3 * (kLocMaxBlocksX + 2) * (DC_MAX_BINS + 1)];  // per block and bin: (F at bin start, slope)
+    float2 tab[3 * (kLocMaxBlocksX + 2) * (DC_MAX_BINS + 8)];  // per block and bin: (F at bin start, slope)
     int2 col[kLocMaxCols + 16];  // per tile column: table slot offset of the left block, weight bits
     int2 row[kLocMaxRows];  // per tile row: table slot offset of the upper block row, weight bits
 };

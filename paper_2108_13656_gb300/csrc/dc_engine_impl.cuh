@@ -247,26 +247,30 @@ __device__ __forceinline__ void walk_block_patches(const DcImage& im, const Tile
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int gx = lane & (lx - 1), gy = lane >> lgx;
     const int npx = (t.c1 - t.c0 + pw - 1) / pw;
-    const int items = npx * ((t.r1 - t.r0 + ly - 1) / ly);
     const bool vec_img = (im.flags & IF_VEC) != 0;
     int c[U], n[U], rr[U];
     bool vec[U];
     float v[U][G];
     uint32_t w[U][PLANE ? 1 : 12];
-    for (int it = warp; it < items; it += U * W) {
+    // warp w takes patch columns w, w + W, ... and walks each down the tile, U
+    // patches at a time (no integer division)
+    for (int px = warp; px < npx; px += W) {
+        const int cc = t.c0 + px * pw + gx * G;
+        const int nn = max(0, min(G, t.c1 - cc));
+        const bool vv = vec_img && nn == G;
+        for (int r0 = t.r0 + gy; r0 < t.r1; r0 += U * ly) {
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int item = it + u * W;
-            const int py = item / npx, px = item - py * npx;
-            rr[u] = t.r0 + py * ly + gy;
-            c[u] = t.c0 + px * pw + gx * G;
-            n[u] = (item < items && rr[u] < t.r1) ? max(0, min(G, t.c1 - c[u])) : 0;
-            vec[u] = vec_img && n[u] == G;
-            if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, rr[u], c[u], n[u], vec[u], v[u], w[u], true);
+            for (int u = 0; u < U; ++u) {
+                rr[u] = r0 + u * ly;
+                c[u] = cc;
+                n[u] = rr[u] < t.r1 ? nn : 0;
+                vec[u] = vv;
+                if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, rr[u], c[u], n[u], vec[u], v[u], w[u], true);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u)
+                if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, rr[u], c[u], n[u], vec[u], v[u], w[u], false);
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-            if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, rr[u], c[u], n[u], vec[u], v[u], w[u], false);
     }
 }
 
@@ -677,8 +681,10 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
     const int nbx = (t.c1 - t.c0 + s - 1) / s;
     const int J0 = t.c0 / s;
     const int W2 = nbx + 2, B1 = B + 1;
-    // slots B+1 pairs apart: the same bin of neighbouring blocks falls in other banks
-    const int SB = B + 1;
+    // slot stride: SB = 8 (mod 16) pairs, so the same or a nearby bin of neighbouring
+    // blocks lands 16 banks away (lanes of a warp read neighbouring blocks' curves
+    // at similar bins)
+    const int SB = apply_slot_stride(B);
     const float* E = reinterpret_cast<const float*>(P.ws + im.ws_hist + align_up((int64_t)Hb * Wb * B * 8, 256));
     for (int k = threadIdx.x; k < 3 * W2 * B; k += kThreads) {
         const int slot = k / B, j = k - slot * B;
