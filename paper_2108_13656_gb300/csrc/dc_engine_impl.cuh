@@ -133,16 +133,18 @@ __device__ __forceinline__ Derived derive(const DcImgCtrl* ic, long long N, bool
 }
 
 // Bin coordinate t = nb u = nb (v - vmin) / R of a fixed-point log value, in units
-// of 2^-S (0 <= t <= nb): the high half of (v - vmin) 2^32 times the fixed-point
-// reciprocal m = floor(nb 2^(32+S) / Rs), i.e. floor(t 2^S) or one unit below it
-// (the reciprocal's truncation is below 2^-32 of it and v - vmin < 2^30).
+// of 2^-S (0 <= t <= nb): floor(dv m / 2^32) with dv = (v - vmin) >> sh <= Rs and
+// the fixed-point reciprocal m = floor(nb 2^(32+S) / Rs), i.e. floor(t 2^S) or one
+// unit below it (the reciprocal's truncation is below 2^-32 of it and dv < 2^30).
+// The product is at most nb 2^S < 2^31, so with m = mh 2^32 + ml it is
+// dv mh + floor(dv ml / 2^32) in 32-bit arithmetic, exactly.
 template <int S>
 __device__ __forceinline__ uint32_t bin_coord(int v, const Derived& d)
 {
     v = min(max(v, d.vmin), d.vmax);
     const uint32_t dv = ((uint32_t)v - (uint32_t)d.vmin) >> d.sh;
     const unsigned long long m = S == kLocTS ? d.m_loc : d.m_glob;
-    return (uint32_t)__umul64hi((unsigned long long)dv << 32, m);
+    return dv * (uint32_t)(m >> 32) + __umulhi(dv, (uint32_t)m);
 }
 
 // Bin coordinate of a value a histogram pass sees: from the plane's fixed-point
@@ -686,15 +688,41 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
     // at similar bins)
     const int SB = apply_slot_stride(B);
     const float* E = reinterpret_cast<const float*>(P.ws + im.ws_hist + align_up((int64_t)Hb * Wb * B * 8, 256));
-    for (int k = threadIdx.x; k < 3 * W2 * B; k += kThreads) {
-        const int slot = k / B, j = k - slot * B;
-        const int sr = slot / W2, sc = slot - sr * W2;
-        const int I2 = min(max(I - 1 + sr, 0), Hb - 1);
-        const int J2 = min(max(J0 - 1 + sc, 0), Wb - 1);
-        const float* e = E + ((size_t)I2 * Wb + J2) * B1 + j;
-        const bool ok = bc_ok(e, 8, P.ws, P.ws_bytes, BC_WS);
-        const float e0 = ok ? ld_cg_f(e) : 0.0f, e1 = ok ? ld_cg_f(e + 1) : 0.0f;
-        S.tab[slot * SB + j] = make_float2(e0, e1 - e0);
+    {
+        static_assert(DC_MAX_BINS <= 32, "one lane per bin");
+        // one warp per slot column and lane j per bin, two columns per
+        // round: the twelve L2 loads of a round are in flight together
+        constexpr int NW = kThreads / 32;
+        const int j = threadIdx.x & 31, w = threadIdx.x >> 5;
+        int rowoff[3];
+#pragma unroll
+        for (int sr = 0; sr < 3; ++sr) rowoff[sr] = min(max(I - 1 + sr, 0), Hb - 1) * Wb;
+        if (j < B) {
+            for (int sc0 = w; sc0 < W2; sc0 += 2 * NW) {
+                float e0[2][3], e1[2][3];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int sc = sc0 + h * NW;
+                    const int J2 = min(max(J0 - 1 + sc, 0), Wb - 1);
+#pragma unroll
+                    for (int sr = 0; sr < 3; ++sr) {
+                        const float* e = E + (size_t)(rowoff[sr] + J2) * B1 + j;
+                        const bool ok = sc < W2 && bc_ok(e, 8, P.ws, P.ws_bytes, BC_WS);
+                        e0[h][sr] = ok ? ld_cg_f(e) : 0.0f;
+                        e1[h][sr] = ok ? ld_cg_f(e + 1) : 0.0f;
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int sc = sc0 + h * NW;
+                    if (sc < W2) {
+#pragma unroll
+                        for (int sr = 0; sr < 3; ++sr)
+                            S.tab[(sr * W2 + sc) * SB + j] = make_float2(e0[h][sr], e1[h][sr] - e0[h][sr]);
+                    }
+                }
+            }
+        }
     }
     // bilinear geometry: nominal block centres ((J + 1/2) s); a pixel at x + 1/2
     // lies between the centres of blocks floor(x/s - 1/2) and the next
