@@ -153,7 +153,16 @@ __device__ __forceinline__ float rcp_fast(float x)
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
 }
-__device__ __forceinline__ float ln_fast(float x) { return __logf(x); }
+// Hardware base-2 logarithm without subnormal handling (every caller's argument is
+// at least FLT_MIN).
+__device__ __forceinline__ float lg2_ftz(float x)
+{
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+// ln x = log2(x) ln 2, for x >= FLT_MIN.
+__device__ __forceinline__ float ln_fast(float x) { return lg2_ftz(x) * 0.693147180559945309f; }
 __device__ __forceinline__ float exp_fast(float x) { return __expf(x); }
 
 // ------------------------------------------------------------- Eq. 1-6 -------
@@ -220,11 +229,12 @@ __device__ __forceinline__ float luminance_f32(float R, float G, float B, const 
 
 // Eq. 1-6 for two pixels: the additions and products in f32x2, the square roots
 // and the reciprocal per lane.
-__device__ __forceinline__ void luminance_x2(F2 R, F2 G, F2 B, const Beta& be, float& L0, float& L1)
+__device__ __forceinline__ void luminance_x2(F2 R, F2 G, F2 B, const Beta& be, float& L0, float& L1, float& s0,
+                                             float& s1)
 {
     const F2 S = (R + G) + B;
     const F2 R2 = R * R, G2 = G * G;
-    float a0, a1, c0, c1, s0, s1;
+    float a0, a1, c0, c1;
     f2split(f2fma(B, B, R2 + G2) * f2s(1.0f / 3.0f), a0, a1);
     const F2 L_WHITE = f2(sqrt_fast(a0), sqrt_fast(a1));                      // Eq. 1
     f2split(f2fma(f2s(be.bR), R2, f2s(be.one_m_bR) * G2), c0, c1);
@@ -237,6 +247,12 @@ __device__ __forceinline__ void luminance_x2(F2 R, F2 G, F2 B, const Beta& be, f
     f2split(f2fma(f2s(be.bk), L_WARM * L_WARM, (f2s(be.one_m_bk) * L_COOL) * L_COOL), a0, a1);
     L0 = s0 > 0.0f ? sqrt_fast(a0) : 0.0f;                                    // Eq. 6
     L1 = s1 > 0.0f ? sqrt_fast(a1) : 0.0f;
+}
+
+__device__ __forceinline__ void luminance_x2(F2 R, F2 G, F2 B, const Beta& be, float& L0, float& L1)
+{
+    float s0, s1;
+    luminance_x2(R, G, B, be, L0, L1, s0, s1);
 }
 
 // Linear samples of arbitrary magnitude: Eq. 1-6 are 1-homogeneous, so a pixel
@@ -272,18 +288,22 @@ __device__ __forceinline__ float luminance_hdr(float R, float G, float B, const 
 // only good to 5e-7 and its normalisation by the log range adds as much again: the
 // histogram forms need the absolute error.
 constexpr long long kLn2Q32 = 2977044472LL;  // round(ln 2 * 2^32)
+constexpr int kLn2Q32Hi = 11629079, kLn2Q32Lo = 248;  // kLn2Q32 = 256 Hi + Lo
+static_assert(256LL * kLn2Q32Hi + kLn2Q32Lo == kLn2Q32, "split of ln 2");
 __device__ __forceinline__ int ln_q24(float x)
 {
-    const uint32_t bits = __float_as_uint(x);
-    int e = (int)(bits >> 23) - 127;
-    uint32_t mb = (bits & 0x007FFFFFu) | 0x3F800000u;  // m in [1, 2)
-    if (mb > 0x3FB504F3u) {                            // m > sqrt 2: use m / 2
-        mb -= 0x00800000u;
-        ++e;
-    }
-    const float lm = __log2f(__uint_as_float(mb)) * 0.693147180559945309f;
-    const int ep = (int)(((long long)e * kLn2Q32 + 128) >> 8);
-    return ep + __float2int_rn(lm * 16777216.0f);
+    // e = floor((bits(x) - bits(m0)) / 2^23) with m0 the first binary32 above
+    // 1/sqrt 2; then bits(m) = bits(x) - e 2^23 lies in [bits(m0), bits(m0) + 2^23),
+    // i.e. m in (1/sqrt 2, sqrt 2] and x = 2^e m
+    const int bits = __float_as_int(x);
+    const int e = (bits - 0x3F3504F4) >> 23;
+    const float m = __int_as_float(bits - (e << 23));
+    // ln m in 2^-24 units (ln 2 2^24 is ln 2 scaled by a power of two: one rounding)
+    const float lm = lg2_ftz(m) * (0.693147180559945309f * 16777216.0f);
+    // e ln 2 in 2^-24 units rounded half up, (e kLn2Q32 + 128) >> 8, in 32-bit
+    // pieces (|e| <= 150): e Hi + floor((e Lo + 128) / 256)
+    const int ep = e * kLn2Q32Hi + ((e * kLn2Q32Lo + 128) >> 8);
+    return ep + __float2int_rn(lm);
 }
 
 // Two linear pixels: negatives (and NaN) to 0, the paired Eq. 1-6, and the scaled
@@ -297,9 +317,10 @@ __device__ __forceinline__ void luminance_hdr_x2(float R0, float G0, float B0, f
     R1 = fmaxf(R1, 0.0f);
     G1 = fmaxf(G1, 0.0f);
     B1 = fmaxf(B1, 0.0f);
-    luminance_x2(f2(R0, R1), f2(G0, G1), f2(B0, B1), be, L0, L1);
-    if (!(L0 <= 3.0e38f) || (L0 == 0.0f && R0 + G0 + B0 > 0.0f)) L0 = luminance_rescaled(R0, G0, B0, be);
-    if (!(L1 <= 3.0e38f) || (L1 == 0.0f && R1 + G1 + B1 > 0.0f)) L1 = luminance_rescaled(R1, G1, B1, be);
+    float s0, s1;  // (R + G) + B of each pixel
+    luminance_x2(f2(R0, R1), f2(G0, G1), f2(B0, B1), be, L0, L1, s0, s1);
+    if (!(L0 <= 3.0e38f) || (L0 == 0.0f && s0 > 0.0f)) L0 = luminance_rescaled(R0, G0, B0, be);
+    if (!(L1 <= 3.0e38f) || (L1 == 0.0f && s1 > 0.0f)) L1 = luminance_rescaled(R1, G1, B1, be);
 }
 
 // 8-bit code of y in [0,1]: floor(255 y + 1/2), clamped.
