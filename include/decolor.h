@@ -158,11 +158,12 @@ typedef struct {
 } dc_global_stats;
 
 /* Kernel launch shape used for one (operation, input sample type): threads per CTA
- * (256), tile rows and columns (columns a multiple of 16, or 0 to size tiles per
- * call so that they split evenly over the CTAs - the default except for the local
- * operator, whose tile is block_s rows high with columns rounded to a multiple of
- * block_s) and resident CTAs per SM (0 = as many as fit).  None of these change
- * results: every reduction in the library is exact integer arithmetic. */
+ * (256), tile rows and columns (columns a multiple of 16, or 0 - the default - to
+ * size tiles per call so that they split evenly over the CTAs; the local operator's
+ * tile is block_s rows high and its columns a multiple of lcm(block_s, 16), with 0
+ * picking the width whose tiles balance best over the resident CTAs) and resident
+ * CTAs per SM (0 = as many as fit).  None of these change results: every reduction
+ * in the library is exact integer arithmetic. */
 typedef struct {
     int32_t threads;
     int32_t tile_rows;
@@ -256,6 +257,13 @@ DC_API int dc_debug_profile(int32_t on);
  * tiles, kernel start, kernel end, reserved) followed, for each of the first n_img
  * images of that launch, by 4 phase start and 4 phase end timestamps. */
 DC_API int dc_debug_read_profile(const void* ws, int32_t n_img, uint64_t* out, void* stream);
+
+/* Local tile width (pixels along a block row) that a dc_decolorize_tonemap_local
+ * call on n images of heights[k] x widths[k] with this block_s would use on a GPU
+ * with n_sm SMs, given the current tuning for in_dtype (0 width = automatic, see
+ * dc_tuning).  Host only; *cols receives the width. */
+DC_API int dc_local_tile_cols(int32_t block_s, const int32_t* heights, const int32_t* widths, int32_t n,
+                              int32_t in_dtype, int32_t n_sm, int32_t* cols);
 
 /* Number of kernels the last successful call on this thread enqueued. */
 DC_API int dc_last_launch_count(void);

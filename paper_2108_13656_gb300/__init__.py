@@ -32,6 +32,7 @@ from ._abi import (  # noqa: F401
     library_path,
     load,
     local_params,
+    local_tile_cols,
     parse_stats,
     query_status,
     read_profile,

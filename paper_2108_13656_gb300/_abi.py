@@ -84,6 +84,8 @@ _SIGS = {
     "dc_debug_profile": (ctypes.c_int, [ctypes.c_int32]),
     "dc_debug_read_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "dc_last_launch_count": (ctypes.c_int, []),
+    "dc_local_tile_cols": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
     "dc_debug_bounds": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
     "dc_version": (ctypes.c_int, []),
 }
@@ -388,6 +390,18 @@ def read_profile(workspace, n_img: int = 1, stream=None) -> dict:
         en = v[12 + i * 8: 16 + i * 8]
         res["images"].append([(s - v[5], e - v[5]) if s else None for s, e in zip(st, en)])
     return res
+
+
+def local_tile_cols(sizes, block_s: int = 32, in_dtype: int = DC_U8, n_sm: int = 152) -> int:
+    """Local tile width a call on images of the given (height, width) sizes would use."""
+    n = len(sizes)
+    hs = (ctypes.c_int32 * n)(*[int(h) for h, _ in sizes])
+    ws = (ctypes.c_int32 * n)(*[int(w) for _, w in sizes])
+    cols = ctypes.c_int32(0)
+    rc = load().dc_local_tile_cols(block_s, hs, ws, n, in_dtype, n_sm, ctypes.byref(cols))
+    if rc != DC_OK:
+        raise DcError(rc, "dc_local_tile_cols")
+    return int(cols.value)
 
 
 def last_launch_count() -> int:

@@ -3,7 +3,8 @@
 The knobs are those of `dc_set_tuning`: the tile width of the pixel passes (0 lets
 the library size tiles per call; otherwise pixels per tile, i.e. tile_cols / 256
 pixels per thread and tile) and the resident CTAs per SM; for the local operator the
-tile width along a block row.  None of them changes a result (every reduction in the
+tile width along a block row (0 lets the library pick the width whose tiles balance
+best over the resident CTAs).  None of them changes a result (every reduction in the
 library is exact integer arithmetic, and the test suite checks bitwise equality
 across launch shapes), so the tuner only measures time.  Choices are cached in a
 JSON file keyed by operation, input sample type, batch-size class, pixel-count class
@@ -18,7 +19,7 @@ import threading
 from . import _abi
 
 GLOBAL_CANDIDATES = [(0, 0), (0, 2), (0, 3), (2048, 0), (8192, 0), (32768, 0), (131072, 0), (8192, 2)]
-LOCAL_CANDIDATES = [(128, 0), (256, 0), (512, 0), (1024, 0), (256, 2), (256, 3)]
+LOCAL_CANDIDATES = [(0, 0), (128, 0), (256, 0), (512, 0), (1024, 0), (256, 2), (256, 3)]
 OP_CODES = {"decolorize": _abi.DC_OP_DECOLORIZE, "global": _abi.DC_OP_GLOBAL, "local": _abi.DC_OP_LOCAL}
 
 

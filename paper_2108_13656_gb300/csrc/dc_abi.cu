@@ -33,7 +33,7 @@ std::mutex g_mu;
 dc_tuning g_tune[3][3] = {
     {{256, 1, 0, 0}, {256, 1, 0, 0}, {256, 1, 0, 0}},
     {{256, 1, 0, 0}, {256, 1, 0, 0}, {256, 1, 0, 0}},
-    {{256, 32, 512, 0}, {256, 32, 512, 0}, {256, 32, 512, 0}},
+    {{256, 32, 0, 0}, {256, 32, 0, 0}, {256, 32, 0, 0}},
 };
 constexpr int kAutoCtasPerSm = 4;  // resident CTAs of a pass kernel (launch bounds)
 
@@ -131,6 +131,75 @@ int local_tile_cols(int s, int want)
     int m = std::max(1, want / l);
     while (m > 1 && ((l * m) / s > kLocMaxBlocksX || l * m > kLocMaxCols)) --m;
     return l * m;
+}
+
+// Local tile width when none is tuned: among the widths above, the one whose tiles
+// spread most evenly over the persistent grid.  Model: CTA c takes tiles c,
+// c + grid, ... and a tile costs its pixels plus 3/4 of a block for the curve
+// staging and prologue; the widest width whose maximum CTA cost is within 6% of
+// the smallest wins (narrow tiles stage more curves per pixel than the model
+// counts).  (A CTA's time follows its own work: one left with a second tile runs
+// mostly alone at the end.)  A single image is modelled tile by tile (cached per
+// size); a batch, whose size mix rarely repeats, by its tile count alone (rounds of
+// the grid times a full tile's cost), so that choosing stays a few microseconds.
+// Batches whose 512-pixel tiling already gives many rounds keep 512 pixels.
+int local_tile_cols_auto(int s, const std::vector<std::pair<int, int>>& hw, int nsm, int cps)
+{
+    const int l = s / gcd_i(s, 16) * 16;
+    const int dflt = local_tile_cols(s, 512);
+    nsm = std::max(1, nsm);
+    const int64_t slots = (int64_t)nsm * std::max(1, cps);
+    int64_t t_dflt = 0;
+    for (const auto& d : hw) t_dflt += (int64_t)((d.first + s - 1) / s) * ((d.second + dflt - 1) / dflt);
+    if (t_dflt > 4 * slots || hw.size() > 64) return dflt;
+    const bool single = hw.size() == 1;
+    uint64_t key = 0;
+    static std::mutex mu;
+    static std::unordered_map<uint64_t, int> cache;
+    if (single) {
+        key = ((uint64_t)(uint32_t)hw[0].first << 32 | (uint32_t)hw[0].second) * 1099511628211ull ^
+              ((uint64_t)s << 48 | (uint64_t)(uint32_t)nsm << 8 | (uint64_t)(cps & 0xFF));
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    const int64_t ovh = std::max<int64_t>(256, (int64_t)s * s * 3 / 4);
+    struct Cand {
+        int w;
+        int64_t mc;
+    };
+    std::vector<Cand> cands;
+    std::vector<int64_t> cta;
+    for (int m = 1;; ++m) {
+        const int w = l * m;
+        if (m > 1 && (w / s > kLocMaxBlocksX || w > kLocMaxCols)) break;
+        int64_t T = 0;
+        for (const auto& d : hw) T += (int64_t)((d.first + s - 1) / s) * ((d.second + w - 1) / w);
+        const int64_t grid = std::min(T, slots);
+        if (!single) {
+            cands.push_back({w, (T + grid - 1) / grid * ((int64_t)s * w + ovh)});
+        } else {
+            cta.assign((size_t)grid, 0);
+            const int H = hw[0].first, W = hw[0].second, tx = (W + w - 1) / w;
+            int64_t t = 0;
+            for (int r0 = 0; r0 < H; r0 += s)
+                for (int c = 0; c < tx; ++c, ++t)
+                    cta[(size_t)(t % grid)] += (int64_t)std::min(s, H - r0) * std::min(w, W - c * w) + ovh;
+            cands.push_back({w, *std::max_element(cta.begin(), cta.end())});
+        }
+        if (w / s > kLocMaxBlocksX || w > kLocMaxCols) break;
+    }
+    int64_t min_mc = INT64_MAX;
+    for (const Cand& c : cands) min_mc = std::min(min_mc, c.mc);
+    int best = dflt;
+    for (const Cand& c : cands)  // narrow to wide: the widest within the margin wins
+        if (c.mc * 100 <= min_mc * 106) best = c.w;
+    if (single) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (cache.size() > 1024) cache.clear();
+        cache[key] = best;
+    }
+    return best;
 }
 
 struct Geometry {
@@ -285,7 +354,18 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
         b->tile_cols = (int)std::min<int64_t>(1 << 20, std::max<int64_t>(1024, (want + 15) / 16 * 16));
         b->tile_rows = 1;
     }
-    b->loc_tile_cols = op.opk == kOpkLocal ? local_tile_cols(op.l->block_s, tu.tile_cols > 0 ? tu.tile_cols : 256) : 0;
+    if (op.opk == kOpkLocal) {
+        if (tu.tile_cols > 0) {
+            b->loc_tile_cols = local_tile_cols(op.l->block_s, tu.tile_cols);
+        } else {
+            std::vector<std::pair<int, int>> hw(n);
+            for (int k = 0; k < n; ++k) hw[k] = {in[idx[k]].height, in[idx[k]].width};
+            int nsm = 152, dev = 0;
+            if (launch && cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            b->loc_tile_cols = local_tile_cols_auto(op.l->block_s, hw, nsm,
+                                                    tu.ctas_per_sm > 0 ? tu.ctas_per_sm : kAutoCtasPerSm);
+        }
+    }
     b->beta_r = p->beta_r;
     b->beta_k = p->beta_k;
     b->ldr = ldr ? 1 : 0;
@@ -608,7 +688,6 @@ DC_API int dc_set_tuning(int32_t op, int32_t in_dtype, const dc_tuning* t)
     if (t->threads != 256) return DC_ERR_INVALID_ARG;
     if (t->tile_rows < 1 || t->tile_rows > 4096 || t->tile_cols < 0 || t->tile_cols > (1 << 20) || (t->tile_cols % 16) != 0)
         return DC_ERR_INVALID_ARG;
-    if (op == DC_OP_LOCAL && t->tile_cols == 0) return DC_ERR_INVALID_ARG;
     if (t->ctas_per_sm < 0 || t->ctas_per_sm > 32) return DC_ERR_INVALID_ARG;
     std::lock_guard<std::mutex> lk(g_mu);
     g_tune[op][in_dtype] = *t;
@@ -649,6 +728,27 @@ DC_API int dc_debug_read_profile(const void* ws, int32_t n_img, uint64_t* out, v
             out[PROF_SLOTS + i * 2 * kMaxPhases + kMaxPhases + p] = ic.t_end[p];
         }
     }
+    return DC_OK;
+}
+
+DC_API int dc_local_tile_cols(int32_t block_s, const int32_t* heights, const int32_t* widths, int32_t n,
+                              int32_t in_dtype, int32_t n_sm, int32_t* cols)
+{
+    if (!heights || !widths || !cols || n < 1 || n > DC_MAX_BATCH || block_s < 1 || block_s > 64 || n_sm < 1 ||
+        !dt_ok(in_dtype))
+        return DC_ERR_INVALID_ARG;
+    dc_tuning tu;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        tu = g_tune[DC_OP_LOCAL][in_dtype];
+    }
+    std::vector<std::pair<int, int>> hw((size_t)n);
+    for (int k = 0; k < n; ++k) {
+        if (heights[k] < 1 || widths[k] < 1) return DC_ERR_INVALID_ARG;
+        hw[(size_t)k] = {heights[k], widths[k]};
+    }
+    *cols = tu.tile_cols > 0 ? local_tile_cols(block_s, tu.tile_cols)
+                             : local_tile_cols_auto(block_s, hw, n_sm, tu.ctas_per_sm > 0 ? tu.ctas_per_sm : kAutoCtasPerSm);
     return DC_OK;
 }
 

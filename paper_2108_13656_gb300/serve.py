@@ -176,11 +176,13 @@ def serve_batched(trace, pool: HostPool, budget_bytes: int = 16 << 30, n_streams
     wss = [_abi.Workspace(device=dev) for _ in range(n_streams)]
     for w in wss:
         w.get(128 << 20)  # sized up front: growing it inside the loop would allocate
-    inflight_per_stream = [0] * n_streams
     outpool, devpool = pool.outpool, pool.devpool
     pending = collections.deque(sorted(trace, key=lambda r: r.t_arrive))
     waiting = collections.deque()
-    inflight = []  # (event, stream index, [(req, x, y, host_out)], bytes)
+    # per stream, in launch order: (event, [(req, x, y, host_out)], bytes).  A stream
+    # completes its batches in order, so only the oldest of each is polled: the cost
+    # of a loop iteration does not grow with the number of batches in flight.
+    inflight = [collections.deque() for _ in range(n_streams)]
     lat = {}
     outputs = {} if keep_outputs else None
     used = peak = 0
@@ -191,14 +193,14 @@ def serve_batched(trace, pool: HostPool, budget_bytes: int = 16 << 30, n_streams
     gc.collect()
     gc.disable()  # a collection pause would stall every request in flight
     t0 = time.perf_counter()
-    while pending or waiting or inflight:
+    while pending or waiting or any(inflight):
         now = time.perf_counter() - t0
         while pending and pending[0].t_arrive <= now:
             waiting.append(pending.popleft())
         # retire finished batches
-        still = []
-        for ev, si, items, nbytes in inflight:
-            if ev.query():
+        for q in inflight:
+            while q and q[0][0].query():
+                _, items, nbytes = q.popleft()
                 t_done = time.perf_counter() - t0
                 for r, x, y, ho in items:
                     lat[r.rid] = t_done - r.t_arrive
@@ -208,10 +210,6 @@ def serve_batched(trace, pool: HostPool, budget_bytes: int = 16 << 30, n_streams
                     devpool.put(x)
                     devpool.put(y)
                 used -= nbytes
-                inflight_per_stream[si] -= 1
-            else:
-                still.append((ev, si, items, nbytes))
-        inflight = still
         # admit what fits, FIFO, and launch it as one batch per operation
         admitted = []
         while waiting and len(admitted) < max_batch:
@@ -225,7 +223,7 @@ def serve_batched(trace, pool: HostPool, budget_bytes: int = 16 << 30, n_streams
             t_launch = time.perf_counter() - t0
             for r, _ in admitted:
                 queued[r.rid] = t_launch - r.t_arrive
-            si = min(range(n_streams), key=lambda k: inflight_per_stream[k])
+            si = min(range(n_streams), key=lambda k: len(inflight[k]))
             s = streams[si]
             with torch.cuda.stream(s):
                 items = []
@@ -243,12 +241,11 @@ def serve_batched(trace, pool: HostPool, budget_bytes: int = 16 << 30, n_streams
                     ho.copy_(y, non_blocking=True)
                 ev = torch.cuda.Event()
                 ev.record(s)
-            inflight.append((ev, si, items, sum(n for _, n in admitted)))
-            inflight_per_stream[si] += 1
+            inflight[si].append((ev, items, sum(n for _, n in admitted)))
             batches += 1
             continue
         # nothing to launch: wait for the next arrival or completion
-        if pending and not inflight and not waiting:
+        if pending and not any(inflight) and not waiting:
             _wait_until(t0 + pending[0].t_arrive)
         else:
             time.sleep(2e-5)

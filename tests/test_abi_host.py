@@ -156,3 +156,64 @@ def test_tuning_table_validation(abi):
 def test_status_strings(abi):
     assert abi.status_string(abi.DC_ERR_TIMEOUT).startswith("device-side")
     assert abi.status_string(0) == "ok"
+
+
+def _lcm16(s):
+    import math
+    return s // math.gcd(s, 16) * 16
+
+
+def _tiles(sizes, s, w):
+    return sum(((h + s - 1) // s) * ((wd + w - 1) // w) for h, wd in sizes)
+
+
+@pytest.mark.parametrize("s", [1, 8, 16, 24, 32, 64])
+@pytest.mark.parametrize("sizes", [[(2160, 3840)], [(4320, 7680)], [(1440, 2560)], [(97, 333)], [(64, 64)],
+                                   [(2160, 3840), (480, 640), (1080, 1920)]])
+def test_automatic_local_tile_width_is_a_valid_tiling(abi, s, sizes):
+    # automatic width (the default): a multiple of lcm(s, 16), at most 1024 pixels,
+    # and the busiest CTA of the persistent grid (CTA c takes tiles c, c + grid, ...)
+    # covers hardly more pixels than with the 512-pixel tiling
+    w = abi.local_tile_cols(sizes, block_s=s, in_dtype=abi.DC_U8, n_sm=152)
+    assert w % _lcm16(s) == 0 and 0 < w <= 1024
+    slots = 152 * 4
+
+    def busiest(w_):
+        px = [min(s, h - r0) * min(w_, wd - c * w_) for h, wd in sizes
+              for r0 in range(0, h, s) for c in range(-(-wd // w_))]
+        grid = min(len(px), slots)
+        load = [0] * grid
+        for t, p in enumerate(px):
+            load[t % grid] += p
+        return max(load)
+
+    l = _lcm16(s)
+    m = max(1, 512 // l)
+    while m > 1 and (l * m // s > 32 or l * m > 1024):  # at most 32 blocks per tile
+        m -= 1
+    w512 = l * m
+    assert busiest(w) <= 1.1 * busiest(w512)
+
+
+def test_automatic_local_tile_width_fills_the_grid(abi):
+    # 2560x1440, 32-pixel blocks: 512-pixel tiles give 225 tiles for 608 resident
+    # CTAs; the balanced width uses most of them in one round
+    w = abi.local_tile_cols([(1440, 2560)], block_s=32, n_sm=152)
+    t = _tiles([(1440, 2560)], 32, w)
+    assert 450 <= t <= 608
+    # 3840x2160: one round of equal tiles (15 of the 120 block columns each)
+    assert abi.local_tile_cols([(2160, 3840)], block_s=32, n_sm=152) == 480
+
+
+def test_tuned_local_tile_width_is_kept(abi):
+    orig = abi.get_tuning(abi.DC_OP_LOCAL, abi.DC_F32)
+    try:
+        abi.set_tuning(abi.DC_OP_LOCAL, abi.DC_F32, 256, 32, 512, 0)
+        assert abi.local_tile_cols([(2160, 3840)], block_s=32, in_dtype=abi.DC_F32) == 512
+        assert abi.local_tile_cols([(2160, 3840)], block_s=24, in_dtype=abi.DC_F32) == 480  # multiple of 48
+    finally:
+        abi.set_tuning(abi.DC_OP_LOCAL, abi.DC_F32, *orig)
+    with pytest.raises(abi.DcError):
+        abi.local_tile_cols([(0, 10)])
+    with pytest.raises(abi.DcError):
+        abi.local_tile_cols([(10, 10)], block_s=65)
