@@ -510,6 +510,40 @@ struct GroupIO {
         }
     }
 
+    // A full, aligned group of G values at p in the output sample type OUT_DT.
+    template <int OUT_DT>
+    __device__ static __forceinline__ void store_full(uint8_t* p, const float (&y)[G])
+    {
+        if constexpr (OUT_DT == DC_U8) {
+            uint32_t w[(G + 3) / 4];
+#pragma unroll
+            for (int k = 0; k < (G + 3) / 4; ++k) w[k] = 0;
+#pragma unroll
+            for (int k = 0; k < G; ++k) w[k >> 2] |= quant_u8(y[k]) << (8 * (k & 3));
+            if constexpr (G == 8) {
+                *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+            } else {
+                *reinterpret_cast<uint32_t*>(p) = w[0];
+            }
+        } else if constexpr (OUT_DT == DC_F16) {
+            uint32_t w[G / 2];
+#pragma unroll
+            for (int k = 0; k < G / 2; ++k) {
+                __half2 h = __floats2half2_rn(y[2 * k], y[2 * k + 1]);
+                memcpy(&w[k], &h, 4);
+            }
+            if constexpr (G == 8) {
+                *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+            } else {
+                *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < G; k += 4)
+                *reinterpret_cast<float4*>(p + 4 * k) = make_float4(y[k], y[k + 1], y[k + 2], y[k + 3]);
+        }
+    }
+
     // Store n values (in [0,1] units) at (r, c) in the output sample type.
     __device__ static void store(const DcImage& im, int r, int c, int n, bool vec, const float (&y)[G])
     {

@@ -276,6 +276,68 @@ __device__ __forceinline__ void walk_block_patches(const DcImage& im, const Tile
     }
 }
 
+// The same walk for a pass that reads the f32 plane and writes the output: f(r, c,
+// v) turns the G plane values of a group into output values in place and the walk
+// stores them in the output type OUT_DT.  A thread's groups share one column, so
+// full groups of an aligned image move through two row pointers advanced by ly
+// rows at a time; a ragged right edge takes the general group I/O.
+template <int IN_DT, int OUT_DT, class F>
+__device__ __forceinline__ void walk_block_patches_plane(const DcImage& im, const TileRect& t, int s, F&& f)
+{
+    constexpr int G = InT<IN_DT>::G, U = Unroll<IN_DT, true>::value;
+    constexpr int OE = OUT_DT == DC_U8 ? 1 : (OUT_DT == DC_F16 ? 2 : 4);
+    constexpr int W = kThreads / 32;
+    const int lgx = min(5, 31 - __clz(max(1, s / G)));
+    const int lx = 1 << lgx, ly = 32 >> lgx, pw = lx * G;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gx = lane & (lx - 1), gy = lane >> lgx;
+    const int npx = (t.c1 - t.c0 + pw - 1) / pw;
+    const bool vec_img = (im.flags & IF_VEC) != 0;
+    const int64_t pstep = im.plane_stride * ly, ostep = im.out_stride * ly;
+    const int64_t pext = GroupIO<IN_DT>::plane_extent(im), oext = GroupIO<IN_DT>::out_extent(im);
+    for (int px = warp; px < npx; px += W) {
+        const int cc = t.c0 + px * pw + gx * G;
+        const int nn = max(0, min(G, t.c1 - cc));
+        if (vec_img && nn == G) {
+            const uint8_t* pp = im.plane + (int64_t)(t.r0 + gy) * im.plane_stride + (int64_t)cc * 4;
+            uint8_t* op = im.out + (int64_t)(t.r0 + gy) * im.out_stride + (int64_t)cc * OE;
+            for (int r0 = t.r0 + gy; r0 < t.r1; r0 += U * ly) {
+                float v[U][G];
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    const float* q = reinterpret_cast<const float*>(pp + u * pstep);
+                    const bool ok = r0 + u * ly < t.r1 && bc_ok(q, G * 4, im.plane, pext, BC_PLANE);
+#pragma unroll
+                    for (int k = 0; k < G; k += 4) {
+                        const float4 x = ok ? ld_cg_f4(q + k) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        v[u][k] = x.x;
+                        v[u][k + 1] = x.y;
+                        v[u][k + 2] = x.z;
+                        v[u][k + 3] = x.w;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < U; ++u) {
+                    if (r0 + u * ly < t.r1) {
+                        f(r0 + u * ly, cc, v[u]);
+                        uint8_t* o = op + u * ostep;
+                        if (bc_ok(o, G * OE, im.out, oext, BC_OUT)) GroupIO<IN_DT>::template store_full<OUT_DT>(o, v[u]);
+                    }
+                }
+                pp += U * pstep;
+                op += U * ostep;
+            }
+        } else if (nn > 0) {
+            for (int r = t.r0 + gy; r < t.r1; r += ly) {
+                float v[G];
+                GroupIO<IN_DT>::from_plane(im, r, cc, nn, false, v);
+                f(r, cc, v);
+                GroupIO<IN_DT>::store(im, r, cc, nn, false, v);
+            }
+        }
+    }
+}
+
 // PLANE: the pass reads the f32 plane an earlier pass kept (every image of the
 // launch has one), else it recomputes the luminance from RGB.
 template <int IN_DT, bool PLANE, class F>
@@ -741,8 +803,9 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
     const float delta = P.delta, Bf = (float)B, alpha = P.alpha;
     const int WSB = W2 * SB;
     cta_sync();
-    auto body = [&](auto alpha_one) {
-        auto pixel_fn = [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+    auto body = [&](auto alpha_one, auto out_dt) {
+        // output values of one group in place
+        auto curve_fn = [&](int r, int c, float (&Lv)[G]) __attribute__((always_inline)) {
             const int2 ri = S.row[r - t.r0];
             const float2* rowp = S.tab + ri.x;
             const float wy = __int_as_float(ri.y);
@@ -784,14 +847,34 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
                     Lv[k] = fmaf(alpha, F - u, u);
                 }
             }
-            GroupIO<IN_DT>::store(im, r, c, n, vec, Lv);
         };
-        walk_block_patches<IN_DT, PLANE>(im, t, s, be, pixel_fn);
+        if constexpr (PLANE) {
+            walk_block_patches_plane<IN_DT, decltype(out_dt)::value>(im, t, s, curve_fn);
+        } else {
+            walk_block_patches<IN_DT, false>(im, t, s, be,
+                                             [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+                                                 curve_fn(r, c, Lv);
+                                                 GroupIO<IN_DT>::store(im, r, c, n, vec, Lv);
+                                             });
+        }
+    };
+    // alpha = 1 and the output type as compile-time constants of the pixel loop
+    auto by_out = [&](auto alpha_one) {
+        if constexpr (!PLANE) {
+            body(alpha_one, std::integral_constant<int, DC_F32>{});  // (the store dispatches itself)
+        } else {
+            if (im.out_dt == DC_U8)
+                body(alpha_one, std::integral_constant<int, DC_U8>{});
+            else if (im.out_dt == DC_F16)
+                body(alpha_one, std::integral_constant<int, DC_F16>{});
+            else
+                body(alpha_one, std::integral_constant<int, DC_F32>{});
+        }
     };
     if (alpha == 1.0f)
-        body(std::true_type{});
+        by_out(std::true_type{});
     else
-        body(std::false_type{});
+        by_out(std::false_type{});
 }
 
 // ------------------------------------------------------------ the engine -----
