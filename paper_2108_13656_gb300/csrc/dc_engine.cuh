@@ -414,7 +414,11 @@ struct GroupIO {
     // once, so it is loaded with an evict-first L2 policy.
     __device__ static __forceinline__ void load_raw(const DcImage& im, int r, int c, uint32_t (&w)[12])
     {
-        const uint8_t* p = im.in + (int64_t)r * im.in_stride + (int64_t)c * 3 * ESZ;
+        load_raw_at(im, im.in + (int64_t)r * im.in_stride + (int64_t)c * 3 * ESZ, w);
+    }
+    // The same from the group's address p.
+    __device__ static __forceinline__ void load_raw_at(const DcImage& im, const uint8_t* p, uint32_t (&w)[12])
+    {
         if (!bc_ok(p, 3 * G * ESZ, im.in, in_extent(im), BC_IN)) {
 #pragma unroll
             for (int k = 0; k < 12; ++k) w[k] = 0u;
@@ -470,6 +474,20 @@ struct GroupIO {
 
     // Luminance (or its fixed-point log or bin coordinate) from the f32 plane an
     // earlier phase wrote.
+    // A full, aligned group of the plane at p.
+    __device__ static __forceinline__ void from_plane_at(const DcImage& im, const float* p, float (&Lv)[G])
+    {
+        const bool ok = bc_ok(p, G * 4, im.plane, plane_extent(im), BC_PLANE);
+#pragma unroll
+        for (int k = 0; k < G; k += 4) {
+            const float4 v = ok ? ld_cg_f4(p + k) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            Lv[k] = v.x;
+            Lv[k + 1] = v.y;
+            Lv[k + 2] = v.z;
+            Lv[k + 3] = v.w;
+        }
+    }
+
     __device__ static void from_plane(const DcImage& im, int r, int c, int n, bool vec, float (&Lv)[G])
     {
         const float* p = reinterpret_cast<const float*>(im.plane + (int64_t)r * im.plane_stride) + c;

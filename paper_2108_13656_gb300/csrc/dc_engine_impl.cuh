@@ -165,14 +165,18 @@ __device__ __forceinline__ uint32_t coord_of(float val, bool is_log_plane, float
 // before computing any of them.
 template <int IN_DT, bool PLANE, class F>
 __device__ __forceinline__ void walk_group(const DcImage& im, const Beta& be, F&& f, int r, int c, int n, bool vec,
-                                           float (&v)[InT<IN_DT>::G], uint32_t (&w)[PLANE ? 1 : 12], bool load)
+                                           const uint8_t* src, float (&v)[InT<IN_DT>::G],
+                                           uint32_t (&w)[PLANE ? 1 : 12], bool load)
 {
     if (load) {
         if constexpr (PLANE) {
-            GroupIO<IN_DT>::from_plane(im, r, c, n, vec, v);
+            if (vec)
+                GroupIO<IN_DT>::from_plane_at(im, reinterpret_cast<const float*>(src), v);
+            else
+                GroupIO<IN_DT>::from_plane(im, r, c, n, false, v);
         } else {
             if (vec)
-                GroupIO<IN_DT>::load_raw(im, r, c, w);
+                GroupIO<IN_DT>::load_raw_at(im, src, w);
             else
                 GroupIO<IN_DT>::luminance(im, r, c, n, false, be, v);
         }
@@ -184,16 +188,22 @@ __device__ __forceinline__ void walk_group(const DcImage& im, const Beta& be, F&
     }
 }
 
+// Full groups are addressed from a pointer per thread: along a row the U groups of
+// an iteration sit at constant offsets from it, down a column it advances by a
+// fixed step, so no group recomputes its address from (r, c).
 template <int IN_DT, bool PLANE, class F>
 __device__ __forceinline__ void walk_tile(const DcImage& im, const TileRect& t, const Beta& be, F&& f)
 {
     constexpr int G = InT<IN_DT>::G, U = Unroll<IN_DT, PLANE>::value;
+    constexpr int GB = PLANE ? 4 * G : 3 * InT<IN_DT>::ESZ * G;  // source bytes of a group
     const int gpr = (t.c1 - t.c0 + G - 1) / G;
     const int lg = gpr >= kThreads ? 8 : 32 - __clz(gpr - 1);
     const int txt = 1 << lg;
     const int tx = threadIdx.x & (txt - 1);
     const int rpi = kThreads >> lg;
     const bool vec_img = (im.flags & IF_VEC) != 0;
+    const uint8_t* const src0 = PLANE ? im.plane : im.in;
+    const int64_t sstride = PLANE ? im.plane_stride : im.in_stride;
     int c[U], n[U], rr[U];
     bool vec[U];
     float v[U][G];
@@ -201,18 +211,20 @@ __device__ __forceinline__ void walk_tile(const DcImage& im, const TileRect& t, 
     if (gpr >= kThreads) {
         // long rows: the U groups of an iteration lie along the row
         for (int r = t.r0; r < t.r1; ++r) {
-            for (int g = tx; g < gpr; g += U * kThreads) {
+            const uint8_t* q = src0 + (int64_t)r * sstride + (int64_t)(t.c0 / G + tx) * GB;
+            for (int g = tx; g < gpr; g += U * kThreads, q += (int64_t)U * kThreads * GB) {
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int gu = g + u * kThreads;
                     c[u] = t.c0 + gu * G;
                     n[u] = gu < gpr ? min(G, t.c1 - c[u]) : 0;
                     vec[u] = vec_img && n[u] == G;
-                    if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, r, c[u], n[u], vec[u], v[u], w[u], true);
+                    if (n[u] > 0)
+                        walk_group<IN_DT, PLANE>(im, be, f, r, c[u], n[u], vec[u], q + u * kThreads * GB, v[u], w[u], true);
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u)
-                    if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, r, c[u], n[u], vec[u], v[u], w[u], false);
+                    if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, r, c[u], n[u], vec[u], nullptr, v[u], w[u], false);
             }
         }
     } else {
@@ -220,16 +232,19 @@ __device__ __forceinline__ void walk_tile(const DcImage& im, const TileRect& t, 
         const int cc = t.c0 + tx * G;
         const int nn = tx < gpr ? min(G, t.c1 - cc) : 0;
         const bool vv = vec_img && nn == G;
-        for (int r = t.r0 + (threadIdx.x >> lg); r < t.r1; r += U * rpi) {
+        const int r_first = t.r0 + (threadIdx.x >> lg);
+        const int64_t step = (int64_t)rpi * sstride;
+        const uint8_t* q = src0 + (int64_t)r_first * sstride + (int64_t)(t.c0 / G + tx) * GB;
+        for (int r = r_first; r < t.r1; r += U * rpi, q += U * step) {
 #pragma unroll
             for (int u = 0; u < U; ++u) {
                 rr[u] = r + u * rpi;
                 n[u] = rr[u] < t.r1 ? nn : 0;
-                if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, rr[u], cc, n[u], vv, v[u], w[u], true);
+                if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, rr[u], cc, n[u], vv, q + u * step, v[u], w[u], true);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, rr[u], cc, n[u], vv, v[u], w[u], false);
+                if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, rr[u], cc, n[u], vv, nullptr, v[u], w[u], false);
         }
     }
 }
@@ -267,11 +282,15 @@ __device__ __forceinline__ void walk_block_patches(const DcImage& im, const Tile
                 c[u] = cc;
                 n[u] = rr[u] < t.r1 ? nn : 0;
                 vec[u] = vv;
-                if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, rr[u], c[u], n[u], vec[u], v[u], w[u], true);
+                if (n[u] > 0) {
+                    const uint8_t* src = PLANE ? im.plane + (int64_t)rr[u] * im.plane_stride + (int64_t)c[u] * 4
+                                               : im.in + (int64_t)rr[u] * im.in_stride + (int64_t)c[u] * 3 * InT<IN_DT>::ESZ;
+                    walk_group<IN_DT, PLANE>(im, be, f, rr[u], c[u], n[u], vec[u], src, v[u], w[u], true);
+                }
             }
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, rr[u], c[u], n[u], vec[u], v[u], w[u], false);
+                if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, rr[u], c[u], n[u], vec[u], nullptr, v[u], w[u], false);
         }
     }
 }
