@@ -714,15 +714,28 @@ __device__ void tile_cdf(const DcBatch<CAP>& P, const DcImage& im, int I, const 
     const int J0 = t.c0;
     const int lo = max(0, J0 - R), hi = min(Wb, t.c1 + R);
     const int ncol = hi - lo;
-    for (int k = threadIdx.x; k < ncol * B; k += kThreads) {
-        const int jj = lo + k / B, j = k % B;
-        unsigned long long v = 0ull;
+    // column sums over the window's block rows: a warp per staged column and a lane
+    // per bin (B <= 32), two columns per round so that their loads are in flight
+    // together; no integer division
+    {
+        constexpr int NW = kThreads / 32;
+        const size_t rs = (size_t)Wb * B;
+        if (lane < B) {
+            for (int c0 = warp; c0 < ncol; c0 += 2 * NW) {
+                const int c1 = c0 + NW;
+                const bool has1 = c1 < ncol;
+                const unsigned long long* q0 = H + ((size_t)i0 * Wb + lo + c0) * B + lane;
+                const unsigned long long* q1 = H + ((size_t)i0 * Wb + lo + (has1 ? c1 : c0)) * B + lane;
+                unsigned long long v0 = 0ull, v1 = 0ull;
 #pragma unroll 5
-        for (int I2 = i0; I2 <= i1; ++I2) {  // loads issued together
-            const unsigned long long* q = &H[((size_t)I2 * Wb + jj) * B + j];
-            v += bc_ok(q, 8, P.ws, P.ws_bytes, BC_WS) ? ld_cg_u64(q) : 0ull;
+                for (int I2 = i0; I2 <= i1; ++I2, q0 += rs, q1 += rs) {
+                    v0 += bc_ok(q0, 8, P.ws, P.ws_bytes, BC_WS) ? ld_cg_u64(q0) : 0ull;
+                    v1 += (has1 && bc_ok(q1, 8, P.ws, P.ws_bytes, BC_WS)) ? ld_cg_u64(q1) : 0ull;
+                }
+                S.v[c0 * B + lane] = v0;
+                if (has1) S.v[c1 * B + lane] = v1;
+            }
         }
-        S.v[k] = v;
     }
     cta_sync();
     const int nout = t.c1 - t.c0;
