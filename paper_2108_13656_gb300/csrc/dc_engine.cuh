@@ -662,7 +662,10 @@ __host__ __device__ constexpr int apply_slot_stride(int bins) { return bins + ((
 constexpr int kLocMaxRows = 64;      // tallest local tile (block_s)
 struct SmemApplyL {
     float2 tab[3 * (kLocMaxBlocksX + 2) * (DC_MAX_BINS + 8)];  // per block and bin: (F at bin start, slope)
-    int2 col[kLocMaxCols + 16];  // per tile column: table slot offset of the left block, weight bits
+    // per tile column x: table slot offset of the left block and the weight bits, at
+    // (x mod G) * (kLocMaxCols + 16) / G + x / G for groups of G pixels, so that the
+    // lanes of a warp, one group each, read neighbouring entries
+    int2 col[kLocMaxCols + 16];
     int2 row[kLocMaxRows];  // per tile row: table slot offset of the upper block row, weight bits
 };
 

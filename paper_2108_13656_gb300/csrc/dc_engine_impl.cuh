@@ -771,6 +771,8 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
                                  const Beta& be, const Derived& d, unsigned char* smem)
 {
     constexpr int G = InT<IN_DT>::G;
+    constexpr int kColGroups = (kLocMaxCols + 16) / G;  // column-table stride between a group's entries
+    static_assert((kLocMaxCols + 16) % G == 0, "column table splits into G rows");
     constexpr bool ldr = IN_DT == DC_U8;  // u = L; otherwise the fixed-point log coordinate
     SmemApplyL& S = *reinterpret_cast<SmemApplyL*>(smem);
     const int s = P.block_s, B = P.bins, Hb = im.Hb, Wb = im.Wb;
@@ -825,7 +827,7 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
     for (int k = threadIdx.x; k < t.c1 - t.c0 + G; k += kThreads) {
         const float fx = fmaf((float)(min(t.c0 + k, t.c1 - 1)) + 0.5f, inv_s, -0.5f);
         const float flx = floorf(fx);
-        S.col[k] = make_int2(((int)flx - (J0 - 1)) * SB, __float_as_int(fx - flx));
+        S.col[(k % G) * kColGroups + k / G] = make_int2(((int)flx - (J0 - 1)) * SB, __float_as_int(fx - flx));
     }
     for (int k = threadIdx.x; k < t.r1 - t.r0; k += kThreads) {
         const float fy = fmaf((float)(t.r0 + k) + 0.5f, inv_s, -0.5f);
@@ -841,7 +843,7 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
             const int2 ri = S.row[r - t.r0];
             const float2* rowp = S.tab + ri.x;
             const float wy = __int_as_float(ri.y);
-            const int2* colp = S.col + (c - t.c0);
+            const int2* colp = S.col + (c - t.c0) / G;  // entry k of the group at colp[k * kColGroups]
 #pragma unroll
             for (int k = 0; k < G; ++k) {
                 // bin j and position tt in it: from u = L (8-bit input) or exactly from
@@ -864,7 +866,7 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
                     tt = __uint_as_float(0x3F800000u + ((q - (jq << kLocTS)) >> (kLocTS - 23))) - 1.0f;
                     if constexpr (!decltype(alpha_one)::value) u = (float)q * (1.0f / (Bf * (float)(1u << kLocTS)));
                 }
-                const int2 ci = colp[k];
+                const int2 ci = colp[k * kColGroups];
                 const float wx = __int_as_float(ci.y);
                 const float2* p = rowp + ci.x + j;
                 const float2 a = p[0], b = p[SB], cc = p[WSB], dd = p[WSB + SB];
