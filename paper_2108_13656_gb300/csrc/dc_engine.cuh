@@ -648,9 +648,13 @@ struct SmemStats {
 struct SmemApplyG {
     float lut[260];
 };
+// Per-block stride of the block-histogram pass's shared counters: at least B and 8
+// (mod 32), so that equal bins of neighbouring blocks (a warp covers several blocks
+// of a row) fall 8 banks apart; at most DC_MAX_BINS + 8.
+__host__ __device__ constexpr int blockh_stride(int bins) { return bins + ((8 - bins % 32) + 32) % 32; }
 struct SmemBlockH {
-    uint32_t cnt[kLocMaxBlocksX * DC_MAX_BINS];  // pixels whose lower tent bin is j
-    uint32_t fs[kLocMaxBlocksX * DC_MAX_BINS];   // their upper-bin fractions, units of 2^-20
+    uint32_t cnt[kLocMaxBlocksX * (DC_MAX_BINS + 8)];  // pixels whose lower tent bin is j
+    uint32_t fs[kLocMaxBlocksX * (DC_MAX_BINS + 8)];   // their upper-bin fractions, units of 2^-20
 };
 struct SmemCdf {
     unsigned long long v[(kCdfChunk + 2 * kMaxRadius) * DC_MAX_BINS];

@@ -626,7 +626,9 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
     SmemBlockH& S = *reinterpret_cast<SmemBlockH*>(smem);
     const int s = P.block_s, B = P.bins;
     const int nbx = (t.c1 - t.c0 + s - 1) / s;
-    for (int k = threadIdx.x; k < nbx * B; k += kThreads) {
+    const int BS = blockh_stride(B);
+    static_assert(blockh_stride(DC_MAX_BINS) <= DC_MAX_BINS + 8, "counter stride");
+    for (int k = threadIdx.x; k < nbx * BS; k += kThreads) {
         S.cnt[k] = 0u;
         S.fs[k] = 0u;
     }
@@ -661,7 +663,7 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
                     const uint32_t off = (uint32_t)(c + k - t.c0);
                     blk = magic ? (int)__umulhi(off, magic) : (int)off;
                 }
-                const int key = blk * B + (x >> 20);
+                const int key = blk * BS + (x >> 20);
                 const uint32_t f = (uint32_t)x & 0xFFFFFu;
                 if (key == cur) {
                     ++rc;
@@ -693,8 +695,9 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
     const int J0 = t.c0 / s;
     for (int k = threadIdx.x; k < nbx * B; k += kThreads) {
         const int blk = k / B, j = k - blk * B;
-        const unsigned long long fprev = j > 0 ? S.fs[k - 1] : 0u;
-        const unsigned long long h = ((unsigned long long)S.cnt[k] << 20) - S.fs[k] + fprev;
+        const int e = blk * BS + j;
+        const unsigned long long fprev = j > 0 ? S.fs[e - 1] : 0u;
+        const unsigned long long h = ((unsigned long long)S.cnt[e] << 20) - S.fs[e] + fprev;
         unsigned long long* q = &H[((size_t)I * im.Wb + (J0 + blk)) * B + j];
         if (bc_ok(q, 8, P.ws, P.ws_bytes, BC_WS)) *q = h;
     }
