@@ -36,7 +36,8 @@ def test_status_word_and_workspace_reuse(dc, oracle_mod):
 @pytest.mark.parametrize("op", ["decolorize", "global", "histeq", "local"])
 @pytest.mark.parametrize("in_dt", [np.uint8, np.float32])
 def test_results_independent_of_launch_shape(dc, op, in_dt):
-    """Tile shape and CTAs per SM change neither the bits of the output nor the stats."""
+    """Tile shape (fixed, or sized per call) and CTAs per SM change neither the bits of
+    the output nor the stats."""
     import torch
     from paper_2108_13656_gb300 import synth
     img = synth.s_ldr(1000, 700, 3) if in_dt == np.uint8 else synth.s_hdr(1000, 700, 3)
@@ -47,7 +48,8 @@ def test_results_independent_of_launch_shape(dc, op, in_dt):
     orig = dc.get_tuning(op_code, dt_code)
     results = []
     try:
-        for (tr, tc, cps) in [(4, 4096, 0), (1, 16, 1), (7, 1040, 3), (64, 65536, 2), (2, 512, 0)]:
+        # tile width 0: sized per call (the local operator's balanced width)
+        for (tr, tc, cps) in [(4, 4096, 0), (1, 16, 1), (7, 1040, 3), (64, 65536, 2), (2, 512, 0), (1, 0, 0)]:
             dc.set_tuning(op_code, dt_code, 256, tr, tc, cps)
             y = torch.empty((700, 1000), dtype=torch.float32, device="cuda")
             st = torch.zeros(dc.STATS_BYTES, dtype=torch.uint8, device="cuda")
