@@ -380,6 +380,10 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
         b->gain_is_one = op.g->gain_k == 1.0f;
         b->need_gray_hist = ldr && (op.g->mode == DC_HISTEQ || op.stats != nullptr);
         b->stats = op.stats;
+        // the sigmoid needs mu; HDR histogram equalisation the log range; a stats
+        // record both
+        b->need_logsum = op.g->mode == DC_SIGMOID || op.stats != nullptr;
+        b->need_minmax = (op.g->mode == DC_HISTEQ && !ldr) || op.stats != nullptr;
     } else if (op.opk == kOpkLocal) {
         b->block_s = op.l->block_s;
         // ceil(2^32 / s) for s >= 2 (2^32 itself does not fit: s = 1 is flagged by 0)
@@ -389,6 +393,8 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
         b->bins = op.l->bins;
         b->alpha = op.l->alpha;
         b->delta = op.l->delta;
+        b->need_logsum = 0;  // the local operator uses only the log range
+        b->need_minmax = 1;
     }
     // workspace layout: header | ctrl | per-image local buffers
     const int64_t ctrl_bytes = align_up((int64_t)sizeof(DcCtrl) + (int64_t)n * sizeof(DcImgCtrl), 256);
@@ -459,7 +465,11 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
     int rc = DC_OK;
     for (int ph = 0; ph < b->n_phase && rc == DC_OK; ++ph) {
         const int kind = b->phase_kind[ph];
-        const bool pl = plane && reads_plane(kind, in_dt);
+        // the flag: reads the plane (histogram and apply passes), or keeps only the
+        // reduction the call uses (statistics passes)
+        const bool pl = kind == PK_STATS       ? b->need_minmax == 0
+                        : kind == PK_STATS_LOG ? b->need_logsum == 0
+                                               : plane && reads_plane(kind, in_dt);
         int occ = in_dt == DC_U8 ? occupancy_u8(CAP, op.opk, kind, pl)
                                  : (in_dt == DC_F16 ? occupancy_f16(CAP, op.opk, kind, pl) : occupancy_f32(CAP, op.opk, kind, pl));
         if (occ <= 0) occ = 1;

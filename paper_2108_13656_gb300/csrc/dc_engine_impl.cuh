@@ -407,7 +407,7 @@ __device__ __forceinline__ uint32_t block_incl_scan(uint32_t v, uint32_t* scratc
 // logarithm, each group's pairwise sum rounded once to 2^-24; min/max on the
 // floats.  LOGQ = true (HDR histogram forms): the fixed-point logarithm of every
 // pixel, summed exactly; min/max on the integers; the plane keeps the integers.
-template <int IN_DT, bool LOGQ, int CAP>
+template <int IN_DT, bool LOGQ, bool LEAN, int CAP>
 __device__ void tile_stats(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* ic,
                            const TileRect& t, const Beta& be, unsigned char* smem)
 {
@@ -424,6 +424,10 @@ __device__ void tile_stats(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* 
     float vmin = INFINITY, vmax = -INFINITY;
     int qmin = INT_MAX, qmax = INT_MIN;
     const float delta = P.delta;
+    // LEAN: only the reduction the call uses - the log-sum for the sigmoid (no min/max),
+    // the log range for the HDR histogram forms (no log-sum); otherwise both, for the
+    // stats record
+    constexpr bool SUM = !(LOGQ && LEAN), MM = !(!LOGQ && LEAN);
     consume_tile<IN_DT, false>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
         float v[G];
         if constexpr (LOGQ) {
@@ -431,7 +435,7 @@ __device__ void tile_stats(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* 
             for (int k = 0; k < G; ++k) {
                 if (k < n) {
                     const int q = ln_q24(Lv[k] + delta);
-                    acc += q;
+                    if constexpr (SUM) acc += q;
                     qmin = min(qmin, q);
                     qmax = max(qmax, q);
                     v[k] = __int_as_float(q);
@@ -445,8 +449,10 @@ __device__ void tile_stats(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* 
             for (int k = 0; k < G; ++k) {
                 if (k < n) {
                     v[k] = ln_fast(Lv[k] + delta);
-                    vmin = fminf(vmin, v[k]);
-                    vmax = fmaxf(vmax, v[k]);
+                    if constexpr (MM) {
+                        vmin = fminf(vmin, v[k]);
+                        vmax = fmaxf(vmax, v[k]);
+                    }
                     if (want_hist) atomicAdd(&S.hist[quant_u8(Lv[k])], 1u);
                 } else {
                     v[k] = 0.0f;
@@ -978,9 +984,9 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
                 GroupIO<IN_DT>::store(im, r, c, n, vec, Lv);
             });
         } else if constexpr (KIND == PK_STATS) {
-            tile_stats<IN_DT, false>(P, im, ic, tr, be, smem);
+            tile_stats<IN_DT, false, PL>(P, im, ic, tr, be, smem);  // (PL: only the log-sum)
         } else if constexpr (KIND == PK_STATS_LOG) {
-            tile_stats<IN_DT, true>(P, im, ic, tr, be, smem);
+            tile_stats<IN_DT, true, PL>(P, im, ic, tr, be, smem);  // (PL: only the log range)
         } else if constexpr (KIND == PK_LOGHIST) {
             tile_loghist<IN_DT, PL>(P, im, ic, tr, be, s_d, smem);
         } else if constexpr (KIND == PK_APPLY_G) {
@@ -1048,12 +1054,15 @@ int occupancy_one()
     return nb;
 }
 
-// Valid (operation, pass kind, reads a plane) triples, expanded for every batch
-// capacity.  8-bit input reads a plane only in the apply passes.
+// Valid (operation, pass kind, flag) triples, expanded for every batch capacity.  The
+// flag is "reads the plane" for the histogram and apply passes (8-bit input: only the
+// apply passes) and "lean reduction" for the statistics passes (8-bit input has no
+// STATS_LOG pass).
 #define DC_FOR_EACH_PASS(X)                                                                                  \
-    X(OPK_DECOLOR, PK_DECOLOR, false) X(OPK_GLOBAL, PK_STATS, false) X(OPK_GLOBAL, PK_STATS_LOG, false)      \
-        X(OPK_GLOBAL, PK_LOGHIST, false) X(OPK_GLOBAL, PK_LOGHIST, true) X(OPK_GLOBAL, PK_APPLY_G, false)    \
-        X(OPK_GLOBAL, PK_APPLY_G, true) X(OPK_LOCAL, PK_STATS_LOG, false) X(OPK_LOCAL, PK_BLOCKH, false)     \
+    X(OPK_DECOLOR, PK_DECOLOR, false) X(OPK_GLOBAL, PK_STATS, false) X(OPK_GLOBAL, PK_STATS, true)          \
+        X(OPK_GLOBAL, PK_STATS_LOG, false) X(OPK_GLOBAL, PK_STATS_LOG, true) X(OPK_GLOBAL, PK_LOGHIST, false) \
+        X(OPK_GLOBAL, PK_LOGHIST, true) X(OPK_GLOBAL, PK_APPLY_G, false) X(OPK_GLOBAL, PK_APPLY_G, true)     \
+        X(OPK_LOCAL, PK_STATS_LOG, false) X(OPK_LOCAL, PK_STATS_LOG, true) X(OPK_LOCAL, PK_BLOCKH, false)    \
         X(OPK_LOCAL, PK_BLOCKH, true) X(OPK_LOCAL, PK_CDF, false) X(OPK_LOCAL, PK_APPLY_L, false)            \
         X(OPK_LOCAL, PK_APPLY_L, true)
 
@@ -1061,7 +1070,7 @@ template <int IN_DT>
 int launch_dispatch(const void* batch, int cap, int opk, int kind, int ph, bool pl, LaunchShape ls, void* stream)
 {
 #define DC_CASE(OP, K, PL)                                                                               \
-    if constexpr (!PL || IN_DT != DC_U8 || K == PK_APPLY_G || K == PK_APPLY_L) {                        \
+    if constexpr (!PL || IN_DT != DC_U8 || K == PK_APPLY_G || K == PK_APPLY_L || K == PK_STATS) {       \
         if (opk == OP && kind == K && pl == PL) {                                                       \
             if (cap == kCapSmall) return launch_one<IN_DT, OP, K, kCapSmall, PL>(batch, ph, ls, stream); \
             if (cap == kCapMid) return launch_one<IN_DT, OP, K, kCapMid, PL>(batch, ph, ls, stream);     \
@@ -1077,7 +1086,7 @@ template <int IN_DT>
 int occupancy_dispatch(int cap, int opk, int kind, bool pl)
 {
 #define DC_CASE(OP, K, PL)                                                                 \
-    if constexpr (!PL || IN_DT != DC_U8 || K == PK_APPLY_G || K == PK_APPLY_L) {          \
+    if constexpr (!PL || IN_DT != DC_U8 || K == PK_APPLY_G || K == PK_APPLY_L || K == PK_STATS) { \
         if (opk == OP && kind == K && pl == PL) {                                         \
             if (cap == kCapSmall) return occupancy_one<IN_DT, OP, K, kCapSmall, PL>(); \
             if (cap == kCapMid) return occupancy_one<IN_DT, OP, K, kCapMid, PL>();     \

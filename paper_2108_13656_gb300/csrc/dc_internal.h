@@ -115,6 +115,9 @@ struct DcBatch {
     float gain_k, delta;
     int32_t gain_is_one;
     int32_t need_gray_hist;            // LDR: gray histogram wanted (HISTEQ or stats)
+    int32_t need_logsum;               // statistics pass: the log-sum is used (sigmoid, or a stats record)
+    int32_t need_minmax;               // statistics pass: min/max of the log are used (histogram
+                                       // coordinates of the HDR forms, or a stats record)
     int32_t block_s, radius, bins;
     uint32_t s_magic;                  // ceil(2^32 / block_s), 0 for block_s = 1: exact division of offsets < 2^16
     float alpha;
