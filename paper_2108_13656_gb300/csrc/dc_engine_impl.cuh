@@ -649,7 +649,6 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
     cta_sync();
     consume_tile<IN_DT, PLANE>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
         const int blk0 = group_in_block ? (int)__umulhi((uint32_t)(c - t.c0), magic) : 0;
-        float tq[G] = {};
         int cur = -1;
         uint32_t rc = 0u, rf = 0u;
 #pragma unroll
@@ -661,7 +660,6 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
                 } else {
                     // t - 1/2 from 2^-24 to 2^-20 units, rounded
                     const uint32_t q = coord_of<kLocTS>(Lv[k], is_log, delta, d);
-                    tq[k] = __uint_as_float(q);
                     x = min(max(((int)q - (1 << (kLocTS - 1)) + 8) >> (kLocTS - 20), 0), xmax);
                 }
                 int blk = blk0;
@@ -689,9 +687,9 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
             atomicAdd(&S.cnt[cur], rc);
             atomicAdd(&S.fs[cur], rf);
         }
-        // the apply pass reads the coordinate instead of the logarithm (HDR), or the
-        // luminance instead of recomputing it (8-bit input with a workspace plane)
-        if (is_log) GroupIO<IN_DT>::store_plane(im, r, c, n, vec, tq);
+        // 8-bit input with a workspace plane: the apply pass reads the luminance
+        // instead of recomputing it (an HDR plane keeps the fixed-point log, from
+        // which the apply pass takes the same coordinate)
         if constexpr (!PLANE) {
             if (plane_out) GroupIO<IN_DT>::store_plane(im, r, c, n, vec, Lv);
         }
@@ -866,9 +864,10 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
                     j = (int)(__float_as_uint(jf) - 0x4B000000u);
                     tt = Bu - (jf - 8388608.0f);
                 } else {
-                    // the plane holds the coordinate the histogram pass kept; an
-                    // image without a plane recomputes it from L
-                    const uint32_t q = PLANE ? __float_as_uint(Lv[k]) : coord_of<kLocTS>(Lv[k], false, delta, d);
+                    // the bin coordinate of the histogram pass, from the fixed-point
+                    // log the plane keeps, or from L for an image without a plane
+                    const uint32_t q = PLANE ? bin_coord<kLocTS>(__float_as_int(Lv[k]), d)
+                                             : coord_of<kLocTS>(Lv[k], false, delta, d);
                     const uint32_t jq = min(q >> kLocTS, (uint32_t)(B - 1));
                     j = (int)jq;
                     // (q - j 2^24) / 2^24 in [0, 1] through the float bit pattern of 1 + x
