@@ -137,11 +137,13 @@ __device__ __forceinline__ Derived derive(const DcImgCtrl* ic, long long N, bool
 // the fixed-point reciprocal m = floor(nb 2^(32+S) / Rs), i.e. floor(t 2^S) or one
 // unit below it (the reciprocal's truncation is below 2^-32 of it and dv < 2^30).
 // The product is at most nb 2^S < 2^31, so with m = mh 2^32 + ml it is
-// dv mh + floor(dv ml / 2^32) in 32-bit arithmetic, exactly.
+// dv mh + floor(dv ml / 2^32) in 32-bit arithmetic, exactly.  v is always one of the
+// image's own fixed-point logs, so vmin <= v <= vmax holds without a clamp (vmin and
+// vmax are their exact minimum and maximum; a value a ragged group's unused lane
+// carries gives an unused coordinate, computed in wrapping unsigned arithmetic).
 template <int S>
 __device__ __forceinline__ uint32_t bin_coord(int v, const Derived& d)
 {
-    v = min(max(v, d.vmin), d.vmax);
     const uint32_t dv = ((uint32_t)v - (uint32_t)d.vmin) >> d.sh;
     const unsigned long long m = S == kLocTS ? d.m_loc : d.m_glob;
     return dv * (uint32_t)(m >> 32) + __umulhi(dv, (uint32_t)m);
