@@ -38,6 +38,9 @@ NPIX = W * H
 METRIC = "Gpix/s and % of HBM roofline"
 L2_FLUSH_BYTES = 256 << 20
 ROT = 8  # input / output sets the steady-state loop rotates through
+# pass kernels of each call of the step, in launch order
+PASSES = {("u8", "global"): ["STATS", "APPLY_G"], ("f32", "global"): ["STATS", "APPLY_G"],
+          ("u8", "local"): ["BLOCKH", "CDF", "APPLY_L"], ("f32", "local"): ["STATS_LOG", "BLOCKH", "CDF", "APPLY_L"]}
 OPS = [  # (name, input variant, operation, output dtype, algorithmic bytes per pixel)
     ("u8_global", "u8", "global", "u8", 3 + 1),
     ("f32_global", "f32", "global", "f32", 12 + 4),
@@ -484,6 +487,27 @@ def run_native(args):
     op_ms = {name: float(np.mean([a.elapsed_time(b) for a, b in ev[name]])) for name, *_ in OPS}
     assert all(dc.query_status(w) == 0 for w in wss.values())
 
+    # per pass, in the stream (after the timed region): the library's profile mode
+    # stamps each pass's first tile start and last tile end with the GPU global timer;
+    # median of 7 calls, each after the L2-flushing write
+    per_pass = {}
+    dc.debug_profile(True)
+    try:
+        for name, var, op, _, _ in OPS:
+            durs = []
+            for rep in range(7):
+                flush.fill_(rep)
+                calls[name]()
+                prof = dc.read_profile(calls[name], 1)
+                durs.append([(b - a) / 1e3 for a, b in (q for q in prof["images"][0] if q)])
+            us = [round(float(v), 2) for v in np.median(np.array(durs), axis=0)]
+            kinds = PASSES[(var, op)]
+            in_bytes = imgs[var].nbytes
+            per_pass[name] = {"passes": kinds, "us": us,
+                              "first_pass_input_GBps": round(in_bytes / (us[0] * 1e-6) / 1e9, 1)}
+    finally:
+        dc.debug_profile(False)
+
     def reduce_max(v):
         if world == 1:
             return v
@@ -559,7 +583,8 @@ def run_native(args):
                              ROT, ROT * (sum(v.nbytes for v in imgs.values()) +
                                          sum(t.numel() * t.element_size() for t in outs.values())) / 1e9),
                    "per_op_sum_ms": sum(op_ms.values()),
-                   "parallelism": "replicas" if world > 1 else "single GPU", "per_op": per_op},
+                   "parallelism": "replicas" if world > 1 else "single GPU", "per_op": per_op,
+                   "per_pass": per_pass},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_kind": peak_kind, "traffic": traffic,
                      "algorithmic_bytes_per_launch": bpp * NPIX},
