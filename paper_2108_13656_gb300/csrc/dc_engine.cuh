@@ -660,12 +660,16 @@ struct SmemCdf {
     unsigned long long v[(kCdfChunk + 2 * kMaxRadius) * DC_MAX_BINS];
 };
 constexpr int kLocMaxCols = 1024;    // widest local tile
-// Slot stride of the apply pass's curve table in (value, slope) pairs: at least B
-// and 8 (mod 16), i.e. 16 banks between neighbouring slots; at most DC_MAX_BINS + 8.
-__host__ __device__ constexpr int apply_slot_stride(int bins) { return bins + ((24 - bins % 16) % 16); }
+// Geometry of the apply pass's curve table, fixed at compile time so that the four
+// curve reads of a pixel are one address plus immediate offsets: slots of
+// kTabSlot (value, slope) pairs - at least DC_MAX_BINS and 8 (mod 16), i.e. 16 banks
+// between neighbouring slots - and block rows of kLocMaxBlocksX + 2 slots.
+constexpr int kTabSlot = DC_MAX_BINS + ((24 - DC_MAX_BINS % 16) % 16);
+constexpr int kTabRow = (kLocMaxBlocksX + 2) * kTabSlot;
+static_assert(kTabSlot % 16 == 8, "neighbouring slots 16 banks apart");
 constexpr int kLocMaxRows = 64;      // tallest local tile (block_s)
 struct SmemApplyL {
-    float2 tab[3 * (kLocMaxBlocksX + 2) * (DC_MAX_BINS + 8)];  // per block and bin: (F at bin start, slope)
+    float2 tab[3 * kTabRow];  // per block and bin: (F at bin start, slope)
     // per tile column x: table slot offset of the left block and the weight bits, at
     // (x mod G) * (kLocMaxCols + 16) / G + x / G for groups of G pixels, so that the
     // lanes of a warp, one group each, read neighbouring entries

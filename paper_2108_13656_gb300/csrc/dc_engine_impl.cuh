@@ -788,10 +788,10 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
     const int nbx = (t.c1 - t.c0 + s - 1) / s;
     const int J0 = t.c0 / s;
     const int W2 = nbx + 2, B1 = B + 1;
-    // slot stride: SB = 8 (mod 16) pairs, so the same or a nearby bin of neighbouring
-    // blocks lands 16 banks away (lanes of a warp read neighbouring blocks' curves
-    // at similar bins)
-    const int SB = apply_slot_stride(B);
+    // slot stride 8 (mod 16) pairs: the same or a nearby bin of neighbouring blocks
+    // lands 16 banks away (lanes of a warp read neighbouring blocks' curves at
+    // similar bins)
+    constexpr int SB = kTabSlot;
     const float* E = reinterpret_cast<const float*>(P.ws + im.ws_hist + align_up((int64_t)Hb * Wb * B * 8, 256));
     {
         static_assert(DC_MAX_BINS <= 32, "one lane per bin");
@@ -823,7 +823,7 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
                     if (sc < W2) {
 #pragma unroll
                         for (int sr = 0; sr < 3; ++sr)
-                            S.tab[(sr * W2 + sc) * SB + j] = make_float2(e0[h][sr], e1[h][sr] - e0[h][sr]);
+                            S.tab[sr * kTabRow + sc * SB + j] = make_float2(e0[h][sr], e1[h][sr] - e0[h][sr]);
                     }
                 }
             }
@@ -841,10 +841,10 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
     for (int k = threadIdx.x; k < t.r1 - t.r0; k += kThreads) {
         const float fy = fmaf((float)(t.r0 + k) + 0.5f, inv_s, -0.5f);
         const float fly = floorf(fy);
-        S.row[k] = make_int2(((int)fly - (I - 1)) * W2 * SB, __float_as_int(fy - fly));
+        S.row[k] = make_int2(((int)fly - (I - 1)) * kTabRow, __float_as_int(fy - fly));
     }
     const float delta = P.delta, Bf = (float)B, alpha = P.alpha;
-    const int WSB = W2 * SB;
+    constexpr int WSB = kTabRow;
     cta_sync();
     auto body = [&](auto alpha_one, auto out_dt) {
         // output values of one group in place
