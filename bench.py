@@ -377,6 +377,36 @@ def precision_8k(dev, peak: float) -> dict:
 
 
 # ------------------------------------------------------------------ serving ----
+def host_link_gbps(dev, nbytes: int = 256 << 20, reps: int = 5) -> dict:
+    """Pinned host<->device copy bandwidth right now (the serving loop's bound; the
+    link is shared with the machine's other GPUs): one direction at a time, then both
+    at once on two streams."""
+    import torch
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    ho = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d2 = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+
+    def timed(fn, nb):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize(dev)
+        return round(nb * reps / (time.perf_counter() - t0) / 1e9, 1)
+
+    def both():
+        with torch.cuda.stream(s1):
+            d.copy_(h, non_blocking=True)
+        with torch.cuda.stream(s2):
+            ho.copy_(d2, non_blocking=True)
+
+    return {"h2d": timed(lambda: d.copy_(h, non_blocking=True), nbytes),
+            "d2h": timed(lambda: ho.copy_(d, non_blocking=True), nbytes),
+            "both": timed(both, 2 * nbytes)}
+
+
 def serving(dev, n_requests: int, rate: float) -> dict:
     """The serving trace (Poisson arrivals, sizes 720p..8K, 70% u8 / 30% f16, half
     global, half local, 16 GB budget) through the continuous-batching loop and through
@@ -387,9 +417,10 @@ def serving(dev, n_requests: int, rate: float) -> dict:
     warm = serve.make_trace(min(200, n_requests), rate, seed=6)
     serve.serve_batched(warm, pool, device=dev)
     serve.serve_serial(warm, pool, device=dev)
+    link = host_link_gbps(dev)
     b = serve.serve_batched(trace, pool, budget_bytes=16 << 30, device=dev).summary()
     s = serve.serve_serial(trace, pool, device=dev).summary()
-    return {"requests": n_requests, "rate_per_s": rate, "budget_gb": 16,
+    return {"requests": n_requests, "rate_per_s": rate, "budget_gb": 16, "host_link_gbps": link,
             "offered_gpix_s": sum(r.size[0] * r.size[1] for r in trace) / (trace[-1].t_arrive - trace[0].t_arrive) / 1e9,
             "batched": b, "serial_plain": s,
             "note": "latency = host-observed completion (event after the device-to-host copy) minus arrival; "
