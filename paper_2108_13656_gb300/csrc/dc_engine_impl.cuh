@@ -94,17 +94,27 @@ __device__ __forceinline__ TileRect tile_rect(const DcBatch<CAP>& P, const DcIma
 
 
 // mu, lmin, lmax from the exact integer accumulators of a finished stats pass
-// (fixed_log: the min and max are of the 2^-24 fixed-point logarithms).
-__device__ __forceinline__ Derived derive(const DcImgCtrl* ic, long long N, bool fixed_log, int bins)
+// (fixed_log: the min and max are of the 2^-24 fixed-point logarithms), and the
+// fixed-point reciprocal of the log range for the operator's histogram: the local
+// operator's (bins) or the global one's (256 bins).  One thread of each CTA runs
+// this while the others wait, so only what the pass uses is computed: mu when the
+// log-sum was kept, the reciprocal by a 64-bit division (nb 2^(32+S) <= 2^62).
+__device__ __forceinline__ Derived derive(const DcImgCtrl* ic, long long N, bool fixed_log, bool want_mu,
+                                          bool local, int bins)
 {
     Derived d;
-    const long long sum = (long long)ld_cg_u64(&ic->logsum);
-    const long long q = sum / N, rem = sum - q * N;
     constexpr float unit = 1.0f / (float)(1 << kLogFixedShift);
-    d.mu = (__ll2float_rn(q) + __ll2float_rn(rem) / __ll2float_rn(N)) * unit;
-    d.exp_mu = expf(d.mu);
+    d.mu = 0.0f;
+    d.exp_mu = 1.0f;
+    if (want_mu) {
+        const long long sum = (long long)ld_cg_u64(&ic->logsum);
+        const long long q = sum / N, rem = sum - q * N;
+        d.mu = (__ll2float_rn(q) + __ll2float_rn(rem) / __ll2float_rn(N)) * unit;
+        d.exp_mu = expf(d.mu);
+    }
     d.vmin = d.vmax = d.sh = 0;
     d.Rs = 2u;
+    d.m_loc = d.m_glob = 0ull;
     if (fixed_log) {
         const int vmax = (int)(ld_cg_u32(&ic->lmax_ord) ^ 0x80000000u);
         const int vmin = (int)(~ld_cg_u32(&ic->lmin_nord) ^ 0x80000000u);
@@ -123,12 +133,15 @@ __device__ __forceinline__ Derived derive(const DcImgCtrl* ic, long long N, bool
             d.vmin = vmin - 1;
             d.vmax = vmin + 1;
         }
+        static_assert(DC_MAX_BINS <= 32 && 32 + kLocTS + 5 <= 63 && 32 + kGlobTS + 8 <= 63, "reciprocals fit in 64 bits");
+        if (local)
+            d.m_loc = ((unsigned long long)(unsigned)max(bins, 1) << (32 + kLocTS)) / d.Rs;
+        else
+            d.m_glob = (256ull << (32 + kGlobTS)) / d.Rs;
     } else {
         d.lmin = ord_dec(~ld_cg_u32(&ic->lmin_nord));
         d.lmax = ord_dec(ld_cg_u32(&ic->lmax_ord));
     }
-    d.m_loc = (unsigned long long)(((unsigned __int128)(unsigned)max(bins, 1) << (32 + kLocTS)) / d.Rs);
-    d.m_glob = (unsigned long long)(((unsigned __int128)256u << (32 + kGlobTS)) / d.Rs);
     return d;
 }
 
@@ -972,7 +985,9 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
         const DcImage& im = P.img[img];
         DcImgCtrl* ic = img_ctrl(P.ctrl, img);
         if (need_d && img != cached) {
-            if (threadIdx.x == 0) s_d = derive(ic, (long long)im.prow * (long long)im.pcol, fixed_log, P.bins);
+            if (threadIdx.x == 0)
+                s_d = derive(ic, (long long)im.prow * (long long)im.pcol, fixed_log, P.need_logsum != 0,
+                             OPK == OPK_LOCAL, P.bins);
             cta_sync();
             cached = img;
         }
