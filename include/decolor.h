@@ -261,7 +261,10 @@ DC_API int dc_debug_read_profile(const void* ws, int32_t n_img, uint64_t* out, v
 /* Local tile width (pixels along a block row) that a dc_decolorize_tonemap_local
  * call on n images of heights[k] x widths[k] with this block_s would use on a GPU
  * with n_sm SMs, given the current tuning for in_dtype (0 width = automatic, see
- * dc_tuning).  Host only; *cols receives the width. */
+ * dc_tuning).  The tiling of Sec. III-B-2's block grid into launch tiles changes no
+ * result; the paper has no counterpart.  Host only, thread-safe; *cols receives the
+ * width.  Errors: DC_ERR_INVALID_ARG for null pointers, n outside 1..DC_MAX_BATCH,
+ * block_s outside 1..64, n_sm < 1, a non-positive size or an unknown in_dtype. */
 DC_API int dc_local_tile_cols(int32_t block_s, const int32_t* heights, const int32_t* widths, int32_t n,
                               int32_t in_dtype, int32_t n_sm, int32_t* cols);
 

@@ -217,3 +217,9 @@ def test_tuned_local_tile_width_is_kept(abi):
         abi.local_tile_cols([(0, 10)])
     with pytest.raises(abi.DcError):
         abi.local_tile_cols([(10, 10)], block_s=65)
+
+
+def test_host_pipeline_rejects_zero_depth():
+    from paper_2108_13656_gb300.pipeline import HostPipeline
+    with pytest.raises(ValueError):
+        HostPipeline({}, {}, [], depth=0)
