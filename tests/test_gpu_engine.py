@@ -193,3 +193,23 @@ def test_registered_workspace_stays_clean(dc):
             assert torch.equal(a, b), "call %d (%s) differs" % (i, op)
         assert torch.equal(res[0][1], res[1][1]), "call %d (%s) statistics differ" % (i, op)
     assert dc.query_status(reg) == 0
+
+
+@pytest.mark.parametrize("mode", ["sigmoid", "histeq"])
+@pytest.mark.parametrize("in_dt", [np.uint8, np.float16, np.float32])
+def test_stats_record_changes_no_output(dc, mode, in_dt):
+    """Without a stats record the statistics pass keeps only the reduction the curve
+    uses (a different kernel variant); the output bits are the same as with one."""
+    import torch
+    from paper_2108_13656_gb300 import synth
+    img = synth.s_ldr(517, 389, 8) if in_dt == np.uint8 else synth.s_hdr(517, 389, 8).astype(in_dt)
+    x = to_dev(img)
+    y0 = torch.empty((389, 517), dtype=torch.float32, device="cuda")
+    y1 = torch.empty_like(y0)
+    st = torch.zeros(dc.STATS_BYTES, dtype=torch.uint8, device="cuda")
+    dc.decolorize_tonemap_global(x, y0, mode=mode)
+    dc.decolorize_tonemap_global(x, y1, mode=mode, stats=st)
+    torch.cuda.synchronize()
+    assert torch.equal(y0, y1)
+    rec = dc.parse_stats(st, 1)[0]
+    assert rec["lmin"] <= rec["mu"] <= rec["lmax"]
