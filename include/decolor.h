@@ -26,10 +26,15 @@
  *    stream).  They never allocate device memory and never synchronise.  Input must
  *    not overlap output.  Two calls that share a workspace must be ordered (same
  *    stream or an event between them).
- *  - Return value: DC_OK or a DC_ERR_* code; nothing is enqueued when a call
- *    returns an error.  A call is a short chain of passes (one persistent kernel
- *    each, chained with programmatic dependent launch on `stream`); no kernel ever
- *    waits for another CTA, so a call cannot hang on the device.
+ *  - Return value: DC_OK or a DC_ERR_* code.  A call is a short chain of passes
+ *    (one persistent kernel each, chained with programmatic dependent launch on
+ *    `stream`); no kernel ever waits for another CTA, so a call cannot hang on the
+ *    device.  Argument errors (DC_ERR_INVALID_ARG, DC_ERR_UNSUPPORTED_DTYPE,
+ *    DC_ERR_WORKSPACE, DC_ERR_TOO_MANY) are found before anything is enqueued.
+ *    DC_ERR_CUDA from a failed memset or launch can come after earlier passes of
+ *    the same call were enqueued: the outputs are then incomplete, and the next
+ *    call on that workspace (registered or not) clears the counters those passes
+ *    left before it starts.
  *  - Vector path: when an image's data pointers and row strides are 16-byte
  *    aligned, pixels move in 16-byte vectors; otherwise the image takes a scalar
  *    path with the same results.
@@ -270,6 +275,14 @@ DC_API int dc_local_tile_cols(int32_t block_s, const int32_t* heights, const int
 
 /* Number of kernels the last successful call on this thread enqueued. */
 DC_API int dc_last_launch_count(void);
+
+/* Test hook for the error paths (host side; the paper has no counterpart): for
+ * k > 0 the k-th kernel launch of every later call (counted from 1 within the
+ * call) is not issued and the call returns DC_ERR_CUDA after enqueueing the passes
+ * before it; k = 0 turns it off.  The library starts with the value of the
+ * environment variable DC_FAIL_LAUNCH, else 0.  Returns DC_ERR_INVALID_ARG for
+ * k < 0.  No GPU fault is involved: the kernel is simply not launched. */
+DC_API int dc_debug_fail_launch(int32_t k);
 
 /* Bounds-checked build (compiled with -DDC_BOUNDS_CHECK): *checked = 1 and *flags =
  * the OR of the buffers some kernel tried to access outside (1 input, 2 output,

@@ -23,6 +23,7 @@ from ._abi import (  # noqa: F401
     PreparedCall,
     Workspace,
     debug_bounds,
+    debug_fail_launch,
     debug_profile,
     decolorize,
     decolorize_tonemap_global,

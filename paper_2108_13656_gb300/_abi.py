@@ -84,6 +84,7 @@ _SIGS = {
     "dc_debug_profile": (ctypes.c_int, [ctypes.c_int32]),
     "dc_debug_read_profile": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "dc_last_launch_count": (ctypes.c_int, []),
+    "dc_debug_fail_launch": (ctypes.c_int, [ctypes.c_int32]),
     "dc_local_tile_cols": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p]),
     "dc_debug_bounds": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p]),
@@ -406,6 +407,14 @@ def local_tile_cols(sizes, block_s: int = 32, in_dtype: int = DC_U8, n_sm: int =
 
 def last_launch_count() -> int:
     return int(load().dc_last_launch_count())
+
+
+def debug_fail_launch(k: int):
+    """Make the k-th kernel launch of every later call fail before it is issued
+    (k = 0: off).  A host-side test hook for the error paths."""
+    rc = load().dc_debug_fail_launch(int(k))
+    if rc != DC_OK:
+        raise DcError(rc, "dc_debug_fail_launch")
 
 
 def debug_bounds() -> tuple[bool, int]:

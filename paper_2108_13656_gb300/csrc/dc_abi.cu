@@ -3,8 +3,10 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cfloat>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -53,7 +55,8 @@ std::unordered_map<uintptr_t, CleanWs> g_clean;  // guarded by g_mu
 
 // For a call whose control block ends at `need` bytes: whether it can skip the
 // clearing memset and whether its last pass must clear the block (registered
-// workspace).  Records what the call leaves.
+// workspace).  Nothing is recorded yet: the block is dirty as soon as a pass runs,
+// and clean again only once the last pass has been enqueued (finish_clear).
 void plan_clear(const void* ws, size_t need, bool profiling, bool* skip_memset, bool* clear_at_end)
 {
     std::lock_guard<std::mutex> lk(g_mu);
@@ -66,8 +69,32 @@ void plan_clear(const void* ws, size_t need, bool profiling, bool* skip_memset, 
     }
     *skip_memset = !profiling && it->second.clean >= need;
     *clear_at_end = !profiling;
-    it->second.clean = profiling ? 0 : need;
+    it->second.clean = 0;  // until every pass of the call is enqueued
 }
+
+// After the launches of a call's group: with every pass enqueued, the last one
+// leaves the control block zero (`clear_at_end`); after a failed memset or launch
+// the block holds partial counters, so the next call on the workspace clears it
+// with a memset.
+void finish_clear(const void* ws, size_t need, bool ok, bool clear_at_end)
+{
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_clean.find(reinterpret_cast<uintptr_t>(ws));
+    if (it == g_clean.end()) return;
+    it->second.clean = (ok && clear_at_end) ? need : 0;
+}
+
+// Launch failure injection for tests of the error paths (host side only): when
+// k > 0, the k-th kernel launch of every later call returns DC_ERR_CUDA without
+// being issued.  Set by dc_debug_fail_launch or, at load, by DC_FAIL_LAUNCH.
+std::atomic<int> g_fail_launch{0};
+struct FailLaunchInit {
+    FailLaunchInit()
+    {
+        const char* e = std::getenv("DC_FAIL_LAUNCH");
+        if (e) g_fail_launch.store(std::atoi(e));
+    }
+} g_fail_launch_init;
 int g_profile = 0;
 thread_local int g_last_launches = 0;
 thread_local int g_call_launches = 0;
@@ -447,21 +474,25 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
     b->ctrl = reinterpret_cast<DcCtrl*>(ws + kHeaderBytes);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     bool skip_memset = false, clear_at_end = false;
-    plan_clear(ws, (size_t)(kHeaderBytes + ctrl_bytes), b->profile != 0, &skip_memset, &clear_at_end);
+    const size_t block_end = (size_t)(kHeaderBytes + ctrl_bytes);
+    plan_clear(ws, block_end, b->profile != 0, &skip_memset, &clear_at_end);
     b->reset_bytes = clear_at_end ? (int32_t)ctrl_bytes : 0;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        finish_clear(ws, block_end, false, clear_at_end);
+        delete b;
+        return DC_ERR_CUDA;
+    }
     if (!skip_memset) {
-        const size_t clear_bytes = first ? (size_t)(kHeaderBytes + ctrl_bytes) : (size_t)ctrl_bytes;
+        const size_t clear_bytes = first ? block_end : (size_t)ctrl_bytes;
         uint8_t* clear_ptr = first ? ws : ws + kHeaderBytes;
         if (cudaMemsetAsync(clear_ptr, 0, clear_bytes, st) != cudaSuccess) {
+            finish_clear(ws, block_end, false, clear_at_end);
             delete b;
             return DC_ERR_CUDA;
         }
     }
-    int dev = 0, nsm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-        delete b;
-        return DC_ERR_CUDA;
-    }
+    const int fail_at = g_fail_launch.load(std::memory_order_relaxed);
     int rc = DC_OK;
     for (int ph = 0; ph < b->n_phase && rc == DC_OK; ++ph) {
         const int kind = b->phase_kind[ph];
@@ -477,7 +508,9 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
         LaunchShape ls;
         ls.threads = 256;
         ls.grid = (int)std::min<int64_t>(b->seg_start[ph][n], (int64_t)per_sm * nsm);
-        if (in_dt == DC_U8)
+        if (fail_at > 0 && g_call_launches + 1 == fail_at)
+            rc = DC_ERR_CUDA;  // injected failure: this pass is not issued
+        else if (in_dt == DC_U8)
             rc = launch_engine_u8(b, CAP, op.opk, kind, ph, pl, ls, stream);
         else if (in_dt == DC_F16)
             rc = launch_engine_f16(b, CAP, op.opk, kind, ph, pl, ls, stream);
@@ -485,6 +518,7 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
             rc = launch_engine_f32(b, CAP, op.opk, kind, ph, pl, ls, stream);
         if (rc == DC_OK) ++g_call_launches;
     }
+    finish_clear(ws, block_end, rc == DC_OK, clear_at_end);
     delete b;
     return rc;
 }
@@ -763,6 +797,13 @@ DC_API int dc_local_tile_cols(int32_t block_s, const int32_t* heights, const int
 }
 
 DC_API int dc_last_launch_count(void) { return g_last_launches; }
+
+DC_API int dc_debug_fail_launch(int32_t k)
+{
+    if (k < 0) return DC_ERR_INVALID_ARG;
+    g_fail_launch.store(k);
+    return DC_OK;
+}
 
 DC_API int dc_debug_bounds(uint32_t* flags, int32_t* checked)
 {

@@ -8,7 +8,7 @@
 // 4 f32 pixels = 48 bytes) with 8- or 16-byte vector loads when the image is
 // 16-byte aligned; everything else (ragged row tails, unaligned images) takes a
 // per-pixel path with identical arithmetic.  All arithmetic is binary32; every
-// cross-thread reduction is exact integer arithmetic (the log-sum in 2^-20 fixed
+// cross-thread reduction is exact integer arithmetic (the log-sum in 2^-24 fixed
 // point, min/max on ordered bit patterns, histograms as counts), so results do
 // not depend on the launch shape.
 #pragma once

@@ -62,7 +62,7 @@ struct DcImage {                 // 96 bytes
 // pass.  done[] is not used by the pass kernels.
 struct DcImgCtrl {
     uint32_t done[kMaxPhases];
-    unsigned long long logsum;   // two's complement, units of 2^-20
+    unsigned long long logsum;   // two's complement, units of 2^-24
     uint32_t lmax_ord;           // ordered encoding of max ln(L+delta): of the float
                                  // (PK_STATS) or of the 2^-24 fixed-point value (PK_STATS_LOG)
     uint32_t lmin_nord;          // bitwise NOT of the ordered encoding of the min

@@ -37,6 +37,58 @@ class Request:
     dtype: str       # "u8" (sRGB, output u8) or "f16" (linear HDR, output f32)
     size: tuple      # (width, height)
     variant: int     # which pooled image of that size and type
+    t_cancel: float | None = None  # the client withdraws the request at this time (if still waiting)
+
+
+class Admission:
+    """FIFO admission of requests against a device-memory budget (host logic only).
+
+    `capacity` = budget minus what the server holds for itself (its per-stream
+    workspaces).  A request whose own bytes exceed the capacity can never be admitted:
+    it is rejected when it arrives, so it cannot block the requests behind it.  A
+    waiting request can be cancelled; once admitted its work is on the device and it
+    completes normally."""
+
+    def __init__(self, budget_bytes: int, reserved_bytes: int = 0, max_batch: int = 64):
+        self.capacity = int(budget_bytes) - int(reserved_bytes)
+        if self.capacity <= 0:
+            raise ValueError("the budget does not cover the server's own buffers")
+        self.max_batch = max_batch
+        self.waiting = collections.deque()  # (request, bytes)
+        self.used = 0
+        self.peak = 0
+        self.rejected = {}       # rid -> reason
+        self.cancelled = set()
+
+    def arrive(self, r: Request, need: int) -> bool:
+        if need > self.capacity:
+            self.rejected[r.rid] = "needs %d bytes, more than the budget's %d" % (need, self.capacity)
+            return False
+        self.waiting.append((r, need))
+        return True
+
+    def cancel(self, rid: int) -> bool:
+        """Withdraw a waiting request; False if it is not waiting (admitted, done or unknown)."""
+        for k, (r, _) in enumerate(self.waiting):
+            if r.rid == rid:
+                del self.waiting[k]
+                self.cancelled.add(rid)
+                return True
+        return False
+
+    def admit(self) -> list:
+        """Requests that fit now, in arrival order, at most max_batch: [(request, bytes)]."""
+        out = []
+        while self.waiting and len(out) < self.max_batch and self.used + self.waiting[0][1] <= self.capacity:
+            r, need = self.waiting.popleft()
+            self.used += need
+            out.append((r, need))
+        self.peak = max(self.peak, self.used)
+        return out
+
+    def release(self, nbytes: int):
+        self.used -= nbytes
+        assert self.used >= 0
 
 
 def make_trace(n: int, rate: float, seed: int, sizes=SERVE_SIZES, p_u8: float = 0.7, p_global: float = 0.5,
@@ -127,18 +179,23 @@ def request_bytes(r: Request, lp=None) -> int:
 
 @dataclasses.dataclass
 class ServeResult:
-    latency_s: np.ndarray      # per request, in request order
+    latency_s: np.ndarray      # per completed request, in request order
     makespan_s: float          # first arrival to last completion
-    pixels: int
+    pixels: int                # of the completed requests
     batches: int
     max_inflight_bytes: int
     outputs: dict | None       # rid -> host tensor, when kept
-    sizes: list | None = None  # per request (width, height), in request order
-    queue_s: np.ndarray | None = None  # per request: arrival to launch of its batch
+    sizes: list | None = None  # per completed request (width, height), in request order
+    queue_s: np.ndarray | None = None  # per completed request: arrival to launch of its batch
+    rejected: dict = dataclasses.field(default_factory=dict)  # rid -> reason (larger than the budget)
+    cancelled: list = dataclasses.field(default_factory=list)  # rids withdrawn while waiting
 
     def summary(self) -> dict:
         lat = self.latency_s * 1e3
-        out = {"requests": int(len(lat)), "p50_ms": float(np.percentile(lat, 50)),
+        if len(lat) == 0:
+            return {"requests": 0, "rejected": len(self.rejected), "cancelled": len(self.cancelled)}
+        out = {"requests": int(len(lat)), "rejected": len(self.rejected), "cancelled": len(self.cancelled),
+               "p50_ms": float(np.percentile(lat, 50)),
                "p99_ms": float(np.percentile(lat, 99)), "mean_ms": float(lat.mean()),
                "gpix_s": self.pixels / self.makespan_s / 1e9, "makespan_s": self.makespan_s,
                "batches": self.batches, "max_inflight_gb": self.max_inflight_bytes / 1e9}
@@ -167,95 +224,122 @@ def _wait_until(t_abs: float):
             time.sleep(d - 1e-4)
 
 
+def schedule(trace, adm: Admission, n_streams: int, launch, done, retire, clock=time.perf_counter,
+             wait_until=None, idle=None, bytes_fn=None) -> dict:
+    """The continuous-batching loop, with the device side passed in.
+
+    launch(si, admitted) enqueues one batch [(request, bytes)] on stream si and
+    returns a handle; done(handle) says whether it has completed (a stream completes
+    its batches in order, so only the oldest batch of each stream is polled);
+    retire(handle) runs once per completed batch.  Arrivals are admitted through
+    `adm` (oversize requests are rejected there), cancellations of waiting requests
+    take effect at their t_cancel.  Returns per-request latencies and queueing times
+    (completed requests only) and the number of batches."""
+    wait_until = wait_until or _wait_until
+    idle = idle or (lambda: time.sleep(2e-5))
+    bytes_fn = bytes_fn or request_bytes
+    pending = collections.deque(sorted(trace, key=lambda r: r.t_arrive))
+    cancels = collections.deque(sorted((r.t_cancel, r.rid) for r in trace if r.t_cancel is not None))
+    inflight = [collections.deque() for _ in range(n_streams)]
+    lat, queued = {}, {}
+    batches = 0
+    t0 = clock()
+    while pending or adm.waiting or any(inflight):
+        now = clock() - t0
+        while pending and pending[0].t_arrive <= now:
+            r = pending.popleft()
+            adm.arrive(r, bytes_fn(r))
+        while cancels and cancels[0][0] <= now:
+            adm.cancel(cancels.popleft()[1])
+        for q in inflight:
+            while q and done(q[0][0]):
+                h, items, nbytes = q.popleft()
+                t_done = clock() - t0
+                for r, _ in items:
+                    lat[r.rid] = t_done - r.t_arrive
+                retire(h)
+                adm.release(nbytes)
+        admitted = adm.admit()
+        if admitted:
+            t_launch = clock() - t0
+            for r, _ in admitted:
+                queued[r.rid] = t_launch - r.t_arrive
+            si = min(range(n_streams), key=lambda k: len(inflight[k]))
+            inflight[si].append((launch(si, admitted), admitted, sum(n for _, n in admitted)))
+            batches += 1
+            continue
+        # nothing to launch: wait for the next arrival or completion
+        if pending and not any(inflight) and not adm.waiting:
+            wait_until(t0 + pending[0].t_arrive)
+        else:
+            idle()
+    return {"lat": lat, "queued": queued, "batches": batches}
+
+
+def _result(trace, lat, queued, batches, peak, outputs, rejected, cancelled) -> "ServeResult":
+    done = sorted((r for r in trace if r.rid in lat), key=lambda r: r.rid)
+    makespan = (max(r.t_arrive + lat[r.rid] for r in done) - min(r.t_arrive for r in done)) if done else 0.0
+    return ServeResult(np.array([lat[r.rid] for r in done]), makespan, sum(r.size[0] * r.size[1] for r in done),
+                       batches, peak, outputs, [r.size for r in done], np.array([queued[r.rid] for r in done]),
+                       dict(rejected), sorted(cancelled))
+
+
+WORKSPACE_BYTES = 128 << 20  # per stream, sized up front
+
+
 def serve_batched(trace, pool: HostPool, budget_bytes: int = 16 << 30, n_streams: int = 4, max_batch: int = 64,
                   keep_outputs: bool = False, device=None) -> ServeResult:
-    """Continuous batching over the trace (arrival times are honoured in real time)."""
+    """Continuous batching over the trace (arrival times are honoured in real time).
+    The per-stream workspaces count against the budget."""
     import torch
     dev = torch.device(device or "cuda")
     streams = [torch.cuda.Stream(device=dev) for _ in range(n_streams)]
     wss = [_abi.Workspace(device=dev) for _ in range(n_streams)]
     for w in wss:
-        w.get(128 << 20)  # sized up front: growing it inside the loop would allocate
+        w.get(WORKSPACE_BYTES)  # sized up front: growing it inside the loop would allocate
+    adm = Admission(budget_bytes, reserved_bytes=sum(w.buf.numel() for w in wss), max_batch=max_batch)
     outpool, devpool = pool.outpool, pool.devpool
-    pending = collections.deque(sorted(trace, key=lambda r: r.t_arrive))
-    waiting = collections.deque()
-    # per stream, in launch order: (event, [(req, x, y, host_out)], bytes).  A stream
-    # completes its batches in order, so only the oldest of each is polled: the cost
-    # of a loop iteration does not grow with the number of batches in flight.
-    inflight = [collections.deque() for _ in range(n_streams)]
-    lat = {}
     outputs = {} if keep_outputs else None
-    used = peak = 0
-    batches = 0
-    queued = {}
+
+    def launch(si, admitted):
+        s = streams[si]
+        with torch.cuda.stream(s):
+            items = []
+            for r, _ in admitted:
+                hx = pool.host_input(r)
+                x = devpool.get(hx.shape, hx.dtype)
+                x.copy_(hx, non_blocking=True)
+                y = devpool.get(hx.shape[:2], out_dtype(r))
+                items.append((r, x, y, outpool.get(tuple(hx.shape[:2]), out_dtype(r))))
+            for op in ("global", "local"):
+                sel = [(x, y) for r, x, y, _ in items if r.op == op]
+                if sel:
+                    _abi.PreparedCall(op, [a for a, _ in sel], [b for _, b in sel], workspace=wss[si])(s)
+            for r, x, y, ho in items:
+                ho.copy_(y, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        return ev, items
+
+    def retire(h):
+        for r, x, y, ho in h[1]:
+            if keep_outputs:
+                outputs[r.rid] = ho.clone()
+            outpool.put(ho)
+            devpool.put(x)
+            devpool.put(y)
+
     torch.cuda.synchronize(dev)
     gc_was = gc.isenabled()
     gc.collect()
     gc.disable()  # a collection pause would stall every request in flight
-    t0 = time.perf_counter()
-    while pending or waiting or any(inflight):
-        now = time.perf_counter() - t0
-        while pending and pending[0].t_arrive <= now:
-            waiting.append(pending.popleft())
-        # retire finished batches
-        for q in inflight:
-            while q and q[0][0].query():
-                _, items, nbytes = q.popleft()
-                t_done = time.perf_counter() - t0
-                for r, x, y, ho in items:
-                    lat[r.rid] = t_done - r.t_arrive
-                    if keep_outputs:
-                        outputs[r.rid] = ho.clone()
-                    outpool.put(ho)
-                    devpool.put(x)
-                    devpool.put(y)
-                used -= nbytes
-        # admit what fits, FIFO, and launch it as one batch per operation
-        admitted = []
-        while waiting and len(admitted) < max_batch:
-            need = request_bytes(waiting[0])
-            if used + need > budget_bytes:
-                break
-            used += need
-            admitted.append((waiting.popleft(), need))
-        peak = max(peak, used)
-        if admitted:
-            t_launch = time.perf_counter() - t0
-            for r, _ in admitted:
-                queued[r.rid] = t_launch - r.t_arrive
-            si = min(range(n_streams), key=lambda k: len(inflight[k]))
-            s = streams[si]
-            with torch.cuda.stream(s):
-                items = []
-                for r, _ in admitted:
-                    hx = pool.host_input(r)
-                    x = devpool.get(hx.shape, hx.dtype)
-                    x.copy_(hx, non_blocking=True)
-                    y = devpool.get(hx.shape[:2], out_dtype(r))
-                    items.append((r, x, y, outpool.get(tuple(hx.shape[:2]), out_dtype(r))))
-                for op in ("global", "local"):
-                    sel = [(x, y) for r, x, y, _ in items if r.op == op]
-                    if sel:
-                        _abi.PreparedCall(op, [a for a, _ in sel], [b for _, b in sel], workspace=wss[si])(s)
-                for r, x, y, ho in items:
-                    ho.copy_(y, non_blocking=True)
-                ev = torch.cuda.Event()
-                ev.record(s)
-            inflight[si].append((ev, items, sum(n for _, n in admitted)))
-            batches += 1
-            continue
-        # nothing to launch: wait for the next arrival or completion
-        if pending and not any(inflight) and not waiting:
-            _wait_until(t0 + pending[0].t_arrive)
-        else:
-            time.sleep(2e-5)
-    if gc_was:
-        gc.enable()
-    makespan = max(r.t_arrive + lat[r.rid] for r in trace) - min(r.t_arrive for r in trace)
-    order = sorted(trace, key=lambda r: r.rid)
-    return ServeResult(np.array([lat[r.rid] for r in order]), makespan,
-                       sum(r.size[0] * r.size[1] for r in trace), batches, peak, outputs, [r.size for r in order],
-                       np.array([queued[r.rid] for r in order]))
+    try:
+        res = schedule(trace, adm, n_streams, launch, lambda h: h[0].query(), retire)
+    finally:
+        if gc_was:
+            gc.enable()
+    return _result(trace, res["lat"], res["queued"], res["batches"], adm.peak, outputs, adm.rejected,
+                   adm.cancelled)
 
 
 def serve_serial(trace, pool: HostPool, keep_outputs: bool = False, device=None) -> ServeResult:
@@ -274,8 +358,12 @@ def serve_serial(trace, pool: HostPool, keep_outputs: bool = False, device=None)
     gc.disable()
     queued = {}
     t0 = time.perf_counter()
+    cancelled = []
     for r in sorted(trace, key=lambda q: q.t_arrive):
         _wait_until(t0 + r.t_arrive)
+        if r.t_cancel is not None and time.perf_counter() - t0 >= r.t_cancel:
+            cancelled.append(r.rid)  # withdrawn before the server got to it
+            continue
         queued[r.rid] = time.perf_counter() - t0 - r.t_arrive
         hx = pool.host_input(r)
         x = devpool.get(hx.shape, hx.dtype)
@@ -293,8 +381,4 @@ def serve_serial(trace, pool: HostPool, keep_outputs: bool = False, device=None)
         outpool.put(ho)
     if gc_was:
         gc.enable()
-    makespan = max(r.t_arrive + lat[r.rid] for r in trace) - min(r.t_arrive for r in trace)
-    order = sorted(trace, key=lambda r: r.rid)
-    return ServeResult(np.array([lat[r.rid] for r in order]), makespan,
-                       sum(r.size[0] * r.size[1] for r in trace), len(trace), 0, outputs, [r.size for r in order],
-                       np.array([queued[r.rid] for r in order]))
+    return _result(trace, lat, queued, len(lat), 0, outputs, {}, cancelled)

@@ -43,7 +43,7 @@ def test_alone_equals_in_mix(setup):
 def test_tight_budget_admits_in_order_and_matches(setup):
     import torch
     m, serve, trace, pool = setup
-    budget = 3 * max(serve.request_bytes(r) for r in trace)
+    budget = 2 * (serve.WORKSPACE_BYTES + 4096) + 3 * max(serve.request_bytes(r) for r in trace)  # 2 workspaces + 3 requests
     res = serve.serve_batched(trace[:60], pool, budget_bytes=budget, n_streams=2, keep_outputs=True)
     assert res.max_inflight_bytes <= budget
     for r in trace[:60]:

@@ -1,6 +1,7 @@
 """Host logic of the serving loop (no GPU): the seeded Poisson trace and the memory
 accounting."""
 import numpy as np
+import pytest
 
 from paper_2108_13656_gb300 import serve
 
@@ -33,3 +34,88 @@ def test_request_bytes():
     h = serve.Request(1, 0.0, "local", "f16", (7680, 4320), 0)
     n = serve.request_bytes(h)
     assert n > 7680 * 4320 * 10 and n < 7680 * 4320 * 10 + 16e6
+
+
+class _SimDevice:
+    """A fake device for the scheduling loop: a batch completes a fixed time per
+    pixel after its launch (streams in parallel); the clock is simulated."""
+
+    def __init__(self, ns_per_px=0.05):
+        self.t = 0.0
+        self.ns_per_px = ns_per_px
+        self.busy_until = {}
+        self.launched = []
+
+    def clock(self):
+        return self.t
+
+    def wait_until(self, t_abs):
+        self.t = max(self.t, t_abs)
+
+    def idle(self):
+        self.t += 1e-5
+
+    def launch(self, si, admitted):
+        px = sum(r.size[0] * r.size[1] for r, _ in admitted)
+        start = max(self.t, self.busy_until.get(si, 0.0))
+        self.busy_until[si] = start + px * self.ns_per_px * 1e-9
+        self.launched.append([r.rid for r, _ in admitted])
+        return self.busy_until[si]
+
+    def done(self, h):
+        return self.t >= h
+
+
+def _trace_with_failures():
+    tr = serve.make_trace(60, rate=4000.0, seed=11, sizes=((640, 480), (1280, 720)))
+    big = serve.Request(1000, tr[5].t_arrive + 1e-6, "local", "f16", (7680, 4320), 0)   # larger than the budget
+    tr.append(big)
+    # a request that arrives behind a queue and is withdrawn 0.1 ms later
+    tr[30].t_cancel = tr[30].t_arrive + 1e-4
+    return tr, big
+
+
+def test_oversize_request_is_rejected_and_the_loop_ends():
+    tr, big = _trace_with_failures()
+    budget = 3 * serve.request_bytes(serve.Request(0, 0.0, "local", "f16", (1280, 720), 0))
+    adm = serve.Admission(budget, reserved_bytes=0, max_batch=8)
+    assert serve.request_bytes(big) > adm.capacity
+    dev = _SimDevice(ns_per_px=2.0)  # slow enough that requests queue behind the budget
+    res = serve.schedule(tr, adm, 2, dev.launch, dev.done, lambda h: None, clock=dev.clock,
+                         wait_until=dev.wait_until, idle=dev.idle)
+    assert big.rid in adm.rejected and "budget" in adm.rejected[big.rid]
+    assert adm.cancelled == {tr[30].rid}
+    done = set(res["lat"])
+    assert done == {r.rid for r in tr} - {big.rid, tr[30].rid}
+    assert all(v >= 0 for v in res["lat"].values())
+    assert adm.used == 0 and adm.peak <= adm.capacity
+    # FIFO: launch order follows arrival order
+    order = [rid for b in dev.launched for rid in b]
+    arrivals = [r.rid for r in sorted(tr, key=lambda r: r.t_arrive) if r.rid in done]
+    assert order == arrivals
+    summ = serve._result(tr, res["lat"], res["queued"], res["batches"], adm.peak, None, adm.rejected,
+                         adm.cancelled).summary()
+    assert summ["rejected"] == 1 and summ["cancelled"] == 1 and summ["requests"] == len(tr) - 2
+
+
+def test_cancel_only_while_waiting():
+    adm = serve.Admission(100, max_batch=4)
+    rs = [serve.Request(i, 0.0, "global", "u8", (4, 4), 0) for i in range(3)]
+    assert all(adm.arrive(r, 40) for r in rs)
+    got = adm.admit()
+    assert [r.rid for r, _ in got] == [0, 1]          # the third does not fit yet
+    assert not adm.cancel(0)                            # admitted: runs to completion
+    assert adm.cancel(2) and adm.cancelled == {2}
+    assert not adm.cancel(2)
+    adm.release(80)
+    assert adm.admit() == [] and adm.used == 0
+
+
+def test_admission_counts_reserved_workspaces():
+    with pytest.raises(ValueError):
+        serve.Admission(4 << 30, reserved_bytes=4 << 30)
+    adm = serve.Admission(16 << 30, reserved_bytes=4 * serve.WORKSPACE_BYTES)
+    assert adm.capacity == (16 << 30) - 4 * (128 << 20)
+    r = serve.Request(0, 0.0, "global", "u8", (4, 4), 0)
+    assert not adm.arrive(r, adm.capacity + 1) and 0 in adm.rejected
+    assert adm.arrive(serve.Request(1, 0.0, "global", "u8", (4, 4), 0), adm.capacity)
