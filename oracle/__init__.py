@@ -29,6 +29,7 @@ _lock = threading.Lock()
 _lib = None
 
 DT_U8, DT_F16, DT_F32 = 0, 1, 2
+LUMA_OURS, LUMA_Y, LUMA_V = 0, 1, 2  # Eq. 1-6; rgb2gray Y of Sec. I; V of HSV (Fig. GTMO)
 BETA_R, BETA_K = 0.55, 0.8  # Sec. II-B: "(beta_R = 0.55; beta_k = 0.8)"
 MODE_SIGMOID, MODE_HISTEQ = 0, 1
 
@@ -73,6 +74,16 @@ def _load():
         lib.oracle_tone_histeq_hdr.restype = None
         lib.oracle_tone_histeq_hdr.argtypes = [_dp, ctypes.c_int64, ctypes.c_double,
                                                ctypes.c_double, ctypes.c_double, _up, _dp]
+        lib.oracle_luma.restype = ctypes.c_double
+        lib.oracle_luma.argtypes = [ctypes.c_double] * 3 + [ctypes.c_int32, ctypes.c_double, ctypes.c_double]
+        lib.oracle_decolorize_luma.restype = ctypes.c_int
+        lib.oracle_decolorize_luma.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                               ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _dp]
+        lib.oracle_color_reconstruct.restype = ctypes.c_int
+        lib.oracle_color_reconstruct.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int64,
+                                                 ctypes.c_int32, _dp, _dp, ctypes.c_double, _dp]
+        lib.oracle_video_mu_update.restype = ctypes.c_double
+        lib.oracle_video_mu_update.argtypes = [ctypes.c_double] * 3
         lib.oracle_tone_local.restype = ctypes.c_int
         lib.oracle_tone_local.argtypes = [_dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -106,22 +117,60 @@ def luminance(R: float, G: float, B: float, beta_R: float = BETA_R, beta_k: floa
     return _load().oracle_luminance(float(R), float(G), float(B), float(beta_R), float(beta_k))
 
 
-def decolorize(img: np.ndarray, beta_R: float = BETA_R, beta_k: float = BETA_K) -> np.ndarray:
-    """Eq. 1-6 over an interleaved (H, W, 3) image (any row stride); returns float64 (H, W)."""
+def luma(R: float, G: float, B: float, channel: int, beta_R: float = BETA_R, beta_k: float = BETA_K) -> float:
+    """One pixel's luminance in the chosen channel (LUMA_OURS, LUMA_Y or LUMA_V)."""
+    return _load().oracle_luma(float(R), float(G), float(B), int(channel), float(beta_R), float(beta_k))
+
+
+def _interleaved(img: np.ndarray) -> np.ndarray:
     if img.ndim != 3 or img.shape[2] != 3:
         raise ValueError("expected (H, W, 3)")
-    H, W = img.shape[:2]
     esz = img.dtype.itemsize
-    if H > 0 and W > 0 and (img.strides[2] != esz or img.strides[1] != 3 * esz):
+    if img.shape[0] > 0 and img.shape[1] > 0 and (img.strides[2] != esz or img.strides[1] != 3 * esz):
         img = np.ascontiguousarray(img)
+    return img
+
+
+def decolorize(img: np.ndarray, beta_R: float = BETA_R, beta_k: float = BETA_K, channel: int = LUMA_OURS) -> np.ndarray:
+    """Eq. 1-6 (or the comparison channel `channel`) over an interleaved (H, W, 3) image
+    (any row stride); returns float64 (H, W)."""
+    img = _interleaved(img)
+    H, W = img.shape[:2]
     out = np.empty((H, W), dtype=np.float64)
     if H == 0 or W == 0:
         return out
-    rc = _load().oracle_decolorize(ctypes.c_void_p(img.ctypes.data), W, H, img.strides[0],
-                                   dtype_code(img), beta_R, beta_k, _dptr(out))
+    if channel == LUMA_OURS:
+        rc = _load().oracle_decolorize(ctypes.c_void_p(img.ctypes.data), W, H, img.strides[0],
+                                       dtype_code(img), beta_R, beta_k, _dptr(out))
+    else:
+        rc = _load().oracle_decolorize_luma(ctypes.c_void_p(img.ctypes.data), W, H, img.strides[0],
+                                            dtype_code(img), int(channel), beta_R, beta_k, _dptr(out))
     if rc != 0:
-        raise ValueError("oracle_decolorize failed (%d)" % rc)
+        raise ValueError("oracle decolorize failed (%d)" % rc)
     return out
+
+
+def color_reconstruct(img: np.ndarray, L: np.ndarray, y: np.ndarray, s: float = 1.0) -> np.ndarray:
+    """C_out = min(1, y (C_in / L)^s) per channel (black pixel: y); float64 (H, W, 3)."""
+    img = _interleaved(img)
+    H, W = img.shape[:2]
+    L = np.ascontiguousarray(L, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    if L.shape != (H, W) or y.shape != (H, W):
+        raise ValueError("L and y must be (H, W)")
+    out = np.empty((H, W, 3), dtype=np.float64)
+    if H == 0 or W == 0:
+        return out
+    rc = _load().oracle_color_reconstruct(ctypes.c_void_p(img.ctypes.data), W, H, img.strides[0], dtype_code(img),
+                                          _dptr(L), _dptr(y), float(s), _dptr(out))
+    if rc != 0:
+        raise ValueError("oracle_color_reconstruct failed (%d)" % rc)
+    return out
+
+
+def video_mu_update(m_prev: float, mu_frame: float, lam: float) -> float:
+    """m_t = (1 - lambda) m_{t-1} + lambda mu_t (the frame-sequence estimate)."""
+    return _load().oracle_video_mu_update(float(m_prev), float(mu_frame), float(lam))
 
 
 # ------------------------------------------------------- global statistics ----
@@ -196,18 +245,54 @@ def tonemap_local_plane(L: np.ndarray, ldr: bool, block_s: int = 32, radius_bloc
 
 
 def tonemap_global(img: np.ndarray, mode: int = MODE_SIGMOID, k: float = 1.0, delta: float = 1e-4,
-                   beta_R: float = BETA_R, beta_k: float = BETA_K):
+                   beta_R: float = BETA_R, beta_k: float = BETA_K, channel: int = LUMA_OURS):
     """Decolorize then apply the global curve; LDR iff 8-bit input. Returns (y, stats)."""
-    L = decolorize(img, beta_R, beta_k)
+    L = decolorize(img, beta_R, beta_k, channel)
     return tonemap_global_plane(L, img.dtype == np.uint8, mode, k, delta)
 
 
 def tonemap_local(img: np.ndarray, block_s: int = 32, radius_blocks: int = 2, bins: int = 32,
                   alpha: float = 1.0, delta: float = 1e-4, beta_R: float = BETA_R,
-                  beta_k: float = BETA_K) -> np.ndarray:
+                  beta_k: float = BETA_K, channel: int = LUMA_OURS) -> np.ndarray:
     """Decolorize then apply the local operator; LDR iff 8-bit input."""
-    L = decolorize(img, beta_R, beta_k)
+    L = decolorize(img, beta_R, beta_k, channel)
     return tonemap_local_plane(L, img.dtype == np.uint8, block_s, radius_blocks, bins, alpha, delta)
+
+
+def tonemap_global_color(img: np.ndarray, s: float = 1.0, channel: int = LUMA_OURS, **kw) -> np.ndarray:
+    """Global tone mapping of the chosen luminance, then colour reconstruction: (H, W, 3)."""
+    beta_R, beta_k = kw.pop("beta_R", BETA_R), kw.pop("beta_k", BETA_K)
+    L = decolorize(img, beta_R, beta_k, channel)
+    y, _ = tonemap_global_plane(L, img.dtype == np.uint8, **kw)
+    return color_reconstruct(img, L, y, s)
+
+
+def tonemap_local_color(img: np.ndarray, s: float = 1.0, channel: int = LUMA_OURS, **kw) -> np.ndarray:
+    """Local tone mapping of the chosen luminance, then colour reconstruction: (H, W, 3)."""
+    beta_R, beta_k = kw.pop("beta_R", BETA_R), kw.pop("beta_k", BETA_K)
+    L = decolorize(img, beta_R, beta_k, channel)
+    y = tonemap_local_plane(L, img.dtype == np.uint8, **kw)
+    return color_reconstruct(img, L, y, s)
+
+
+def tonemap_video_global(frames, lam: float = 1.0, k: float = 1.0, delta: float = 1e-4, beta_R: float = BETA_R,
+                         beta_k: float = BETA_K, channel: int = LUMA_OURS):
+    """A frame sequence through the centred sigmoid with the carried log-mean estimate:
+    frame 0 around its own log-mean mu_0 (m_0 = mu_0); frame t >= 1 around m_{t-1},
+    then m_t = (1 - lambda) m_{t-1} + lambda mu_t.  Returns ([y_t], [m_t])."""
+    ys, ms = [], []
+    m = None
+    lib = _load()
+    for img in frames:
+        L = np.ascontiguousarray(decolorize(img, beta_R, beta_k, channel))
+        mu, _, _ = log_stats(L, delta)
+        centre = mu if m is None else m
+        y = np.empty_like(L)
+        lib.oracle_tone_sigmoid(_dptr(L), L.size, k, delta, centre, _dptr(y))
+        m = mu if m is None else video_mu_update(m, mu, lam)
+        ys.append(y)
+        ms.append(m)
+    return ys, ms
 
 
 def u8_boundary_mask(y: np.ndarray, eps: float = 1e-5) -> np.ndarray:

@@ -31,6 +31,13 @@
  *    spread uniformly over its bin, and bilinear interpolation between the
  *    four nearest nominal block centres ((I+1/2)s, (J+1/2)s), clamped at the
  *    border.  Output alpha*F + (1-alpha)*u.
+ *  - comparison channels (Sec. I, Fig. GTMO): MATLAB's rgb2gray weights as the
+ *    paper quotes them, and V of HSV = max(R, G, B), on the same decoded samples.
+ *  - colour reconstruction (colour outputs of Fig. tmo_1 and Fig. GTMO, no formula):
+ *    C_out = min(1, y (C_in / L)^s), a black pixel taken as achromatic.
+ *  - frame sequences (real-time use, Sec. I; no scheme given): frame t is centred
+ *    on the log-mean estimate carried from the frames before it,
+ *    m_t = (1 - lambda) m_{t-1} + lambda mu_t, the first frame on its own mu_0.
  * Parity of the tone-mapping parameters (k, delta, s, R, bins, alpha) is
  * unpinned by the paper, which prints none of them; the operators are pinned
  * by closed forms and invariants in the tests instead.
@@ -324,4 +331,101 @@ int oracle_tone_local(const double* L, int32_t W, int32_t H, int32_t ldr, int32_
     free(edge);
     free(u);
     return 0;
+}
+
+/*
+ * Comparison luminance channels of Sec. I and Fig. GTMO / Sec. III-B-1, which the
+ * paper tone-maps beside its own:
+ *   luma 0: the colour-temperature luminance of Eq. 1-6;
+ *   luma 1: MATLAB's rgb2gray weighted sum quoted in Sec. I,
+ *           Gray = 0.2989 R + 0.5870 G + 0.1140 B;
+ *   luma 2: V of HSV, the largest channel.
+ * Returns NAN for an unknown luma code.
+ */
+double oracle_luma(double R, double G, double B, int32_t luma, double beta_R, double beta_k)
+{
+    if (luma == 0)
+        return oracle_luminance(R, G, B, beta_R, beta_k);
+    if (luma == 1)
+        return 0.2989 * R + 0.5870 * G + 0.1140 * B;
+    if (luma == 2) {
+        double m = R;
+        if (G > m) m = G;
+        if (B > m) m = B;
+        return m;
+    }
+    return NAN;
+}
+
+/* oracle_decolorize with a choice of luminance channel. */
+int oracle_decolorize_luma(const void* data, int32_t W, int32_t H, int64_t stride_bytes, int32_t dtype,
+                           int32_t luma, double beta_R, double beta_k, double* L)
+{
+    if (W < 0 || H < 0 || dtype < OR_U8 || dtype > OR_F32 || luma < 0 || luma > 2)
+        return 1;
+    int esz = dtype == OR_U8 ? 1 : (dtype == OR_F16 ? 2 : 4);
+    const unsigned char* base = (const unsigned char*)data;
+    for (int32_t y = 0; y < H; ++y) {
+        const unsigned char* row = base + (int64_t)y * stride_bytes;
+        for (int32_t x = 0; x < W; ++x) {
+            const unsigned char* px = row + (int64_t)x * 3 * esz;
+            double R = or_sample(px, dtype, 0);
+            double G = or_sample(px, dtype, 1);
+            double B = or_sample(px, dtype, 2);
+            L[(int64_t)y * W + x] = oracle_luma(R, G, B, luma, beta_R, beta_k);
+        }
+    }
+    return 0;
+}
+
+/*
+ * Colour reconstruction of a tone-mapped luminance (the colour outputs of
+ * Fig. tmo_1, Fig. GTMO and Sec. II-D; the paper does not state the method).
+ * Reading: every channel keeps its ratio to the luminance it was decolorized to,
+ * raised to a saturation exponent s, and is scaled to the tone-mapped value:
+ *   C_out = min(1, y (C_in / L)^s),
+ * with 0^0 = 1 (a black channel is y when s = 0, 0 when s > 0) and a black pixel
+ * (L = 0) taken as achromatic: every channel is y.  `L` and `y` are W x H planes;
+ * `out` is W x H x 3, interleaved.
+ */
+int oracle_color_reconstruct(const void* data, int32_t W, int32_t H, int64_t stride_bytes, int32_t dtype,
+                             const double* L, const double* y, double s, double* out)
+{
+    if (W < 0 || H < 0 || dtype < OR_U8 || dtype > OR_F32 || !(s >= 0.0))
+        return 1;
+    int esz = dtype == OR_U8 ? 1 : (dtype == OR_F16 ? 2 : 4);
+    const unsigned char* base = (const unsigned char*)data;
+    for (int32_t py = 0; py < H; ++py) {
+        const unsigned char* row = base + (int64_t)py * stride_bytes;
+        for (int32_t px = 0; px < W; ++px) {
+            int64_t i = (int64_t)py * W + px;
+            for (int c = 0; c < 3; ++c) {
+                double C = or_sample(row + (int64_t)px * 3 * esz, dtype, c);
+                double v;
+                if (L[i] == 0.0)
+                    v = y[i];
+                else if (C == 0.0)
+                    v = s == 0.0 ? y[i] : 0.0;
+                else
+                    v = y[i] * pow(C / L[i], s);
+                out[3 * i + c] = v < 1.0 ? v : 1.0;
+            }
+        }
+    }
+    return 0;
+}
+
+/*
+ * Frame sequences (the real-time use of Sec. I and Sec. III-B; the paper names no
+ * temporal scheme).  Reading: frame t is tone-mapped with the centred sigmoid
+ * around the log-mean estimate m_{t-1} carried from the frames before it, so one
+ * pass over the frame suffices, and the estimate then follows the frame's own
+ * log-mean mu_t by exponential smoothing:
+ *   m_t = (1 - lambda) m_{t-1} + lambda mu_t,   0 < lambda <= 1.
+ * The first frame has no estimate: it is centred on its own mu_0, and m_0 = mu_0.
+ * This function is that update (one step), written out for the test of the state.
+ */
+double oracle_video_mu_update(double m_prev, double mu_frame, double lambda)
+{
+    return (1.0 - lambda) * m_prev + lambda * mu_frame;
 }
