@@ -93,17 +93,33 @@ typedef struct {
 } dc_image_in;
 
 typedef struct {
-    void* data;           /* device pointer, width x height samples of `dtype` */
-    int64_t stride_bytes; /* bytes between rows, >= width * sample size */
+    void* data;           /* device pointer, width x height x channels samples of `dtype` */
+    int64_t stride_bytes; /* bytes between rows, >= width * channels * sample size */
     int32_t dtype;        /* DC_U8, DC_F16 or DC_F32 */
-    int32_t reserved;     /* must be 0 */
+    int32_t channels;     /* 0 or 1: the gray (tone-mapped) plane; 3: interleaved RGB colour
+                             reconstruction of the tone-mapped image (tone-mapping calls only),
+                             C_out = min(1, y (C_in / L)^color_s) per channel, a black pixel
+                             (L = 0) giving y in every channel.  The paper shows colour
+                             tone-mapped images (Fig. tmo_1, Fig. GTMO, Sec. II-D) without
+                             stating how they are formed; this is the library's reading. */
 } dc_image_out;
 
+/* Luminance channel the tone mapping works on (Sec. III-B-1, Fig. GTMO, compares the
+ * paper's channel with Y of YCbCr and V of HSV). */
+#define DC_LUMA_OURS 0 /* Eq. 1-6 (Sec. II-B) */
+#define DC_LUMA_Y 1    /* Gray = 0.2989 R + 0.5870 G + 0.1140 B (MATLAB rgb2gray, quoted in Sec. I) */
+#define DC_LUMA_V 2    /* V of HSV = max(R, G, B) */
+
 /* Eq. 3 and Eq. 6 weights; the paper uses beta_r = 0.55 and beta_k = 0.8
- * (Sec. II-B).  The paper states 0.5 < beta < 1; the library accepts [0, 1]. */
+ * (Sec. II-B).  The paper states 0.5 < beta < 1; the library accepts [0, 1].
+ * luma selects the channel (DC_LUMA_*; the betas are used by DC_LUMA_OURS only);
+ * color_s in [0, 8] is the saturation exponent of colour outputs (1 keeps every
+ * channel's ratio to the luminance, 0 gives gray; unused for gray outputs). */
 typedef struct {
     float beta_r;
     float beta_k;
+    int32_t luma;
+    float color_s;
 } dc_decolor_params;
 
 /* Global curve (Sec. III-B-1 names it a centred sigmoid and prints no formula):
@@ -192,6 +208,44 @@ DC_API int dc_decolorize_tonemap_local(const dc_image_in* in, const dc_image_out
                                        const dc_decolor_params* params,
                                        const dc_local_params* lparams, void* ws, size_t ws_bytes,
                                        void* stream);
+
+/* Frame sequences (the real-time use the paper motivates in Sec. I and
+ * Sec. III-B-2; it names no temporal scheme).  Per video stream a device record
+ * carries m, an estimate of the log-mean of ln(L + delta); a frame is tone-mapped
+ * with the centred sigmoid of Sec. III-B-1 around the carried m instead of its own
+ * log-mean, so one pass over the frame suffices, and the pass also sums the
+ * frame's own log-mean mu_t, after which m <- (1 - lambda) m + lambda mu_t.
+ * `state` is a device array of n records (one per image of the batch, each image
+ * the next frame of its own stream), caller-owned and written by the call.
+ * restart = 1 starts the streams afresh: each frame is centred on its own log-mean
+ * (two passes, the global call's result) and m = mu.  Records must be restarted
+ * before their first use.  lambda in (0, 1]; gparams->mode must be DC_SIGMOID.
+ * The outputs of a restarted frame equal dc_decolorize_tonemap_global's. */
+typedef struct {
+    float m;           /* carried log-mean estimate */
+    float mu_last;     /* log-mean of the last frame */
+    int64_t frames;    /* frames seen since the restart */
+} dc_video_state;
+
+DC_API int dc_decolorize_tonemap_video(const dc_image_in* in, const dc_image_out* out, int32_t n,
+                                       const dc_decolor_params* params, const dc_global_params* gparams,
+                                       float lambda, int32_t restart, dc_video_state* state, void* ws,
+                                       size_t ws_bytes, void* stream);
+
+/* Parameter presets (host only).  DC_PRESET_PAPER: beta_r = 0.55, beta_k = 0.8
+ * (Sec. II-B).  Fig. SLHE_TMO(c) shows the paper's luminance controlling the
+ * background and the foreground separately through local tone mapping: TM1,
+ * "background boost", and TM2, "background suppression", without their values.
+ * Reading: beta_k trades the warm blend L_WARM against the cool blend L_COOL in
+ * Eq. 6, so a lower beta_k lifts the cool (typically background) colours and a higher
+ * one suppresses them: TM1 = (0.55, 0.55), TM2 = (0.55, 0.95), both within the
+ * paper's 0.5 < beta < 1.  Every preset uses DC_LUMA_OURS, color_s = 1 and the
+ * default local operator (block_s 32, radius 2, 32 bins, alpha 1, delta 1e-4).
+ * `p` or `l` may be NULL.  Returns DC_ERR_INVALID_ARG for an unknown preset. */
+#define DC_PRESET_PAPER 0
+#define DC_PRESET_TM1 1
+#define DC_PRESET_TM2 2
+DC_API int dc_preset(int32_t preset, dc_decolor_params* p, dc_local_params* l);
 
 /* Global tone mapping for callers that cannot allocate device memory (no
  * counterpart in the paper; it is a deployment convenience).  Same arguments and
@@ -291,7 +345,8 @@ DC_API int dc_debug_fail_launch(int32_t k);
  * memory).  The paper has no counterpart. */
 DC_API int dc_debug_bounds(uint32_t* flags, int32_t* checked);
 
-/* ABI version (major * 100 + minor). */
+/* ABI version (major * 100 + minor): 200 since the channel choice, colour outputs,
+ * frame sequences and presets. */
 DC_API int dc_version(void);
 
 #ifdef __cplusplus

@@ -13,6 +13,9 @@ from ._abi import (  # noqa: F401
     DC_F16,
     DC_F32,
     DC_HISTEQ,
+    DC_LUMA_OURS,
+    DC_LUMA_V,
+    DC_LUMA_Y,
     DC_OP_DECOLORIZE,
     DC_OP_GLOBAL,
     DC_OP_LOCAL,
@@ -21,6 +24,7 @@ from ._abi import (  # noqa: F401
     STATS_BYTES,
     DcError,
     PreparedCall,
+    VideoStreams,
     Workspace,
     debug_bounds,
     debug_fail_launch,
@@ -35,6 +39,7 @@ from ._abi import (  # noqa: F401
     local_params,
     local_tile_cols,
     parse_stats,
+    preset,
     query_status,
     read_profile,
     set_tuning,

@@ -20,7 +20,11 @@ DC_ERR_CUDA, DC_ERR_TIMEOUT, DC_ERR_TOO_MANY = 4, 5, 6
 DC_U8, DC_F16, DC_F32 = 0, 1, 2
 DC_OP_DECOLORIZE, DC_OP_GLOBAL, DC_OP_LOCAL = 0, 1, 2
 DC_SIGMOID, DC_HISTEQ = 0, 1
+DC_LUMA_OURS, DC_LUMA_Y, DC_LUMA_V = 0, 1, 2
+DC_PRESET_PAPER, DC_PRESET_TM1, DC_PRESET_TM2 = 0, 1, 2
 BETA_R, BETA_K = 0.55, 0.8
+LUMA = {"ours": DC_LUMA_OURS, "y": DC_LUMA_Y, "v": DC_LUMA_V}
+VIDEO_STATE_BYTES = 16  # sizeof(dc_video_state)
 
 
 class DcError(RuntimeError):
@@ -36,11 +40,19 @@ class dc_image_in(ctypes.Structure):
 
 class dc_image_out(ctypes.Structure):
     _fields_ = [("data", ctypes.c_void_p), ("stride_bytes", ctypes.c_int64), ("dtype", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("channels", ctypes.c_int32)]
 
 
 class dc_decolor_params(ctypes.Structure):
-    _fields_ = [("beta_r", ctypes.c_float), ("beta_k", ctypes.c_float)]
+    _fields_ = [("beta_r", ctypes.c_float), ("beta_k", ctypes.c_float), ("luma", ctypes.c_int32),
+                ("color_s", ctypes.c_float)]
+
+    def __init__(self, beta_r=0.55, beta_k=0.8, luma=0, color_s=1.0):
+        super().__init__(beta_r, beta_k, luma, color_s)
+
+
+class dc_video_state(ctypes.Structure):
+    _fields_ = [("m", ctypes.c_float), ("mu_last", ctypes.c_float), ("frames", ctypes.c_int64)]
 
 
 class dc_global_params(ctypes.Structure):
@@ -73,6 +85,11 @@ _SIGS = {
     "dc_decolorize_tonemap_global_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
                                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                                                             ctypes.c_void_p]),
+    "dc_decolorize_tonemap_video": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float, ctypes.c_int32,
+                                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
+                                                   ctypes.c_void_p]),
+    "dc_preset": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
     "dc_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "dc_workspace_min_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "dc_workspace_prepare": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
@@ -159,13 +176,19 @@ def _in_desc(t) -> dc_image_in:
 
 
 def _out_desc(t) -> dc_image_out:
-    if t.dim() != 2 or t.stride(1) != 1:
-        raise ValueError("output must be a (H, W) plane with unit column stride")
+    """A (H, W) gray plane, or a (H, W, 3) interleaved colour output."""
     d = dc_image_out()
+    if t.dim() == 3 and t.shape[2] == 3:
+        if t.stride(2) != 1 or t.stride(1) != 3:
+            raise ValueError("colour output pixels must be interleaved (channel stride 1, pixel stride 3)")
+        d.channels = 3
+    elif t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("output must be a (H, W) plane with unit column stride or (H, W, 3) interleaved")
+    else:
+        d.channels = 0
     d.data = t.data_ptr()
     d.stride_bytes = int(t.stride(0)) * t.element_size()
     d.dtype = dtype_code(t)
-    d.reserved = 0
     return d
 
 
@@ -178,7 +201,7 @@ def _arrays(inputs, outputs):
         if len(outputs) != len(inputs):
             raise ValueError("inputs and outputs differ in length")
         for a, b in zip(inputs, outputs):
-            if tuple(b.shape) != (a.shape[0], a.shape[1]):
+            if tuple(b.shape[:2]) != (a.shape[0], a.shape[1]):
                 raise ValueError("output shape %s does not match input %s" % (tuple(b.shape), tuple(a.shape)))
         outs = (dc_image_out * len(outputs))(*[_out_desc(t) for t in outputs])
     return ins, outs
@@ -268,12 +291,13 @@ class PreparedCall:
 
     def __init__(self, op: str, inputs, outputs, beta_r: float = BETA_R, beta_k: float = BETA_K,
                  mode="sigmoid", gain_k: float = 1.0, delta: float = 1e-4, stats=None, block_s: int = 32,
-                 radius_blocks: int = 2, bins: int = 32, alpha: float = 1.0, workspace=None):
+                 radius_blocks: int = 2, bins: int = 32, alpha: float = 1.0, workspace=None, luma="ours",
+                 color_s: float = 1.0):
         self.lib = load()
         self.inputs, self.outputs = _as_list(inputs), _as_list(outputs)
         self.n = len(self.inputs)
         self.ins, self.outs = _arrays(self.inputs, self.outputs)
-        self.p = dc_decolor_params(beta_r, beta_k)
+        self.p = dc_decolor_params(beta_r, beta_k, LUMA.get(luma, luma), color_s)
         self.op = op
         self.stats = stats
         self.lp = None
@@ -317,27 +341,87 @@ class PreparedCall:
 
 
 def decolorize(inputs, outputs, beta_r: float = BETA_R, beta_k: float = BETA_K, workspace=None,
-               stream=None):
-    """Eq. 1-6 over a (ragged) batch: outputs[i] = L(inputs[i])."""
+               stream=None, luma="ours"):
+    """Eq. 1-6 (or the comparison channel `luma`: "ours", "y", "v") over a (ragged)
+    batch: outputs[i] = L(inputs[i])."""
     return PreparedCall("decolorize", inputs, outputs, beta_r=beta_r, beta_k=beta_k,
-                        workspace=workspace)(stream)
+                        workspace=workspace, luma=luma)(stream)
 
 
 def decolorize_tonemap_global(inputs, outputs, mode: str | int = "sigmoid", gain_k: float = 1.0,
                               delta: float = 1e-4, stats=None, beta_r: float = BETA_R,
-                              beta_k: float = BETA_K, workspace=None, stream=None):
-    """Eq. 1-6 then the global curve; `stats` is None or a uint8 CUDA tensor of n*STATS_BYTES."""
+                              beta_k: float = BETA_K, workspace=None, stream=None, luma="ours",
+                              color_s: float = 1.0):
+    """Eq. 1-6 then the global curve; `stats` is None or a uint8 CUDA tensor of n*STATS_BYTES.
+    An (H, W, 3) output receives the colour reconstruction (saturation exponent color_s)."""
     return PreparedCall("global", inputs, outputs, beta_r=beta_r, beta_k=beta_k, mode=mode, gain_k=gain_k,
-                        delta=delta, stats=stats, workspace=workspace)(stream)
+                        delta=delta, stats=stats, workspace=workspace, luma=luma, color_s=color_s)(stream)
 
 
 def decolorize_tonemap_local(inputs, outputs, block_s: int = 32, radius_blocks: int = 2, bins: int = 32,
                              alpha: float = 1.0, delta: float = 1e-4, beta_r: float = BETA_R,
-                             beta_k: float = BETA_K, workspace=None, stream=None):
-    """Eq. 1-6 then smoothed local-histogram equalisation."""
+                             beta_k: float = BETA_K, workspace=None, stream=None, luma="ours",
+                             color_s: float = 1.0):
+    """Eq. 1-6 then smoothed local-histogram equalisation (colour output as for the global call)."""
     return PreparedCall("local", inputs, outputs, beta_r=beta_r, beta_k=beta_k, block_s=block_s,
                         radius_blocks=radius_blocks, bins=bins, alpha=alpha, delta=delta,
-                        workspace=workspace)(stream)
+                        workspace=workspace, luma=luma, color_s=color_s)(stream)
+
+
+def preset(name) -> tuple[dc_decolor_params, dc_local_params]:
+    """Parameter preset ("paper", "tm1" background boost, "tm2" background suppression)."""
+    code = {"paper": DC_PRESET_PAPER, "tm1": DC_PRESET_TM1, "tm2": DC_PRESET_TM2}.get(name, name)
+    p, lp = dc_decolor_params(), dc_local_params()
+    rc = load().dc_preset(int(code), ctypes.byref(p), ctypes.byref(lp))
+    if rc != DC_OK:
+        raise DcError(rc, "dc_preset")
+    return p, lp
+
+
+class VideoStreams:
+    """n video streams tone-mapped frame by frame with the carried log-mean estimate
+    (dc_decolorize_tonemap_video): the first call (or one after restart()) centres each
+    frame on its own log-mean, later calls take one pass per frame.  The per-stream
+    state lives in a device tensor owned here."""
+
+    def __init__(self, n: int, lam: float = 1.0, gain_k: float = 1.0, delta: float = 1e-4,
+                 beta_r: float = BETA_R, beta_k: float = BETA_K, luma="ours", device=None, workspace=None):
+        torch = _torch()
+        self.lib = load()
+        self.n = int(n)
+        self.lam = float(lam)
+        self.state = torch.zeros(self.n * VIDEO_STATE_BYTES, dtype=torch.uint8, device=device or "cuda")
+        self.p = dc_decolor_params(beta_r, beta_k, LUMA.get(luma, luma), 1.0)
+        self.g = dc_global_params(DC_SIGMOID, gain_k, delta, 0)
+        self.ws = workspace
+        self._restart = True
+
+    def restart(self):
+        self._restart = True
+
+    def __call__(self, frames, outputs, stream=None):
+        frames, outputs = _as_list(frames), _as_list(outputs)
+        if len(frames) != self.n:
+            raise ValueError("expected %d frames (one per stream)" % self.n)
+        ins, outs = _arrays(frames, outputs)
+        ptr, size, _ = _workspace(DC_OP_GLOBAL, ins, self.n, None, self.ws)
+        rc = self.lib.dc_decolorize_tonemap_video(ins, outs, self.n, ctypes.byref(self.p), ctypes.byref(self.g),
+                                                  self.lam, 1 if self._restart else 0,
+                                                  ctypes.c_void_p(self.state.data_ptr()), ctypes.c_void_p(ptr), size,
+                                                  _stream_handle(stream))
+        if rc != DC_OK:
+            raise DcError(rc, "dc_decolorize_tonemap_video")
+        self._restart = False
+        return outputs
+
+    def states(self) -> list[dict]:
+        raw = self.state.cpu().numpy().tobytes()
+        out = []
+        for i in range(self.n):
+            f = np.frombuffer(raw[i * 16:i * 16 + 8], dtype=np.float32)
+            q = np.frombuffer(raw[i * 16 + 8:i * 16 + 16], dtype=np.int64)
+            out.append({"m": float(f[0]), "mu_last": float(f[1]), "frames": int(q[0])})
+        return out
 
 
 def workspace_bytes(op: int, inputs, lparams: dc_local_params | None = None, minimum: bool = False) -> int:

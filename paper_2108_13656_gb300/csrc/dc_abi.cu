@@ -109,9 +109,14 @@ struct OpArgs {
     const dc_global_params* g;
     const dc_local_params* l;
     dc_global_stats* stats;
+    dc_video_state* vstate = nullptr;  // frame sequences (global sigmoid only)
+    bool restart = false;              // frame sequences: centre each frame on its own log-mean
+    float lambda = 1.0f;
 };
 
-int validate_image(const dc_image_in& in, const dc_image_out* out, bool local)
+int out_channels(const dc_image_out& o) { return o.channels == 3 ? 3 : 1; }
+
+int validate_image(const dc_image_in& in, const dc_image_out* out, bool local, bool tonemap)
 {
     if (!dt_ok(in.dtype)) return DC_ERR_UNSUPPORTED_DTYPE;
     if (in.reserved != 0 || in.width < 1 || in.height < 1) return DC_ERR_INVALID_ARG;
@@ -122,10 +127,12 @@ int validate_image(const dc_image_in& in, const dc_image_out* out, bool local)
     if ((reinterpret_cast<uintptr_t>(in.data) % ie) != 0 || (in.stride_bytes % ie) != 0) return DC_ERR_INVALID_ARG;
     if (out) {
         if (!dt_ok(out->dtype)) return DC_ERR_UNSUPPORTED_DTYPE;
-        if (out->reserved != 0 || out->data == nullptr) return DC_ERR_INVALID_ARG;
-        const int oe = esz(out->dtype);
+        if (out->data == nullptr || (out->channels != 0 && out->channels != 1 && out->channels != 3))
+            return DC_ERR_INVALID_ARG;
+        if (out->channels == 3 && !tonemap) return DC_ERR_INVALID_ARG;  // colour needs a tone-mapped y
+        const int oe = esz(out->dtype) * out_channels(*out);
         if (out->stride_bytes < (int64_t)in.width * oe) return DC_ERR_INVALID_ARG;
-        if ((reinterpret_cast<uintptr_t>(out->data) % oe) != 0 || (out->stride_bytes % oe) != 0)
+        if ((reinterpret_cast<uintptr_t>(out->data) % esz(out->dtype)) != 0 || (out->stride_bytes % esz(out->dtype)) != 0)
             return DC_ERR_INVALID_ARG;
     }
     return DC_OK;
@@ -134,6 +141,12 @@ int validate_image(const dc_image_in& in, const dc_image_out* out, bool local)
 int validate_params(const dc_decolor_params* p, const OpArgs& op)
 {
     if (!p || !finite_in(p->beta_r, 0.f, 1.f) || !finite_in(p->beta_k, 0.f, 1.f)) return DC_ERR_INVALID_ARG;
+    if (p->luma < DC_LUMA_OURS || p->luma > DC_LUMA_V || !finite_in(p->color_s, 0.f, 8.f)) return DC_ERR_INVALID_ARG;
+    if (op.vstate || op.restart) {
+        if (op.opk != kOpkGlobal || !op.vstate || !finite_in(op.lambda, 0.f, 1.f) || !(op.lambda > 0.f))
+            return DC_ERR_INVALID_ARG;
+        if (op.g && op.g->mode != DC_SIGMOID) return DC_ERR_INVALID_ARG;
+    }
     if (op.opk == kOpkGlobal) {
         const dc_global_params* g = op.g;
         if (!g || (g->mode != DC_SIGMOID && g->mode != DC_HISTEQ) || g->reserved != 0) return DC_ERR_INVALID_ARG;
@@ -239,14 +252,23 @@ struct Geometry {
 struct LaunchPlan {
     int in_dt;
     bool plane;            // every image keeps an f32 plane between passes
+    bool color;            // every image has a colour (3-channel) output
     std::vector<int> idx;  // positions in the caller's arrays
 };
 
 // An image keeps its luminance (or its fixed-point log) in its f32 output between
-// passes: HDR input, a tone-mapping operation, f32 output.
-bool keeps_plane(const OpArgs& op, int in_dt, int out_dt)
+// passes: HDR input, a tone-mapping operation, a gray f32 output.
+bool keeps_plane(const OpArgs& op, int in_dt, const dc_image_out& o)
 {
-    return op.opk != kOpkDecolor && in_dt != DC_U8 && out_dt == DC_F32;
+    return op.opk != kOpkDecolor && in_dt != DC_U8 && o.dtype == DC_F32 && out_channels(o) == 1;
+}
+
+// 8-bit input through the local operator with an f32 output (gray or colour): the bin
+// coordinate comes from the float-float luminance (binary32 L is too coarse for the
+// curve's slope at f32 precision).
+bool precise_coord(const OpArgs& op, int in_dt, const dc_image_out& o)
+{
+    return op.opk == kOpkLocal && in_dt == DC_U8 && o.dtype == DC_F32;
 }
 
 // Passes that read the plane instead of recomputing L from RGB (an 8-bit local
@@ -264,6 +286,10 @@ int phase_list(const OpArgs& op, bool ldr, int32_t* kinds)
         return 1;
     }
     if (op.opk == kOpkGlobal) {
+        if (op.vstate && !op.restart) {  // a frame of a running sequence: one pass
+            kinds[0] = PK_VIDEO;
+            return 1;
+        }
         kinds[0] = PK_STATS;
         if (op.g->mode == DC_HISTEQ && !ldr) {
             kinds[0] = PK_STATS_LOG;  // the histogram of u needs the exact log coordinate
@@ -295,12 +321,13 @@ void make_geometry(const dc_image_in& in, const dc_image_out& out, const OpArgs&
     im.out_dt = out.dtype;
     im.prow = H;
     im.pcol = W;
-    const bool dense = in.stride_bytes == (int64_t)3 * W * ie && out.stride_bytes == (int64_t)W * oe;
+    const int och = out_channels(out);
+    const bool dense = in.stride_bytes == (int64_t)3 * W * ie && out.stride_bytes == (int64_t)W * oe * och;
     if (op.opk != kOpkLocal && dense) {
         im.rows = 1;
         im.cols = W * H;
         im.in_stride = (int64_t)3 * W * H * ie;
-        im.out_stride = (int64_t)W * H * oe;
+        im.out_stride = (int64_t)W * H * oe * och;
     } else {
         im.rows = H;
         im.cols = W;
@@ -310,8 +337,10 @@ void make_geometry(const dc_image_in& in, const dc_image_out& out, const OpArgs&
     bool vec = al16(in.data) && al16(out.data);
     if (im.rows > 1) vec = vec && (in.stride_bytes % 16 == 0) && (out.stride_bytes % 16 == 0);
     im.flags = vec ? IF_VEC : 0u;
+    if (och == 3) im.flags |= IF_COLOR;
+    if (precise_coord(op, in.dtype, out)) im.flags |= IF_UPRECISE;
     g.plane_bytes = 0;
-    if (keeps_plane(op, in.dtype, out.dtype)) {
+    if (keeps_plane(op, in.dtype, out)) {
         im.flags |= IF_LPLANE;
         im.plane = im.out;
         im.plane_stride = im.out_stride;
@@ -345,14 +374,16 @@ void make_geometry(const dc_image_in& in, const dc_image_out& out, const OpArgs&
 
 template <int CAP>
 int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::vector<int>& idx, bool plane,
-                     bool allow_u8_plane, const dc_decolor_params* p, const OpArgs& op, uint8_t* ws,
+                     bool color, bool allow_u8_plane, const dc_decolor_params* p, const OpArgs& op, uint8_t* ws,
                      int64_t ws_bytes_total, bool first, int64_t* need, void* stream, bool launch)
 {
     const int n = (int)idx.size();
     const int in_dt = in[idx[0]].dtype;
     const bool ldr = in_dt == DC_U8;
     bool u8_plane = false;
-    if (allow_u8_plane && ldr && op.opk != kOpkDecolor) {
+    // (not for colour outputs, whose apply pass re-reads RGB anyway, nor for a frame of
+    // a running sequence, which is a single pass)
+    if (allow_u8_plane && ldr && op.opk != kOpkDecolor && !color && !(op.vstate && !op.restart)) {
         int64_t px = 0;
         for (int k = 0; k < n; ++k) px += (int64_t)in[idx[k]].width * in[idx[k]].height;
         u8_plane = px <= kU8PlaneMaxPixels;
@@ -395,6 +426,11 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
     }
     b->beta_r = p->beta_r;
     b->beta_k = p->beta_k;
+    b->luma = p->luma;
+    b->color_s = p->color_s;
+    b->color_s_one = p->color_s == 1.0f;
+    b->lambda = op.lambda;
+    b->vstate = op.vstate;
     b->ldr = ldr ? 1 : 0;
     {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -498,9 +534,10 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
         const int kind = b->phase_kind[ph];
         // the flag: reads the plane (histogram and apply passes), or keeps only the
         // reduction the call uses (statistics passes)
-        const bool pl = kind == PK_STATS       ? b->need_minmax == 0
-                        : kind == PK_STATS_LOG ? b->need_logsum == 0
-                                               : plane && reads_plane(kind, in_dt);
+        const int pl = kind == PK_STATS       ? (b->need_minmax == 0 ? 1 : 0)
+                       : kind == PK_STATS_LOG ? (b->need_logsum == 0 ? 1 : 0)
+                       : (color && (kind == PK_APPLY_G || kind == PK_APPLY_L)) ? 2
+                                              : ((plane && reads_plane(kind, in_dt)) ? 1 : 0);
         int occ = in_dt == DC_U8 ? occupancy_u8(CAP, op.opk, kind, pl)
                                  : (in_dt == DC_F16 ? occupancy_f16(CAP, op.opk, kind, pl) : occupancy_f32(CAP, op.opk, kind, pl));
         if (occ <= 0) occ = 1;
@@ -532,7 +569,7 @@ int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_deco
     int rc = validate_params(p, op);
     if (rc != DC_OK) return rc;
     for (int k = 0; k < n; ++k) {
-        rc = validate_image(in[k], query ? nullptr : &out[k], op.opk == kOpkLocal);
+        rc = validate_image(in[k], query ? nullptr : &out[k], op.opk == kOpkLocal, op.opk != kOpkDecolor);
         if (rc != DC_OK) return rc;
     }
     if (!query) {
@@ -541,7 +578,8 @@ int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_deco
             const uint8_t* a0 = static_cast<const uint8_t*>(in[k].data);
             const uint8_t* a1 = a0 + (in[k].height - 1) * in[k].stride_bytes + (int64_t)3 * in[k].width * esz(in[k].dtype);
             const uint8_t* b0 = static_cast<const uint8_t*>(out[k].data);
-            const uint8_t* b1 = b0 + (in[k].height - 1) * out[k].stride_bytes + (int64_t)in[k].width * esz(out[k].dtype);
+            const uint8_t* b1 = b0 + (in[k].height - 1) * out[k].stride_bytes +
+                                (int64_t)in[k].width * esz(out[k].dtype) * out_channels(out[k]);
             if (a0 < b1 && b0 < a1) return DC_ERR_INVALID_ARG;
         }
     }
@@ -554,7 +592,7 @@ int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_deco
             fake[k].data = reinterpret_cast<void*>(uintptr_t(256));
             fake[k].stride_bytes = (int64_t)in[k].width * 4;
             fake[k].dtype = DC_F32;
-            fake[k].reserved = 0;
+            fake[k].channels = 0;
         }
         outs = fake.data();
     }
@@ -563,12 +601,14 @@ int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_deco
     // never smaller than the call's)
     std::vector<LaunchPlan> plans;
     for (int dt = DC_U8; dt <= DC_F32; ++dt) {
-        for (int pl = 0; pl < 2; ++pl) {
+        for (int pl = 0; pl < 3; ++pl) {  // no plane, plane, colour output (never a plane)
             LaunchPlan cur;
             cur.in_dt = dt;
-            cur.plane = pl != 0;
+            cur.plane = pl == 1;
+            cur.color = pl == 2;
             for (int k = 0; k < n; ++k) {
-                if (in[k].dtype != dt || keeps_plane(op, dt, outs[k].dtype) != cur.plane) continue;
+                if (in[k].dtype != dt || keeps_plane(op, dt, outs[k]) != cur.plane || (out_channels(outs[k]) == 3) != cur.color)
+                    continue;
                 cur.idx.push_back(k);
                 if ((int)cur.idx.size() == kCapLarge) {
                     plans.push_back(cur);
@@ -589,11 +629,11 @@ int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_deco
             int64_t* nd = &need[with_plane];
             int r2;
             if (cnt <= kCapSmall)
-                r2 = build_and_launch<kCapSmall>(in, outs, pl.idx, pl.plane, a, p, op, nullptr, 0, false, nd, nullptr, false);
+                r2 = build_and_launch<kCapSmall>(in, outs, pl.idx, pl.plane, pl.color, a, p, op, nullptr, 0, false, nd, nullptr, false);
             else if (cnt <= kCapMid)
-                r2 = build_and_launch<kCapMid>(in, outs, pl.idx, pl.plane, a, p, op, nullptr, 0, false, nd, nullptr, false);
+                r2 = build_and_launch<kCapMid>(in, outs, pl.idx, pl.plane, pl.color, a, p, op, nullptr, 0, false, nd, nullptr, false);
             else
-                r2 = build_and_launch<kCapLarge>(in, outs, pl.idx, pl.plane, a, p, op, nullptr, 0, false, nd, nullptr, false);
+                r2 = build_and_launch<kCapLarge>(in, outs, pl.idx, pl.plane, pl.color, a, p, op, nullptr, 0, false, nd, nullptr, false);
             if (r2 != DC_OK) return r2;
         }
     }
@@ -611,11 +651,11 @@ int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_deco
         uint8_t* w = static_cast<uint8_t*>(ws);
         int r2;
         if (cnt <= kCapSmall)
-            r2 = build_and_launch<kCapSmall>(in, out, pl.idx, pl.plane, use_planes, p, op, w, (int64_t)ws_bytes, first, &dummy, stream, true);
+            r2 = build_and_launch<kCapSmall>(in, out, pl.idx, pl.plane, pl.color, use_planes, p, op, w, (int64_t)ws_bytes, first, &dummy, stream, true);
         else if (cnt <= kCapMid)
-            r2 = build_and_launch<kCapMid>(in, out, pl.idx, pl.plane, use_planes, p, op, w, (int64_t)ws_bytes, first, &dummy, stream, true);
+            r2 = build_and_launch<kCapMid>(in, out, pl.idx, pl.plane, pl.color, use_planes, p, op, w, (int64_t)ws_bytes, first, &dummy, stream, true);
         else
-            r2 = build_and_launch<kCapLarge>(in, out, pl.idx, pl.plane, use_planes, p, op, w, (int64_t)ws_bytes, first, &dummy, stream, true);
+            r2 = build_and_launch<kCapLarge>(in, out, pl.idx, pl.plane, pl.color, use_planes, p, op, w, (int64_t)ws_bytes, first, &dummy, stream, true);
         if (r2 != DC_OK) return r2;
         first = false;
     }
@@ -627,7 +667,7 @@ int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_deco
 // least it accepts.  0 on invalid arguments.
 size_t workspace_query(int32_t op, const dc_image_in* in, int32_t n, const void* op_params, bool min_only)
 {
-    static const dc_decolor_params kBeta = {0.55f, 0.8f};
+    static const dc_decolor_params kBeta = {0.55f, 0.8f, DC_LUMA_OURS, 1.0f};
     static const dc_global_params kGlobal = {DC_SIGMOID, 1.0f, 1e-4f, 0};
     OpArgs a{0, nullptr, nullptr, nullptr};
     if (op == DC_OP_DECOLORIZE) {
@@ -672,6 +712,32 @@ DC_API int dc_decolorize_tonemap_local(const dc_image_in* in, const dc_image_out
 {
     OpArgs op{kOpkLocal, nullptr, lparams, nullptr};
     return run(in, out, n, params, op, ws, ws_bytes, stream, nullptr);
+}
+
+DC_API int dc_decolorize_tonemap_video(const dc_image_in* in, const dc_image_out* out, int32_t n,
+                                       const dc_decolor_params* params, const dc_global_params* gparams, float lambda,
+                                       int32_t restart, dc_video_state* state, void* ws, size_t ws_bytes, void* stream)
+{
+    if (!state || (restart != 0 && restart != 1)) return DC_ERR_INVALID_ARG;
+    OpArgs op{kOpkGlobal, gparams, nullptr, nullptr};
+    op.vstate = state;
+    op.restart = restart != 0;
+    op.lambda = lambda;
+    return run(in, out, n, params, op, ws, ws_bytes, stream, nullptr);
+}
+
+DC_API int dc_preset(int32_t preset, dc_decolor_params* p, dc_local_params* l)
+{
+    float bk;
+    switch (preset) {
+    case DC_PRESET_PAPER: bk = 0.8f; break;   // Sec. II-B
+    case DC_PRESET_TM1: bk = 0.55f; break;    // background boost: cool blend weighted up
+    case DC_PRESET_TM2: bk = 0.95f; break;    // background suppression: warm blend dominates
+    default: return DC_ERR_INVALID_ARG;
+    }
+    if (p) *p = dc_decolor_params{0.55f, bk, DC_LUMA_OURS, 1.0f};
+    if (l) *l = dc_local_params{32, 2, 32, 1.0f, 1e-4f, 0};
+    return DC_OK;
 }
 
 DC_API size_t dc_workspace_bytes(int32_t op, const dc_image_in* in, int32_t n, const void* op_params)
@@ -816,7 +882,7 @@ DC_API int dc_debug_bounds(uint32_t* flags, int32_t* checked)
     return DC_OK;
 }
 
-DC_API int dc_version(void) { return 100; }
+DC_API int dc_version(void) { return 200; }
 
 }  // extern "C"
 

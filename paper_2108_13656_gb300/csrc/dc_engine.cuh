@@ -168,7 +168,15 @@ __device__ __forceinline__ float exp_fast(float x) { return __expf(x); }
 // ------------------------------------------------------------- Eq. 1-6 -------
 struct Beta {
     float bR, one_m_bR, bk, one_m_bk;
+    int luma;  // DC_LUMA_OURS (Eq. 1-6), DC_LUMA_Y or DC_LUMA_V
 };
+
+// The comparison channels of Sec. I / Fig. GTMO on non-negative samples: MATLAB's
+// rgb2gray weights, or V of HSV.
+__device__ __forceinline__ float luma_other(float R, float G, float B, int luma)
+{
+    return luma == DC_LUMA_Y ? fmaf(0.1140f, B, fmaf(0.5870f, G, 0.2989f * R)) : fmaxf(R, fmaxf(G, B));
+}
 
 // ------------------------------------------------- paired binary32 (f32x2) ---
 // Blackwell executes add/sub/mul/fma on a pair of binary32 values as one
@@ -323,6 +331,105 @@ __device__ __forceinline__ void luminance_hdr_x2(float R0, float G0, float B0, f
     if (!(L1 <= 3.0e38f) || (L1 == 0.0f && s1 > 0.0f)) L1 = luminance_rescaled(R1, G1, B1, be);
 }
 
+// ----------------------------------------------- float-float (hi + lo) ------
+// Unevaluated sums of two binary32 numbers (Dekker; Knuth's two-sum; the FMA
+// product error), about 44 significant bits.  Used where binary32 alone is too
+// coarse: the 8-bit local operator's bin coordinate, whose curve slope reaches the
+// bin count (a binary32 L, good to about 1e-7, would move its output by up to 3e-6).
+struct FF {
+    float hi, lo;
+};
+__device__ __forceinline__ FF ff_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b), bp = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp))};
+}
+__device__ __forceinline__ FF ff_fast_two_sum(float a, float b)  // |a| >= |b| or a = 0
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ FF ff_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ FF ff_add(FF x, FF y)
+{
+    const FF s = ff_two_sum(x.hi, y.hi);
+    return ff_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
+}
+__device__ __forceinline__ FF ff_neg(FF x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ FF ff_mul(FF x, FF y)
+{
+    const FF p = ff_prod(x.hi, y.hi);
+    return ff_fast_two_sum(p.hi, fmaf(x.hi, y.lo, fmaf(x.lo, y.hi, p.lo)));
+}
+__device__ __forceinline__ FF ff_mulf(FF x, float f)
+{
+    const FF p = ff_prod(x.hi, f);
+    return ff_fast_two_sum(p.hi, fmaf(x.lo, f, p.lo));
+}
+// a / b for binary32 a, b (b > 0): the rounded quotient and the exact remainder's share.
+__device__ __forceinline__ FF ff_divf(float a, float b)
+{
+    const float q = __fdiv_rn(a, b);
+    return ff_fast_two_sum(q, __fdiv_rn(fmaf(-q, b, a), b));
+}
+// x / b for a float-float x and binary32 b > 0.
+__device__ __forceinline__ FF ff_div_by(FF x, float b)
+{
+    const float q = __fdiv_rn(x.hi, b);
+    return ff_fast_two_sum(q, __fdiv_rn(__fadd_rn(fmaf(-q, b, x.hi), x.lo), b));
+}
+// Square root: the rounded root s of hi and one Newton correction (x - s^2) / 2s.
+__device__ __forceinline__ FF ff_sqrt(FF x)
+{
+    if (!(x.hi > 0.0f)) return {0.0f, 0.0f};
+    const float s = __fsqrt_rn(x.hi);
+    const float r = __fadd_rn(fmaf(-s, s, x.hi), x.lo);
+    return ff_fast_two_sum(s, __fdiv_rn(r, __fmul_rn(2.0f, s)));
+}
+
+// Eq. 1-6 in float-float for 8-bit codes R, G, B (0..255, exact in binary32), in
+// code units; the betas are the binary32 parameters themselves (1 - beta exactly).
+__device__ __forceinline__ FF luminance_ff(float R, float G, float B, const Beta& be)
+{
+    const float S = (R + G) + B;  // exact
+    if (S == 0.0f) return {0.0f, 0.0f};
+    const float R2 = R * R, G2 = G * G;                     // exact (< 2^16)
+    const float n1 = fmaf(B, B, R2 + G2);                   // exact (< 2^18)
+    const FF L_WHITE = ff_sqrt(ff_divf(n1, 3.0f));          // Eq. 1
+    const FF omR = ff_two_sum(1.0f, -be.bR);
+    const FF L_GR = ff_sqrt(ff_add(ff_prod(be.bR, R2), ff_mulf(omR, G2)));  // Eq. 3
+    const FF r = ff_divf(R, S), b = ff_divf(B, S);
+    const FF L_WARM = ff_add(L_WHITE, ff_mul(r, ff_add(L_GR, ff_neg(L_WHITE))));   // Eq. 4
+    const FF L_COOL = ff_add({B, 0.0f}, ff_mul(b, ff_add(L_WHITE, {-B, 0.0f})));   // Eq. 5, L_B = B
+    const FF omk = ff_two_sum(1.0f, -be.bk);
+    const FF Q = ff_add(ff_mulf(ff_mul(L_WARM, L_WARM), be.bk), ff_mul(omk, ff_mul(L_COOL, L_COOL)));
+    return ff_sqrt(Q);                                      // Eq. 6
+}
+
+// The chosen channel of 8-bit codes in float-float (code units).
+__device__ __forceinline__ FF luma_ff(float R, float G, float B, const Beta& be)
+{
+    if (be.luma == DC_LUMA_OURS) return luminance_ff(R, G, B, be);
+    if (be.luma == DC_LUMA_Y) return ff_add(ff_add(ff_prod(0.2989f, R), ff_prod(0.5870f, G)), ff_prod(0.1140f, B));
+    return {fmaxf(R, fmaxf(G, B)), 0.0f};
+}
+
+// Bin coordinate t = bins * L / 255 of an 8-bit pixel in units of 2^-24 (rounded),
+// from the float-float luminance: 0 <= t 2^24 <= bins 2^24 <= 2^29.
+__device__ __forceinline__ uint32_t ucoord_u8(float R, float G, float B, const Beta& be, int bins)
+{
+    const FF L = luma_ff(R, G, B, be);
+    const FF t = ff_div_by(ff_mulf(L, (float)bins), 255.0f);
+    const float hs = t.hi * 16777216.0f, ls = t.lo * 16777216.0f;  // exact scalings
+    const int qh = __float2int_rn(hs);
+    const int q = qh + __float2int_rn(__fadd_rn(__fsub_rn(hs, (float)qh), ls));
+    return (uint32_t)min(max(q, 0), bins << 24);
+}
+
 // 8-bit code of y in [0,1]: floor(255 y + 1/2), clamped.
 __device__ __forceinline__ uint32_t quant_u8(float y)
 {
@@ -363,6 +470,10 @@ struct GroupIO {
     // full group given as its 48 raw bytes (twelve 32-bit words).
     __device__ static __forceinline__ void decode(const uint32_t (&w)[12], const Beta& be, float (&Lv)[G])
     {
+        if (be.luma != DC_LUMA_OURS) {
+            decode_other(w, be.luma, Lv);
+            return;
+        }
         if constexpr (IN_DT == DC_U8) {
 #pragma unroll
             for (int k = 0; k < G; k += 2) {
@@ -393,6 +504,33 @@ struct GroupIO {
         }
     }
 
+    // Sample i (0 .. 3G-1) of a group's raw words as a linear value: 8-bit codes as
+    // code values (0..255, not yet divided by 255); HDR samples with negatives and
+    // NaN read as 0.
+    __device__ static __forceinline__ float sample(const uint32_t (&w)[12], int i)
+    {
+        if constexpr (IN_DT == DC_U8) {
+            return u8_at(w, i);
+        } else if constexpr (IN_DT == DC_F16) {
+            __half2 h;
+            memcpy(&h, &w[i >> 1], 4);
+            const float2 v = __half22float2(h);
+            return fmaxf((i & 1) ? v.y : v.x, 0.0f);
+        } else {
+            return fmaxf(__uint_as_float(w[i]), 0.0f);
+        }
+    }
+
+    // The comparison channels (DC_LUMA_Y, DC_LUMA_V) of a group, in [0,1] units.
+    __device__ static __forceinline__ void decode_other(const uint32_t (&w)[12], int luma, float (&Lv)[G])
+    {
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            const float v = luma_other(sample(w, 3 * k), sample(w, 3 * k + 1), sample(w, 3 * k + 2), luma);
+            Lv[k] = IN_DT == DC_U8 ? v * (1.0f / 255.0f) : v;
+        }
+    }
+
     // Bytes each buffer of an image spans (for the bounds-checked build).
     __device__ static __forceinline__ int64_t in_extent(const DcImage& im)
     {
@@ -405,7 +543,125 @@ struct GroupIO {
     __device__ static __forceinline__ int64_t out_extent(const DcImage& im)
     {
         const int oe = im.out_dt == DC_U8 ? 1 : (im.out_dt == DC_F16 ? 2 : 4);
-        return (int64_t)(im.rows - 1) * im.out_stride + (int64_t)im.cols * oe;
+        return (int64_t)(im.rows - 1) * im.out_stride + (int64_t)im.cols * oe * ((im.flags & IF_COLOR) ? 3 : 1);
+    }
+
+    // The n (< G, or unaligned) pixels at (r, c) packed like a full group's raw words,
+    // the lanes past n zero: the same decode then applies.
+    __device__ static void gather_raw(const DcImage& im, int r, int c, int n, uint32_t (&w)[12])
+    {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) w[k] = 0u;
+        const uint8_t* p = im.in + (int64_t)r * im.in_stride + (int64_t)c * 3 * ESZ;
+        if (!bc_ok(p, (int64_t)n * 3 * ESZ, im.in, in_extent(im), BC_IN)) return;
+        for (int i = 0; i < 3 * n; ++i) {
+            if constexpr (ESZ == 1) {
+                w[i >> 2] |= (uint32_t)__ldg(p + i) << (8 * (i & 3));
+            } else if constexpr (ESZ == 2) {
+                w[i >> 1] |= (uint32_t)__ldg(reinterpret_cast<const unsigned short*>(p) + i) << (16 * (i & 1));
+            } else {
+                w[i] = __ldg(reinterpret_cast<const uint32_t*>(p) + i);
+            }
+        }
+    }
+
+    // Colour reconstruction of one group (DC_LUMA_* luminance Lv in [0,1] units, tone-
+    // mapped values y): o[3k + i] = min(1, y (C_i / L)^s), a black pixel giving y.
+    // The ratio C_i / L is taken in code units for 8-bit input; a pixel whose L lies
+    // outside [2^-60, 2^60] is scaled by a power of two first (exact), its luminance
+    // recomputed, so that the ratio keeps full precision.
+    __device__ static __forceinline__ void color_values(const uint32_t (&w)[12], const float (&Lv)[G],
+                                                        const float (&y)[G], const Beta& be, float s, bool s_one,
+                                                        float (&o)[3 * G])
+    {
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            float C[3] = {sample(w, 3 * k), sample(w, 3 * k + 1), sample(w, 3 * k + 2)};
+            float L = IN_DT == DC_U8 ? Lv[k] * 255.0f : Lv[k];
+            if (!(L > 0.0f)) {
+                o[3 * k] = o[3 * k + 1] = o[3 * k + 2] = y[k];
+                continue;
+            }
+            if (L < 0x1p-60f || L > 0x1p60f) rescale_pixel(C, be, L);
+            if (s_one) {
+                const float q = y[k] * rcp_fast(L);
+#pragma unroll
+                for (int i = 0; i < 3; ++i) o[3 * k + i] = fminf(C[i] * q, 1.0f);
+            } else {
+                const float lL = lg2_ftz(L);
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+                    o[3 * k + i] = C[i] > 0.0f ? fminf(y[k] * exp2f(s * (lg2_ftz(C[i]) - lL)), 1.0f)
+                                               : (s == 0.0f ? y[k] : 0.0f);
+            }
+        }
+    }
+
+    // A pixel with a tiny or huge luminance: samples scaled by 2^-e (e the exponent of
+    // the largest) and its luminance recomputed from them (every channel is
+    // 1-homogeneous, so the ratios are unchanged).
+    __device__ static __forceinline__ void rescale_pixel(float (&C)[3], const Beta& be, float& L)
+    {
+        int e;
+        frexpf(fmaxf(C[0], fmaxf(C[1], C[2])), &e);
+        const float sc = ldexpf(1.0f, -e);
+        C[0] *= sc;
+        C[1] *= sc;
+        C[2] *= sc;
+        L = be.luma == DC_LUMA_OURS ? luminance_f32(C[0], C[1], C[2], be) : luma_other(C[0], C[1], C[2], be.luma);
+    }
+
+    // Store the 3n colour values of n pixels at (r, c) (interleaved RGB output).
+    __device__ static void store_rgb(const DcImage& im, int r, int c, int n, bool vec, const float (&o)[3 * G])
+    {
+        const int oe = im.out_dt == DC_U8 ? 1 : (im.out_dt == DC_F16 ? 2 : 4);
+        uint8_t* p = im.out + (int64_t)r * im.out_stride + (int64_t)c * 3 * oe;
+        if (!bc_ok(p, (int64_t)(vec ? G : n) * 3 * oe, im.out, out_extent(im), BC_OUT)) return;
+        if (im.out_dt == DC_U8) {
+            if (vec) {  // 3G bytes at a multiple of 3G: 8-byte pieces (G = 8) or 4-byte ones (G = 4)
+                uint32_t wv[3 * G / 4];
+#pragma unroll
+                for (int k = 0; k < 3 * G / 4; ++k) wv[k] = 0u;
+#pragma unroll
+                for (int k = 0; k < 3 * G; ++k) wv[k >> 2] |= quant_u8(o[k]) << (8 * (k & 3));
+                if constexpr (G == 8) {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) reinterpret_cast<uint2*>(p)[k] = make_uint2(wv[2 * k], wv[2 * k + 1]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) reinterpret_cast<uint32_t*>(p)[k] = wv[k];
+                }
+            } else {
+                for (int k = 0; k < 3 * n; ++k) p[k] = (uint8_t)quant_u8(o[k]);
+            }
+        } else if (im.out_dt == DC_F16) {
+            if (vec) {  // 6G bytes at a multiple of 6G: 16-byte pieces (G = 8) or 8-byte ones (G = 4)
+                uint32_t wv[3 * G / 2];
+#pragma unroll
+                for (int k = 0; k < 3 * G / 2; ++k) {
+                    __half2 h = __floats2half2_rn(o[2 * k], o[2 * k + 1]);
+                    memcpy(&wv[k], &h, 4);
+                }
+                if constexpr (G == 8) {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k)
+                        reinterpret_cast<uint4*>(p)[k] = make_uint4(wv[4 * k], wv[4 * k + 1], wv[4 * k + 2], wv[4 * k + 3]);
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) reinterpret_cast<uint2*>(p)[k] = make_uint2(wv[2 * k], wv[2 * k + 1]);
+                }
+            } else {
+                for (int k = 0; k < 3 * n; ++k) reinterpret_cast<__half*>(p)[k] = __float2half_rn(o[k]);
+            }
+        } else {
+            if (vec) {  // 12G bytes: 16-byte pieces
+#pragma unroll
+                for (int k = 0; k < 3 * G / 4; ++k)
+                    reinterpret_cast<float4*>(p)[k] = make_float4(o[4 * k], o[4 * k + 1], o[4 * k + 2], o[4 * k + 3]);
+            } else {
+                for (int k = 0; k < 3 * n; ++k) reinterpret_cast<float*>(p)[k] = o[k];
+            }
+        }
     }
 
     // The raw bytes of a full, aligned group: 24 (u8, three 8-byte loads) or 48
@@ -461,6 +717,21 @@ struct GroupIO {
     // One pixel through the scalar path (ragged tails and unaligned images).
     __device__ static __noinline__ float scalar_luminance(const uint8_t* q, const Beta& be)
     {
+        if (be.luma != DC_LUMA_OURS) {
+            float c[3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                if constexpr (IN_DT == DC_U8) {
+                    c[i] = (float)__ldg(q + i);
+                } else if constexpr (IN_DT == DC_F16) {
+                    c[i] = fmaxf(__half2float(reinterpret_cast<const __half*>(q)[i]), 0.0f);
+                } else {
+                    c[i] = fmaxf(__ldg(reinterpret_cast<const float*>(q) + i), 0.0f);
+                }
+            }
+            const float v = luma_other(c[0], c[1], c[2], be.luma);
+            return IN_DT == DC_U8 ? v * (1.0f / 255.0f) : v;
+        }
         if constexpr (IN_DT == DC_U8) {
             return luminance_f32((float)__ldg(q), (float)__ldg(q + 1), (float)__ldg(q + 2), be) * (1.0f / 255.0f);
         } else if constexpr (IN_DT == DC_F16) {

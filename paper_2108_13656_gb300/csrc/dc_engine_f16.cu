@@ -3,12 +3,12 @@
 
 namespace dc {
 
-int launch_engine_f16(const void* batch, int cap, int opk, int kind, int ph, bool pl, LaunchShape ls, void* stream)
+int launch_engine_f16(const void* batch, int cap, int opk, int kind, int ph, int pl, LaunchShape ls, void* stream)
 {
     return launch_dispatch<DC_F16>(batch, cap, opk, kind, ph, pl, ls, stream);
 }
 
-int occupancy_f16(int cap, int opk, int kind, bool pl)
+int occupancy_f16(int cap, int opk, int kind, int pl)
 {
     return occupancy_dispatch<DC_F16>(cap, opk, kind, pl);
 }

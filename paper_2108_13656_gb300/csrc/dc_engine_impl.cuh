@@ -32,6 +32,17 @@ constexpr int kLocTS = 24, kGlobTS = 22;
 
 __device__ __forceinline__ void cta_sync() { __syncthreads(); }
 
+// Precise 8-bit bin coordinates of a group (IF_UPRECISE), as int32 bits in q.
+template <int IN_DT>
+__device__ __forceinline__ void ucoord_group(const uint32_t (&w)[12], int n, const Beta& be, int bins,
+                                             float (&q)[InT<IN_DT>::G])
+{
+#pragma unroll
+    for (int k = 0; k < InT<IN_DT>::G; ++k)
+        q[k] = k < n ? __uint_as_float(ucoord_u8(u8_at(w, 3 * k), u8_at(w, 3 * k + 1), u8_at(w, 3 * k + 2), be, bins))
+                     : 0.0f;
+}
+
 // Groups a thread loads before computing any of them (memory-level parallelism):
 // the light plane-reading phases keep 64 bytes in flight per thread, the f32 RGB
 // phases two 48-byte groups; the 8-bit and f16 RGB phases (more arithmetic per
@@ -178,11 +189,15 @@ __device__ __forceinline__ uint32_t coord_of(float val, bool is_log_plane, float
 // TXT x (256/TXT) grid, TXT the smallest power of two covering a row's groups, so
 // the mapping needs no integer division; each thread issues the loads of U groups
 // before computing any of them.
-template <int IN_DT, bool PLANE, class F>
+// RAW (RGB walks only): f also receives the group's raw sample words, which a
+// ragged or unaligned group gathers sample by sample (lanes past n zero), so that
+// every group then takes the same decode.
+template <int IN_DT, bool PLANE, bool RAW = false, class F>
 __device__ __forceinline__ void walk_group(const DcImage& im, const Beta& be, F&& f, int r, int c, int n, bool vec,
                                            const uint8_t* src, float (&v)[InT<IN_DT>::G],
                                            uint32_t (&w)[PLANE ? 1 : 12], bool load)
 {
+    static_assert(!(RAW && PLANE), "raw samples come from an RGB walk");
     if (load) {
         if constexpr (PLANE) {
             if (vec)
@@ -192,21 +207,26 @@ __device__ __forceinline__ void walk_group(const DcImage& im, const Beta& be, F&
         } else {
             if (vec)
                 GroupIO<IN_DT>::load_raw_at(im, src, w);
+            else if constexpr (RAW)
+                GroupIO<IN_DT>::gather_raw(im, r, c, n, w);
             else
                 GroupIO<IN_DT>::luminance(im, r, c, n, false, be, v);
         }
     } else {
         if constexpr (!PLANE) {
-            if (vec) GroupIO<IN_DT>::decode(w, be, v);
+            if (vec || RAW) GroupIO<IN_DT>::decode(w, be, v);
         }
-        f(r, c, n, vec, v);
+        if constexpr (RAW)
+            f(r, c, n, vec, v, w);
+        else
+            f(r, c, n, vec, v);
     }
 }
 
 // Full groups are addressed from a pointer per thread: along a row the U groups of
 // an iteration sit at constant offsets from it, down a column it advances by a
 // fixed step, so no group recomputes its address from (r, c).
-template <int IN_DT, bool PLANE, class F>
+template <int IN_DT, bool PLANE, bool RAW = false, class F>
 __device__ __forceinline__ void walk_tile(const DcImage& im, const TileRect& t, const Beta& be, F&& f)
 {
     constexpr int G = InT<IN_DT>::G, U = Unroll<IN_DT, PLANE>::value;
@@ -235,11 +255,12 @@ __device__ __forceinline__ void walk_tile(const DcImage& im, const TileRect& t, 
                     n[u] = gu < gpr ? min(G, t.c1 - c[u]) : 0;
                     vec[u] = vec_img && n[u] == G;
                     if (n[u] > 0)
-                        walk_group<IN_DT, PLANE>(im, be, f, r, c[u], n[u], vec[u], q + u * kThreads * GB, v[u], w[u], true);
+                        walk_group<IN_DT, PLANE, RAW>(im, be, f, r, c[u], n[u], vec[u], q + u * kThreads * GB, v[u], w[u],
+                                                      true);
                 }
 #pragma unroll
                 for (int u = 0; u < U; ++u)
-                    if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, r, c[u], n[u], vec[u], nullptr, v[u], w[u], false);
+                    if (n[u] > 0) walk_group<IN_DT, PLANE, RAW>(im, be, f, r, c[u], n[u], vec[u], nullptr, v[u], w[u], false);
             }
         }
     } else {
@@ -255,11 +276,11 @@ __device__ __forceinline__ void walk_tile(const DcImage& im, const TileRect& t, 
             for (int u = 0; u < U; ++u) {
                 rr[u] = r + u * rpi;
                 n[u] = rr[u] < t.r1 ? nn : 0;
-                if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, rr[u], cc, n[u], vv, q + u * step, v[u], w[u], true);
+                if (n[u] > 0) walk_group<IN_DT, PLANE, RAW>(im, be, f, rr[u], cc, n[u], vv, q + u * step, v[u], w[u], true);
             }
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, rr[u], cc, n[u], vv, nullptr, v[u], w[u], false);
+                if (n[u] > 0) walk_group<IN_DT, PLANE, RAW>(im, be, f, rr[u], cc, n[u], vv, nullptr, v[u], w[u], false);
         }
     }
 }
@@ -269,7 +290,7 @@ __device__ __forceinline__ void walk_tile(const DcImage& im, const TileRect& t, 
 // 32/lx rows down), so that the lanes of a warp read the same block's tone curves -
 // mostly the same or neighbouring bins of them - instead of several blocks' (fewer
 // shared-memory bank conflicts).  Groups stay aligned to multiples of G.
-template <int IN_DT, bool PLANE, class F>
+template <int IN_DT, bool PLANE, bool RAW = false, class F>
 __device__ __forceinline__ void walk_block_patches(const DcImage& im, const TileRect& t, int s, const Beta& be, F&& f)
 {
     constexpr int G = InT<IN_DT>::G, U = Unroll<IN_DT, PLANE>::value;
@@ -300,12 +321,12 @@ __device__ __forceinline__ void walk_block_patches(const DcImage& im, const Tile
                 if (n[u] > 0) {
                     const uint8_t* src = PLANE ? im.plane + (int64_t)rr[u] * im.plane_stride + (int64_t)c[u] * 4
                                                : im.in + (int64_t)rr[u] * im.in_stride + (int64_t)c[u] * 3 * InT<IN_DT>::ESZ;
-                    walk_group<IN_DT, PLANE>(im, be, f, rr[u], c[u], n[u], vec[u], src, v[u], w[u], true);
+                    walk_group<IN_DT, PLANE, RAW>(im, be, f, rr[u], c[u], n[u], vec[u], src, v[u], w[u], true);
                 }
             }
 #pragma unroll
             for (int u = 0; u < U; ++u)
-                if (n[u] > 0) walk_group<IN_DT, PLANE>(im, be, f, rr[u], c[u], n[u], vec[u], nullptr, v[u], w[u], false);
+                if (n[u] > 0) walk_group<IN_DT, PLANE, RAW>(im, be, f, rr[u], c[u], n[u], vec[u], nullptr, v[u], w[u], false);
         }
     }
 }
@@ -633,6 +654,91 @@ __device__ void tile_apply_global(const DcBatch<CAP>& P, const DcImage& im,
     }
 }
 
+// Global curve with colour output: L and the tone-mapped y from the recomputed
+// luminance, then the colour reconstruction of every pixel (interleaved RGB out).
+template <int IN_DT, int CAP>
+__device__ void tile_apply_global_color(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* ic, const TileRect& t,
+                                        const Beta& be, const Derived& d, unsigned char* smem)
+{
+    constexpr int G = InT<IN_DT>::G;
+    SmemApplyG& S = *reinterpret_cast<SmemApplyG*>(smem);
+    const float delta = P.delta, cs = P.color_s;
+    const bool s_one = P.color_s_one != 0, sigmoid = P.mode == DC_SIGMOID, ldr = P.ldr != 0;
+    if (!sigmoid) {
+        const long long N = (long long)im.prow * (long long)im.pcol;
+        const uint32_t h = ld_cg_u32(&ic->hist[threadIdx.x]);
+        SmemStats& T = *reinterpret_cast<SmemStats*>(smem + sizeof(SmemApplyG));
+        const uint32_t cum = block_incl_scan(h, T.scan);
+        const float invN = 1.0f / __ll2float_rn(N);
+        if (ldr) {
+            S.lut[threadIdx.x] = __uint2float_rn(cum) * invN;
+        } else {
+            S.lut[threadIdx.x] = __uint2float_rn(cum - h) * invN;
+            if (threadIdx.x == 0) S.lut[256] = 1.0f;
+        }
+        cta_sync();
+    }
+    const float mu = d.mu, exp_mu = d.exp_mu, k = P.gain_k;
+    const bool one = P.gain_is_one != 0;
+    walk_tile<IN_DT, false, true>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G], const uint32_t (&w)[12])
+                                                 __attribute__((always_inline)) {
+        float y[G], o[3 * G];
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if (sigmoid) {
+                const float x = Lv[j] + delta;
+                y[j] = one ? __fdividef(x, x + exp_mu) : rcp_fast(1.0f + exp_fast(-k * (ln_fast(x) - mu)));
+            } else if (ldr) {
+                y[j] = S.lut[quant_u8(Lv[j])];
+            } else {
+                const uint32_t q = coord_of<kGlobTS>(Lv[j], false, delta, d);
+                const uint32_t b = min(q >> kGlobTS, 255u);
+                const float frac = (float)(q - (b << kGlobTS)) * (1.0f / (float)(1u << kGlobTS));
+                const float e0 = S.lut[b], e1 = S.lut[b + 1];
+                y[j] = fmaf(frac, e1 - e0, e0);
+            }
+        }
+        GroupIO<IN_DT>::color_values(w, Lv, y, be, cs, s_one, o);
+        GroupIO<IN_DT>::store_rgb(im, r, c, n, vec, o);
+    });
+}
+
+// ---------------------------------------------------------- phase: video --
+// Frame sequences: the centred sigmoid around the carried log-mean m of the image's
+// stream (one pass), and the frame's own log-sum for the next estimate, rounded per
+// group to 2^-24 exactly as the statistics pass sums it.
+template <int IN_DT, int CAP>
+__device__ void tile_video(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* ic, const TileRect& t,
+                           const Beta& be, const Derived& d, unsigned char* smem)
+{
+    constexpr int G = InT<IN_DT>::G;
+    SmemStats& S = *reinterpret_cast<SmemStats*>(smem);
+    const float delta = P.delta, mu = d.mu, exp_mu = d.exp_mu, k = P.gain_k;
+    const bool one = P.gain_is_one != 0;
+    long long acc = 0;
+    consume_tile<IN_DT, false>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+        float v[G];
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            const float x = Lv[j] + delta;
+            const float lx = ln_fast(x);
+            v[j] = j < n ? lx : 0.0f;
+            Lv[j] = one ? __fdividef(x, x + exp_mu) : rcp_fast(1.0f + exp_fast(-k * (lx - mu)));
+        }
+        GroupIO<IN_DT>::store(im, r, c, n, vec, Lv);
+        acc += __float2ll_rn(pairwise_sum<G>(v) * (float)(1 << kLogFixedShift));
+    });
+    acc = warp_sum_ll(acc);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) S.wsum[warp] = acc;
+    cta_sync();
+    if (threadIdx.x == 0) {
+        long long sum = 0;
+        for (int w = 0; w < (kThreads / 32); ++w) sum += S.wsum[w];
+        atomicAdd(&ic->logsum, (unsigned long long)sum);
+    }
+}
+
 // ---------------------------------------------------- phase: local histograms --
 // Tent binning: x = B u - 1/2 in 2^-20 fixed point, clamped to [0, (B-1) 2^20];
 // j = x >> 20 takes 1 - f, bin j+1 takes f.  Per block and bin the tile counts the
@@ -661,8 +767,16 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
     const int xmax = (B - 1) << 20;
     const uint32_t magic = P.s_magic;
     const bool group_in_block = magic != 0u && s % G == 0;  // a G-pixel group never straddles blocks
+    // 8-bit input with the precise coordinate: from the raw codes of an RGB walk
+    const bool precise = ldr && (im.flags & IF_UPRECISE) != 0;
     cta_sync();
-    consume_tile<IN_DT, PLANE>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+    // wp: the group's raw words (RGB walk) or null (plane walk)
+    auto group_fn = [&](int r, int c, int n, bool vec, float (&Lv)[G], const uint32_t (*wp)[12])
+                        __attribute__((always_inline)) {
+        float qv[G];
+        if constexpr (IN_DT == DC_U8) {
+            if (precise && wp) ucoord_group<IN_DT>(*wp, n, be, B, qv);
+        }
         const int blk0 = group_in_block ? (int)__umulhi((uint32_t)(c - t.c0), magic) : 0;
         int cur = -1;
         uint32_t rc = 0u, rf = 0u;
@@ -670,7 +784,10 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
         for (int k = 0; k < G; ++k) {
             if (k < n) {
                 int x;
-                if (ldr) {
+                if (ldr && precise) {
+                    // t - 1/2 from 2^-24 to 2^-20 units, rounded (as for HDR input)
+                    x = min(max(((int)__float_as_uint(qv[k]) - (1 << (kLocTS - 1)) + 8) >> (kLocTS - 20), 0), xmax);
+                } else if (ldr) {
                     x = min(max(__float2int_rn(fmaf(fminf(fmaxf(Lv[k], 0.0f), 1.0f), scale, -524288.0f)), 0), xmax);
                 } else {
                     // t - 1/2 from 2^-24 to 2^-20 units, rounded
@@ -706,9 +823,20 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
         // instead of recomputing it (an HDR plane keeps the fixed-point log, from
         // which the apply pass takes the same coordinate)
         if constexpr (!PLANE) {
-            if (plane_out) GroupIO<IN_DT>::store_plane(im, r, c, n, vec, Lv);
+            if (plane_out) GroupIO<IN_DT>::store_plane(im, r, c, n, vec, precise ? qv : Lv);
         }
-    });
+    };
+    if constexpr (PLANE) {
+        walk_tile<IN_DT, true>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G])
+                                              __attribute__((always_inline)) { group_fn(r, c, n, vec, Lv, nullptr); });
+    } else if (IN_DT == DC_U8 && precise) {  // the raw codes are needed
+        walk_tile<IN_DT, false, true>(im, t, be,
+                                      [&](int r, int c, int n, bool vec, float (&Lv)[G], const uint32_t (&w)[12])
+                                          __attribute__((always_inline)) { group_fn(r, c, n, vec, Lv, &w); });
+    } else {
+        walk_tile<IN_DT, false>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G])
+                                               __attribute__((always_inline)) { group_fn(r, c, n, vec, Lv, nullptr); });
+    }
     cta_sync();
     unsigned long long* H = reinterpret_cast<unsigned long long*>(P.ws + im.ws_hist);
     const int J0 = t.c0 / s;
@@ -788,10 +916,13 @@ __device__ void tile_cdf(const DcBatch<CAP>& P, const DcImage& im, int I, const 
 // costs one 64-bit shared load and one FMA.  The bilinear geometry is tabulated
 // once per tile: per column the table slot of its left block and its weight, per
 // row the slot row of its upper block and its weight.
-template <int IN_DT, bool PLANE, int CAP>
+// PL: 0 recomputes L from RGB, 1 reads the plane, 2 recomputes L and writes the
+// colour reconstruction (interleaved RGB output).
+template <int IN_DT, int PL, int CAP>
 __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const TileRect& t, int I,
                                  const Beta& be, const Derived& d, unsigned char* smem)
 {
+    constexpr bool PLANE = PL == 1, COLOR = PL == 2;
     constexpr int G = InT<IN_DT>::G;
     constexpr int kColGroups = (kLocMaxCols + 16) / G;  // column-table stride between a group's entries
     static_assert((kLocMaxCols + 16) % G == 0, "column table splits into G rows");
@@ -858,8 +989,13 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
     }
     const float delta = P.delta, Bf = (float)B, alpha = P.alpha;
     constexpr int WSB = kTabRow;
+    const bool precise = ldr && (im.flags & IF_UPRECISE) != 0;
     cta_sync();
-    auto body = [&](auto alpha_one, auto out_dt) {
+    // CM, how a pixel's value gives its bin coordinate: 0 u = L (8-bit input), 1 the
+    // precise 8-bit coordinate as int32 bits, 2 the HDR fixed-point log (from the plane)
+    // or L (recomputed from RGB)
+    auto body = [&](auto alpha_one, auto out_dt, auto cm) {
+        constexpr int CM = decltype(cm)::value;
         // output values of one group in place
         auto curve_fn = [&](int r, int c, float (&Lv)[G]) __attribute__((always_inline)) {
             const int2 ri = S.row[r - t.r0];
@@ -869,20 +1005,23 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
 #pragma unroll
             for (int k = 0; k < G; ++k) {
                 // bin j and position tt in it: from u = L (8-bit input) or exactly from
-                // the fixed-point log coordinate (HDR)
+                // a fixed-point coordinate (precise 8-bit, HDR)
                 int j;
                 float tt, u = 0.0f;
-                if constexpr (ldr) {
+                if constexpr (CM == 0) {
                     u = fminf(fmaxf(Lv[k], 0.0f), 1.0f);
                     const float Bu = Bf * u;
                     const float jf = fminf(__fadd_rd(Bu, 8388608.0f), 8388608.0f + (float)(B - 1));  // 2^23 + floor
                     j = (int)(__float_as_uint(jf) - 0x4B000000u);
                     tt = Bu - (jf - 8388608.0f);
                 } else {
-                    // the bin coordinate of the histogram pass, from the fixed-point
-                    // log the plane keeps, or from L for an image without a plane
-                    const uint32_t q = PLANE ? bin_coord<kLocTS>(__float_as_int(Lv[k]), d)
-                                             : coord_of<kLocTS>(Lv[k], false, delta, d);
+                    // the bin coordinate of the histogram pass: the precise 8-bit one, the
+                    // HDR one from the fixed-point log the plane keeps, or from L
+                    uint32_t q;
+                    if constexpr (CM == 1)
+                        q = __float_as_uint(Lv[k]);
+                    else
+                        q = PLANE ? bin_coord<kLocTS>(__float_as_int(Lv[k]), d) : coord_of<kLocTS>(Lv[k], false, delta, d);
                     const uint32_t jq = min(q >> kLocTS, (uint32_t)(B - 1));
                     j = (int)jq;
                     // (q - j 2^24) / 2^24 in [0, 1] through the float bit pattern of 1 + x
@@ -907,6 +1046,31 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
         };
         if constexpr (PLANE) {
             walk_block_patches_plane<IN_DT, decltype(out_dt)::value>(im, t, s, curve_fn);
+        } else if constexpr (COLOR) {
+            const float cs = P.color_s;
+            const bool s_one = P.color_s_one != 0;
+            walk_block_patches<IN_DT, false, true>(
+                im, t, s, be, [&](int r, int c, int n, bool vec, float (&Lv)[G], const uint32_t (&w)[12])
+                                  __attribute__((always_inline)) {
+                    float y[G], o[3 * G];
+                    if constexpr (CM == 1) {
+                        ucoord_group<IN_DT>(w, n, be, B, y);
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < G; ++k) y[k] = Lv[k];
+                    }
+                    curve_fn(r, c, y);
+                    GroupIO<IN_DT>::color_values(w, Lv, y, be, cs, s_one, o);
+                    GroupIO<IN_DT>::store_rgb(im, r, c, n, vec, o);
+                });
+        } else if constexpr (CM == 1) {
+            walk_block_patches<IN_DT, false, true>(
+                im, t, s, be, [&](int r, int c, int n, bool vec, float (&Lv)[G], const uint32_t (&w)[12])
+                                  __attribute__((always_inline)) {
+                    ucoord_group<IN_DT>(w, n, be, B, Lv);
+                    curve_fn(r, c, Lv);
+                    GroupIO<IN_DT>::store(im, r, c, n, vec, Lv);
+                });
         } else {
             walk_block_patches<IN_DT, false>(im, t, s, be,
                                              [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
@@ -915,17 +1079,28 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
                                              });
         }
     };
-    // alpha = 1 and the output type as compile-time constants of the pixel loop
+    // alpha = 1, the output type (plane-reading pass) and the coordinate mode as
+    // compile-time constants of the pixel loop
+    auto by_cm = [&](auto alpha_one, auto out_dt) {
+        if constexpr (ldr) {
+            if (precise)
+                body(alpha_one, out_dt, std::integral_constant<int, 1>{});
+            else
+                body(alpha_one, out_dt, std::integral_constant<int, 0>{});
+        } else {
+            body(alpha_one, out_dt, std::integral_constant<int, 2>{});
+        }
+    };
     auto by_out = [&](auto alpha_one) {
         if constexpr (!PLANE) {
-            body(alpha_one, std::integral_constant<int, DC_F32>{});  // (the store dispatches itself)
+            by_cm(alpha_one, std::integral_constant<int, DC_F32>{});  // (the store dispatches itself)
         } else {
             if (im.out_dt == DC_U8)
-                body(alpha_one, std::integral_constant<int, DC_U8>{});
+                by_cm(alpha_one, std::integral_constant<int, DC_U8>{});
             else if (im.out_dt == DC_F16)
-                body(alpha_one, std::integral_constant<int, DC_F16>{});
+                by_cm(alpha_one, std::integral_constant<int, DC_F16>{});
             else
-                body(alpha_one, std::integral_constant<int, DC_F32>{});
+                by_cm(alpha_one, std::integral_constant<int, DC_F32>{});
         }
     };
     if (alpha == 1.0f)
@@ -939,7 +1114,8 @@ static_assert(kThreads == 256, "per-bin work uses one consumer thread per histog
 
 template <int KIND>
 struct PassSmem {
-    static constexpr size_t value = KIND == PK_STATS || KIND == PK_STATS_LOG || KIND == PK_LOGHIST ? sizeof(SmemStats)
+    static constexpr size_t value = KIND == PK_STATS || KIND == PK_STATS_LOG || KIND == PK_LOGHIST || KIND == PK_VIDEO
+                                        ? sizeof(SmemStats)
                                     : KIND == PK_APPLY_G                   ? sizeof(SmemApplyG) + sizeof(SmemStats)
                                     : KIND == PK_BLOCKH                    ? sizeof(SmemBlockH)
                                     : KIND == PK_CDF                       ? sizeof(SmemCdf)
@@ -951,15 +1127,36 @@ struct PassSmem {
 #define DC_MIN_CTAS 4
 #endif
 
+// Frame sequences, after the last tile of the pass: every image's stream estimate
+// m <- m + lambda (mu_t - m), mu_t the frame's log-mean from its exact log-sum.
+template <int CAP>
+__device__ void video_update(const DcBatch<CAP>& P)
+{
+    constexpr float unit = 1.0f / (float)(1 << kLogFixedShift);
+    for (int i = threadIdx.x; i < P.n_img; i += kThreads) {
+        const DcImage& im = P.img[i];
+        const long long N = (long long)im.prow * (long long)im.pcol;
+        const long long sum = (long long)ld_cg_u64(&img_ctrl(P.ctrl, i)->logsum);
+        const long long q = sum / N, rem = sum - q * N;
+        const float mu = (__ll2float_rn(q) + __ll2float_rn(rem) / __ll2float_rn(N)) * unit;
+        dc_video_state* st = &P.vstate[P.stats_index[i]];
+        st->m = fmaf(P.lambda, mu - st->m, st->m);
+        st->mu_last = mu;
+        st->frames += 1;
+    }
+}
+
 // One pass over all tiles of pass `ph` (kind KIND) of every image in the batch.
 // CTAs take tiles round-robin (last-first when the pass re-reads what the previous
-// pass just read, so the most recently touched data is still in L2).
-template <int IN_DT, int OPK, int KIND, int CAP, bool PL>
+// pass just read, so the most recently touched data is still in L2).  PL: for the
+// histogram and apply passes 1 = reads the plane, 2 = colour output (apply passes);
+// for the statistics passes 1 = only the reduction the call uses.
+template <int IN_DT, int OPK, int KIND, int CAP, int PL>
 __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __grid_constant__ DcBatch<CAP> P, int ph)
 {
     __shared__ __align__(16) unsigned char smem[PassSmem<KIND>::value];
     __shared__ Derived s_d;
-    const Beta be = {P.beta_r, 1.0f - P.beta_r, P.beta_k, 1.0f - P.beta_k};
+    const Beta be = {P.beta_r, 1.0f - P.beta_r, P.beta_k, 1.0f - P.beta_k, P.luma};
     const int total = P.seg_start[ph][P.n_img];
     const bool rev = P.reverse[ph] != 0;
     // derived values of the stats pass are needed by every later pass that
@@ -991,6 +1188,16 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
             cta_sync();
             cached = img;
         }
+        if constexpr (KIND == PK_VIDEO) {
+            if (img != cached) {  // the stream's carried estimate (updated only after the pass)
+                if (threadIdx.x == 0) {
+                    s_d.mu = ld_cg_f(&P.vstate[P.stats_index[img]].m);
+                    s_d.exp_mu = expf(s_d.mu);
+                }
+                cta_sync();
+                cached = img;
+            }
+        }
         if (P.profile && threadIdx.x == 0) atomicMax(&ic->t_start_not[ph], ~globaltimer_ns());
         int I;
         const TileRect tr = tile_rect<OPK>(P, im, KIND, lt, I);
@@ -1000,18 +1207,29 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
                 GroupIO<IN_DT>::store(im, r, c, n, vec, Lv);
             });
         } else if constexpr (KIND == PK_STATS) {
-            tile_stats<IN_DT, false, PL>(P, im, ic, tr, be, smem);  // (PL: only the log-sum)
+            tile_stats<IN_DT, false, PL != 0>(P, im, ic, tr, be, smem);  // (PL: only the log-sum)
         } else if constexpr (KIND == PK_STATS_LOG) {
-            tile_stats<IN_DT, true, PL>(P, im, ic, tr, be, smem);  // (PL: only the log range)
+            tile_stats<IN_DT, true, PL != 0>(P, im, ic, tr, be, smem);  // (PL: only the log range)
         } else if constexpr (KIND == PK_LOGHIST) {
-            tile_loghist<IN_DT, PL>(P, im, ic, tr, be, s_d, smem);
+            tile_loghist<IN_DT, PL == 1>(P, im, ic, tr, be, s_d, smem);
         } else if constexpr (KIND == PK_APPLY_G) {
             if (P.stats && lt == 0) write_stats(P, im, ic, img, s_d);
-            tile_apply_global<IN_DT, PL>(P, im, ic, tr, be, s_d, smem);
+            if (P.vstate && lt == 0 && threadIdx.x == 0) {  // a restarted stream: m = this frame's mu
+                dc_video_state* st = &P.vstate[P.stats_index[img]];
+                st->m = s_d.mu;
+                st->mu_last = s_d.mu;
+                st->frames = 1;
+            }
+            if constexpr (PL == 2)
+                tile_apply_global_color<IN_DT>(P, im, ic, tr, be, s_d, smem);
+            else
+                tile_apply_global<IN_DT, PL == 1>(P, im, ic, tr, be, s_d, smem);
         } else if constexpr (KIND == PK_BLOCKH) {
-            tile_blockh<IN_DT, PL>(P, im, tr, I, be, s_d, smem);
+            tile_blockh<IN_DT, PL == 1>(P, im, tr, I, be, s_d, smem);
         } else if constexpr (KIND == PK_CDF) {
             tile_cdf(P, im, I, tr, smem);
+        } else if constexpr (KIND == PK_VIDEO) {
+            tile_video<IN_DT>(P, im, ic, tr, be, s_d, smem);
         } else {
             tile_apply_local<IN_DT, PL>(P, im, tr, I, be, s_d, smem);
         }
@@ -1026,7 +1244,8 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
     // next call on this workspace.  Every CTA fences its work on the block and counts
     // itself; the one that counts last clears the block, counter included.  No CTA
     // waits for another.
-    if (P.reset_bytes > 0 && ph == P.n_phase - 1) {
+    // A frame-sequence pass's last CTA also updates every stream's estimate first.
+    if ((P.reset_bytes > 0 || KIND == PK_VIDEO) && ph == P.n_phase - 1) {
         __shared__ uint32_t s_last;
         cta_sync();
         if (threadIdx.x == 0) {
@@ -1036,13 +1255,19 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
         cta_sync();
         if (s_last) {
             __threadfence();
-            uint4* c = reinterpret_cast<uint4*>(P.ctrl);
-            for (int i = threadIdx.x; i < P.reset_bytes / 16; i += kThreads) c[i] = make_uint4(0u, 0u, 0u, 0u);
+            if constexpr (KIND == PK_VIDEO) {
+                video_update(P);
+                cta_sync();
+            }
+            if (P.reset_bytes > 0) {
+                uint4* c = reinterpret_cast<uint4*>(P.ctrl);
+                for (int i = threadIdx.x; i < P.reset_bytes / 16; i += kThreads) c[i] = make_uint4(0u, 0u, 0u, 0u);
+            }
         }
     }
 }
 
-template <int IN_DT, int OPK, int KIND, int CAP, bool PL>
+template <int IN_DT, int OPK, int KIND, int CAP, int PL>
 int launch_one(const void* batch, int ph, LaunchShape ls, void* stream)
 {
     const DcBatch<CAP>& b = *reinterpret_cast<const DcBatch<CAP>*>(batch);
@@ -1060,7 +1285,7 @@ int launch_one(const void* batch, int ph, LaunchShape ls, void* stream)
     return cudaGetLastError() == cudaSuccess ? DC_OK : DC_ERR_CUDA;
 }
 
-template <int IN_DT, int OPK, int KIND, int CAP, bool PL>
+template <int IN_DT, int OPK, int KIND, int CAP, int PL>
 int occupancy_one()
 {
     int nb = 0;
@@ -1070,20 +1295,21 @@ int occupancy_one()
     return nb;
 }
 
-// Valid (operation, pass kind, flag) triples, expanded for every batch capacity.  The
-// flag is "reads the plane" for the histogram and apply passes (8-bit input: only the
-// apply passes) and "lean reduction" for the statistics passes (8-bit input has no
-// STATS_LOG pass).
-#define DC_FOR_EACH_PASS(X)                                                                                  \
-    X(OPK_DECOLOR, PK_DECOLOR, false) X(OPK_GLOBAL, PK_STATS, false) X(OPK_GLOBAL, PK_STATS, true)          \
-        X(OPK_GLOBAL, PK_STATS_LOG, false) X(OPK_GLOBAL, PK_STATS_LOG, true) X(OPK_GLOBAL, PK_LOGHIST, false) \
-        X(OPK_GLOBAL, PK_LOGHIST, true) X(OPK_GLOBAL, PK_APPLY_G, false) X(OPK_GLOBAL, PK_APPLY_G, true)     \
-        X(OPK_LOCAL, PK_STATS_LOG, false) X(OPK_LOCAL, PK_STATS_LOG, true) X(OPK_LOCAL, PK_BLOCKH, false)    \
-        X(OPK_LOCAL, PK_BLOCKH, true) X(OPK_LOCAL, PK_CDF, false) X(OPK_LOCAL, PK_APPLY_L, false)            \
-        X(OPK_LOCAL, PK_APPLY_L, true)
+// Valid (operation, pass kind, variant) triples, expanded for every batch capacity.
+// The variant is 1 = "reads the plane" for the histogram and apply passes (8-bit
+// input: only the apply passes) and "lean reduction" for the statistics passes
+// (8-bit input has no STATS_LOG pass), 2 = colour output for the apply passes.
+#define DC_FOR_EACH_PASS(X)                                                                           \
+    X(OPK_DECOLOR, PK_DECOLOR, 0) X(OPK_GLOBAL, PK_STATS, 0) X(OPK_GLOBAL, PK_STATS, 1)              \
+        X(OPK_GLOBAL, PK_STATS_LOG, 0) X(OPK_GLOBAL, PK_STATS_LOG, 1) X(OPK_GLOBAL, PK_LOGHIST, 0)    \
+        X(OPK_GLOBAL, PK_LOGHIST, 1) X(OPK_GLOBAL, PK_APPLY_G, 0) X(OPK_GLOBAL, PK_APPLY_G, 1)        \
+        X(OPK_GLOBAL, PK_APPLY_G, 2) X(OPK_GLOBAL, PK_VIDEO, 0) X(OPK_LOCAL, PK_STATS_LOG, 0)         \
+        X(OPK_LOCAL, PK_STATS_LOG, 1) X(OPK_LOCAL, PK_BLOCKH, 0) X(OPK_LOCAL, PK_BLOCKH, 1)           \
+        X(OPK_LOCAL, PK_CDF, 0) X(OPK_LOCAL, PK_APPLY_L, 0) X(OPK_LOCAL, PK_APPLY_L, 1)               \
+        X(OPK_LOCAL, PK_APPLY_L, 2)
 
 template <int IN_DT>
-int launch_dispatch(const void* batch, int cap, int opk, int kind, int ph, bool pl, LaunchShape ls, void* stream)
+int launch_dispatch(const void* batch, int cap, int opk, int kind, int ph, int pl, LaunchShape ls, void* stream)
 {
 #define DC_CASE(OP, K, PL)                                                                               \
     if constexpr (!PL || IN_DT != DC_U8 || K == PK_APPLY_G || K == PK_APPLY_L || K == PK_STATS) {       \
@@ -1099,7 +1325,7 @@ int launch_dispatch(const void* batch, int cap, int opk, int kind, int ph, bool 
 }
 
 template <int IN_DT>
-int occupancy_dispatch(int cap, int opk, int kind, bool pl)
+int occupancy_dispatch(int cap, int opk, int kind, int pl)
 {
 #define DC_CASE(OP, K, PL)                                                                 \
     if constexpr (!PL || IN_DT != DC_U8 || K == PK_APPLY_G || K == PK_APPLY_L || K == PK_STATS) { \

@@ -29,6 +29,7 @@ enum PhaseKind : int32_t {
     PK_CDF = 5,       // local: window sums -> per-block cumulative tables
     PK_APPLY_L = 6,   // local: bilinear blend of block curves -> out
     PK_STATS_LOG = 7, // HDR histogram forms: exact fixed-point log statistics (+ plane)
+    PK_VIDEO = 8,     // frame sequences: sigmoid around the carried log-mean + this frame's log-sum
 };
 
 // per-image flags
@@ -36,6 +37,9 @@ enum : uint32_t {
     IF_VEC = 1u,      // 16-byte aligned pointers and strides: vector path
     IF_LPLANE = 2u,   // the image keeps an f32 plane (`plane`) that holds L between phases
     IF_PLANE_LOG = 4u,  // ... and it holds round(ln(L + delta) 2^24) as int32 bits instead of L
+    IF_COLOR = 8u,    // interleaved RGB output (colour reconstruction), 3 samples per pixel
+    IF_UPRECISE = 16u,  // 8-bit input, local operator: the bin coordinate comes from the float-float
+                        // luminance (f32 outputs); a plane, if kept, holds that coordinate as int32 bits
 };
 
 struct DcImage {                 // 96 bytes
@@ -118,6 +122,11 @@ struct DcBatch {
     int32_t need_logsum;               // statistics pass: the log-sum is used (sigmoid, or a stats record)
     int32_t need_minmax;               // statistics pass: min/max of the log are used (histogram
                                        // coordinates of the HDR forms, or a stats record)
+    int32_t luma;                      // DC_LUMA_*
+    float color_s;                     // saturation exponent of colour outputs
+    int32_t color_s_one;               // color_s == 1
+    float lambda;                      // frame sequences: smoothing of the carried log-mean
+    dc_video_state* vstate;            // frame sequences: per image (input order), or NULL
     int32_t block_s, radius, bins;
     uint32_t s_magic;                  // ceil(2^32 / block_s), 0 for block_s = 1: exact division of offsets < 2^16
     float alpha;
@@ -147,13 +156,15 @@ struct LaunchShape {
 };
 
 // opk: 0 decolorize, 1 global, 2 local; kind: PhaseKind; ph: index of the pass;
-// pl: the pass reads the plane every image of the launch keeps (f16/f32 input only)
-int launch_engine_u8(const void* batch, int cap, int opk, int kind, int ph, bool pl, LaunchShape ls, void* stream);
-int launch_engine_f16(const void* batch, int cap, int opk, int kind, int ph, bool pl, LaunchShape ls, void* stream);
-int launch_engine_f32(const void* batch, int cap, int opk, int kind, int ph, bool pl, LaunchShape ls, void* stream);
-int occupancy_u8(int cap, int opk, int kind, bool pl);
-int occupancy_f16(int cap, int opk, int kind, bool pl);
-int occupancy_f32(int cap, int opk, int kind, bool pl);
+// pl: 1 = the pass reads the plane every image of the launch keeps (histogram and apply
+// passes) or keeps only the reduction the call uses (statistics passes); 2 = colour output
+// (apply passes)
+int launch_engine_u8(const void* batch, int cap, int opk, int kind, int ph, int pl, LaunchShape ls, void* stream);
+int launch_engine_f16(const void* batch, int cap, int opk, int kind, int ph, int pl, LaunchShape ls, void* stream);
+int launch_engine_f32(const void* batch, int cap, int opk, int kind, int ph, int pl, LaunchShape ls, void* stream);
+int occupancy_u8(int cap, int opk, int kind, int pl);
+int occupancy_f16(int cap, int opk, int kind, int pl);
+int occupancy_f32(int cap, int opk, int kind, int pl);
 int bounds_u8(uint32_t* flags);   // bounds-check flags per translation unit (-1: not built with checks)
 int bounds_f16(uint32_t* flags);
 int bounds_f32(uint32_t* flags);

@@ -42,13 +42,14 @@ def test_library_exports_every_declared_symbol(abi):
     for name in syms:
         assert hasattr(lib, name), name
         assert name in abi._SIGS, "binding lacks " + name
-    assert lib.dc_version() == 100
+    assert lib.dc_version() == 200
 
 
 def test_struct_sizes(abi):
     assert ctypes.sizeof(abi.dc_image_in) == 32
     assert ctypes.sizeof(abi.dc_image_out) == 24
-    assert ctypes.sizeof(abi.dc_decolor_params) == 8
+    assert ctypes.sizeof(abi.dc_decolor_params) == 16
+    assert ctypes.sizeof(abi.dc_video_state) == 16
     assert ctypes.sizeof(abi.dc_global_params) == 16
     assert ctypes.sizeof(abi.dc_local_params) == 24
     assert ctypes.sizeof(abi.dc_tuning) == 16
@@ -223,3 +224,61 @@ def test_host_pipeline_rejects_zero_depth():
     from paper_2108_13656_gb300.pipeline import HostPipeline
     with pytest.raises(ValueError):
         HostPipeline({}, {}, [], depth=0)
+
+
+def test_new_fields_validated(abi):
+    lib = abi.load()
+    ins = (abi.dc_image_in * 1)(_img(16, 4))
+    out = (abi.dc_image_out * 1)(abi.dc_image_out(1 << 22, 16, 0, 0))
+    ws = ctypes.c_void_p(1 << 12)
+    g = abi.dc_global_params(0, 1.0, 1e-4, 0)
+    for bad in (abi.dc_decolor_params(0.55, 0.8, 3, 1.0), abi.dc_decolor_params(0.55, 0.8, -1, 1.0),
+                abi.dc_decolor_params(0.55, 0.8, 0, -0.5), abi.dc_decolor_params(0.55, 0.8, 0, 9.0),
+                abi.dc_decolor_params(0.55, 0.8, 0, float("nan"))):
+        assert lib.dc_decolorize_tonemap_global(ins, out, 1, ctypes.byref(bad), ctypes.byref(g), None, ws,
+                                                1 << 20, None) == abi.DC_ERR_INVALID_ARG
+    p = abi.dc_decolor_params(0.55, 0.8, 0, 1.0)
+    # 3-channel outputs: only for the tone-mapping calls, and with room for 3 samples a pixel
+    col = (abi.dc_image_out * 1)(abi.dc_image_out(1 << 22, 48, 0, 3))
+    assert lib.dc_decolorize(ins, col, 1, ctypes.byref(p), ws, 1 << 20, None) == abi.DC_ERR_INVALID_ARG
+    narrow = (abi.dc_image_out * 1)(abi.dc_image_out(1 << 22, 47, 0, 3))
+    assert lib.dc_decolorize_tonemap_global(ins, narrow, 1, ctypes.byref(p), ctypes.byref(g), None, ws, 1 << 20,
+                                            None) == abi.DC_ERR_INVALID_ARG
+    two = (abi.dc_image_out * 1)(abi.dc_image_out(1 << 22, 48, 0, 2))
+    assert lib.dc_decolorize_tonemap_global(ins, two, 1, ctypes.byref(p), ctypes.byref(g), None, ws, 1 << 20,
+                                            None) == abi.DC_ERR_INVALID_ARG
+    # a colour output that would overlap its input
+    ovl = (abi.dc_image_out * 1)(abi.dc_image_out(0x100000 - 100, 48, 0, 3))
+    ins2 = (abi.dc_image_in * 1)(_img(16, 4))
+    assert lib.dc_decolorize_tonemap_global(ins2, ovl, 1, ctypes.byref(p), ctypes.byref(g), None, ws, 1 << 20,
+                                            None) == abi.DC_ERR_INVALID_ARG
+
+
+def test_video_arguments_validated(abi):
+    lib = abi.load()
+    ins = (abi.dc_image_in * 1)(_img(16, 4))
+    out = (abi.dc_image_out * 1)(abi.dc_image_out(1 << 22, 16, 0, 0))
+    ws = ctypes.c_void_p(1 << 12)
+    p = abi.dc_decolor_params(0.55, 0.8, 0, 1.0)
+    g = abi.dc_global_params(0, 1.0, 1e-4, 0)
+    st = ctypes.c_void_p(1 << 24)
+    call = lib.dc_decolorize_tonemap_video
+    assert call(ins, out, 1, ctypes.byref(p), ctypes.byref(g), 1.0, 0, None, ws, 1 << 20, None) == abi.DC_ERR_INVALID_ARG
+    assert call(ins, out, 1, ctypes.byref(p), ctypes.byref(g), 1.0, 2, st, ws, 1 << 20, None) == abi.DC_ERR_INVALID_ARG
+    for lam in (0.0, -0.1, 1.5, float("nan")):
+        assert call(ins, out, 1, ctypes.byref(p), ctypes.byref(g), lam, 0, st, ws, 1 << 20, None) == abi.DC_ERR_INVALID_ARG
+    h = abi.dc_global_params(1, 1.0, 1e-4, 0)  # histogram equalisation has no frame-sequence form
+    assert call(ins, out, 1, ctypes.byref(p), ctypes.byref(h), 1.0, 0, st, ws, 1 << 20, None) == abi.DC_ERR_INVALID_ARG
+
+
+def test_presets(abi):
+    lib = abi.load()
+    p, lp = abi.dc_decolor_params(), abi.dc_local_params()
+    expect = {abi.DC_PRESET_PAPER: 0.8, abi.DC_PRESET_TM1: 0.55, abi.DC_PRESET_TM2: 0.95}
+    for code, bk in expect.items():
+        assert lib.dc_preset(code, ctypes.byref(p), ctypes.byref(lp)) == 0
+        assert p.beta_r == pytest.approx(0.55) and p.beta_k == pytest.approx(bk)
+        assert 0.5 < p.beta_k < 1 and p.luma == abi.DC_LUMA_OURS and p.color_s == 1.0
+        assert (lp.block_s, lp.radius_blocks, lp.bins, lp.alpha) == (32, 2, 32, 1.0)
+    assert lib.dc_preset(3, ctypes.byref(p), None) == abi.DC_ERR_INVALID_ARG
+    assert lib.dc_preset(abi.DC_PRESET_TM1, None, None) == 0

@@ -2,7 +2,8 @@
 
 - 512 x 512 8-bit S-LDR (seed 0), decolorize only: every pixel against the oracle.
 - 3840 x 2160 8-bit S-LDR (seed 1) and FP32 S-HDR over 5 decades (seed 2), both
-  tone-mapping operators: every pixel against the oracle.
+  tone-mapping operators: every pixel against the oracle; the 8-bit image also with
+  f32 outputs (the local operator's precise bin coordinate).
 - 7680 x 4320 S-HDR over 6 decades (mu = 0, sigma = 2.76, seed 4), local operator, FP16 storage and FP32
   storage with FP32 arithmetic: every pixel against the oracle run on the stored
   samples, and the error against the FP32 original reported (the precision study;
@@ -68,6 +69,23 @@ def test_config_4k(dc, oracle_mod, variant, op):
         y = _run(dc, op, img, torch.float32)
         err = check_f32(y, y64, what="4K f32 %s" % op)
         print("4K f32 %s: max |err| %.3g" % (op, err))
+
+
+@pytest.mark.parametrize("op", ["global", "local"])
+def test_config_4k_u8_input_f32_output(dc, oracle_mod, op):
+    # 8-bit input with an f32 output: the local operator takes its bin coordinate from
+    # the float-float luminance, so its output meets the f32 tolerance like the rest
+    import torch
+    from paper_2108_13656_gb300 import synth
+    img = synth.s_ldr(3840, 2160, seed=1)
+    L64 = oracle_mod.decolorize(img)
+    if op == "global":
+        y64, _ = oracle_mod.tonemap_global_plane(L64, ldr=True)
+    else:
+        y64 = oracle_mod.tonemap_local_plane(L64, ldr=True)
+    y = _run(dc, op, img, torch.float32)
+    err = check_f32(y, y64, what="4K u8 -> f32 %s" % op)
+    print("4K u8 -> f32 %s: max |err| %.3g" % (op, err))
 
 
 @pytest.mark.parametrize("storage", [np.float16, np.float32])
