@@ -182,6 +182,36 @@ def ncu_traffic(op_name: str):
     return float(v) if v is not None else None
 
 
+def issue_roofline(op_ms: dict, sm_mhz: float, n_sm: int):
+    """Per call, the time the SMs need just to issue its instructions - warp
+    instructions (ncu smsp__inst_executed.sum over the call's passes, from the committed
+    summary, taken on the current kernels) at one warp instruction per clock per SM
+    sub-partition (4 per SM) at the sampled SM clock - and that time over the measured
+    call time.  The 8-bit calls move 4 bytes a pixel, so their bound is instruction
+    issue, not HBM."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel_source_hash") != kernel_source_hash() or not sm_mhz:
+        return None
+    per = d.get("per_pass", {})
+    out = {}
+    for name, var, op, _, _ in OPS:
+        keys = ["%s/%s" % (name, k) for k in PASSES[(var, op)]]
+        if not all("inst" in per.get(k, {}) for k in keys):
+            continue
+        inst = sum(per[k]["inst"] for k in keys)
+        tinst = sum(per[k].get("thread_inst", 0.0) for k in keys)
+        t_issue_us = inst / (4.0 * n_sm * sm_mhz)
+        out[name] = {"warp_inst": inst, "thread_inst_per_px": tinst / NPIX, "issue_bound_us": t_issue_us,
+                     "measured_us": op_ms[name] * 1e3, "frac": t_issue_us / (op_ms[name] * 1e3),
+                     "peak": "%d SMs x 4 warp-instr/clk x %.0f MHz" % (n_sm, sm_mhz)}
+    return out or None
+
+
 # ----------------------------------------------------------------- CPU oracle ----
 def oracle_step(imgs, rows: int, r0: int = 0):
     """The FP64 oracle on the band of `rows` rows from row r0 of each variant, all four
@@ -373,6 +403,103 @@ def precision_8k(dev, peak: float) -> dict:
                      "frac_of_measured_hbm": bpp * W8 * H8 / ms / 1e6 / peak, "bytes_per_px": bpp}
         del x, y, call
     out["l2"] = "inputs (199 / 398 MB) larger than L2"
+    return out
+
+
+def _alone_ms(calls, flush, reps: int) -> list:
+    """Mean device time of each call alone, after an L2-flushing write: everything is
+    enqueued behind a 20 ms device sleep so the host is ahead and the events time the
+    device only."""
+    import torch
+    stream = torch.cuda.current_stream()
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+          for _ in calls]
+    torch.cuda.synchronize()
+    torch.cuda._sleep(20_000_000)
+    for k in range(reps):
+        for i, fn in enumerate(calls):
+            flush.fill_(k & 0xFF)
+            a, b = ev[i][k]
+            a.record(stream)
+            fn(k)
+            b.record(stream)
+    torch.cuda.synchronize()
+    return [float(np.mean([a.elapsed_time(b) for a, b in e])) for e in ev]
+
+
+# ------------------------------------------------------------ frame sequences ----
+def video_4k(dev, peak: float) -> dict:
+    """Frame sequences at 3840x2160: a frame of a running stream is ONE pass (Eq. 1-6,
+    the sigmoid around the carried log-mean, and the frame's own log-sum).  Each
+    variant alone after an L2-flushing write, and frames back to back: 8 frames on
+    rotating buffers captured in one CUDA graph and replayed (inputs far above L2)."""
+    import torch
+    import paper_2108_13656_gb300 as dc
+    imgs = make_inputs()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = {}
+    for var, odt, bpp in (("u8", torch.uint8, 4), ("f32", torch.float32, 16)):
+        xs = [torch.from_numpy(imgs[var]).to(dev) for _ in range(ROT)]
+        ys = [torch.empty((H, W), dtype=odt, device=dev) for _ in range(ROT)]
+        vs = dc.VideoStreams(1, lam=0.5, device=dev, workspace=dc.Workspace(device=dev))
+        calls = [vs.prepare(xs[r], ys[r]) for r in range(ROT)]
+        calls[0](restart=True)
+        for r in range(ROT):
+            calls[r]()
+        launches = dc.last_launch_count()
+        ms_alone = _alone_ms([lambda k: calls[k % ROT]()], flush, 60)[0]
+        g = torch.cuda.CUDAGraph()
+        main = torch.cuda.current_stream()
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(g, stream=side):
+                for r in range(ROT):
+                    calls[r](stream=side)
+        main.wait_stream(side)
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        reps = 40
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(main)
+        for _ in range(reps):
+            g.replay()
+        e1.record(main)
+        torch.cuda.synchronize()
+        ms_b2b = e0.elapsed_time(e1) / (reps * ROT)
+        out[var] = {"launches_per_frame": launches, "bytes_per_px": bpp,
+                    "alone_us": ms_alone * 1e3, "alone_GBps": bpp * NPIX / ms_alone / 1e6,
+                    "alone_frac_of_measured_hbm": bpp * NPIX / ms_alone / 1e6 / peak,
+                    "back_to_back_us": ms_b2b * 1e3, "back_to_back_gpix_s": NPIX / ms_b2b / 1e6,
+                    "back_to_back_GBps": bpp * NPIX / ms_b2b / 1e6,
+                    "back_to_back_frac_of_measured_hbm": bpp * NPIX / ms_b2b / 1e6 / peak}
+        del g, calls, vs, xs, ys
+        torch.cuda.empty_cache()
+    return out
+
+
+# ------------------------------------------------------------- colour outputs ----
+def color_4k(dev, peak: float) -> dict:
+    """Colour reconstruction at 3840x2160 (interleaved RGB out, s = 1): each call alone
+    after an L2-flushing write; algorithmic bytes = input + 3-channel output."""
+    import torch
+    import paper_2108_13656_gb300 as dc
+    imgs = make_inputs()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    out = {}
+    for var, odt, bpp in (("u8", torch.uint8, 3 + 3), ("f32", torch.float32, 12 + 12)):
+        x = torch.from_numpy(imgs[var]).to(dev)
+        y = torch.empty((H, W, 3), dtype=odt, device=dev)
+        for op in ("global", "local"):
+            kw = {"mode": "sigmoid"} if op == "global" else {}
+            call = dc.PreparedCall(op, x, y, workspace=dc.Workspace(device=dev), **kw)
+            call()
+            ms = _alone_ms([lambda k: call()], flush, 40)[0]
+            out["%s_%s" % (var, op)] = {"us": ms * 1e3, "gpix_s": NPIX / ms / 1e6, "bytes_per_px": bpp,
+                                        "GBps": bpp * NPIX / ms / 1e6,
+                                        "frac_of_measured_hbm": bpp * NPIX / ms / 1e6 / peak,
+                                        "launches": dc.last_launch_count()}
     return out
 
 
@@ -625,6 +752,10 @@ def run_native(args):
         "clocks": clk,
         "gpu_launches": launches,
     }
+    iss = issue_roofline(op_ms, (clk or {}).get("sm_mhz") or 0.0,
+                         torch.cuda.get_device_properties(dev).multi_processor_count)
+    if iss:
+        line["issue_roofline"] = iss
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(imgs)
     if not args.no_extras:
@@ -632,6 +763,9 @@ def run_native(args):
         line["ragged_batch"] = ragged_batch(dev, args.ragged_images, peak)
         torch.cuda.empty_cache()
         line["precision_8k_local"] = precision_8k(dev, peak)
+        torch.cuda.empty_cache()
+        line["video_4k"] = video_4k(dev, peak)
+        line["color_4k"] = color_4k(dev, peak)
         torch.cuda.empty_cache()
         line["serving"] = serving(dev, args.serve_requests, args.serve_rate)
     print(json.dumps(line))

@@ -399,20 +399,31 @@ class VideoStreams:
     def restart(self):
         self._restart = True
 
-    def __call__(self, frames, outputs, stream=None):
+    def prepare(self, frames, outputs):
+        """The call for these frame and output buffers with descriptors and workspace
+        resolved once: `call(restart=None, stream=None)` enqueues one frame per stream
+        (restart None: as the streams' state requires)."""
         frames, outputs = _as_list(frames), _as_list(outputs)
         if len(frames) != self.n:
             raise ValueError("expected %d frames (one per stream)" % self.n)
         ins, outs = _arrays(frames, outputs)
-        ptr, size, _ = _workspace(DC_OP_GLOBAL, ins, self.n, None, self.ws)
-        rc = self.lib.dc_decolorize_tonemap_video(ins, outs, self.n, ctypes.byref(self.p), ctypes.byref(self.g),
-                                                  self.lam, 1 if self._restart else 0,
-                                                  ctypes.c_void_p(self.state.data_ptr()), ctypes.c_void_p(ptr), size,
-                                                  _stream_handle(stream))
-        if rc != DC_OK:
-            raise DcError(rc, "dc_decolorize_tonemap_video")
-        self._restart = False
-        return outputs
+        ptr, size, buf = _workspace(DC_OP_GLOBAL, ins, self.n, None, self.ws)
+        ws, st = ctypes.c_void_p(ptr), ctypes.c_void_p(self.state.data_ptr())
+
+        def call(restart=None, stream=None):
+            r = self._restart if restart is None else bool(restart)
+            rc = self.lib.dc_decolorize_tonemap_video(ins, outs, self.n, ctypes.byref(self.p), ctypes.byref(self.g),
+                                                      self.lam, 1 if r else 0, st, ws, size, _stream_handle(stream))
+            if rc != DC_OK:
+                raise DcError(rc, "dc_decolorize_tonemap_video")
+            self._restart = False
+            return outputs
+
+        call.keep = (frames, outputs, buf)  # the buffers stay alive with the call
+        return call
+
+    def __call__(self, frames, outputs, stream=None):
+        return self.prepare(frames, outputs)(stream=stream)
 
     def states(self) -> list[dict]:
         raw = self.state.cpu().numpy().tobytes()
