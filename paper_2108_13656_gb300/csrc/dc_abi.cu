@@ -37,7 +37,7 @@ dc_tuning g_tune[3][3] = {
     {{256, 1, 0, 0}, {256, 1, 0, 0}, {256, 1, 0, 0}},
     {{256, 32, 0, 0}, {256, 32, 0, 0}, {256, 32, 0, 0}},
 };
-constexpr int kAutoCtasPerSm = 4;  // resident CTAs of a pass kernel (launch bounds)
+constexpr int kAutoCtasPerSm = DC_MIN_CTAS;  // resident CTAs of a pass kernel (launch bounds)
 
 // Workspaces registered with dc_workspace_prepare.  A call's control block (header
 // and per-launch / per-image records at the start of the workspace) must be zero

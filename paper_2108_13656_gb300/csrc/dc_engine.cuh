@@ -56,11 +56,15 @@ __device__ __forceinline__ bool bc_ok(const void*, int64_t, const void*, int64_t
 
 // ------------------------------------------------------------ memory access ---
 // Input pixels: read-only for the whole launch, so the loads may be scheduled
-// freely (not volatile); no L1 allocation, normal L2 caching.
+// freely (not volatile).  A thread's group is 24 or 48 contiguous bytes, so the lanes
+// of a warp read at a 24- or 48-byte stride and the two or three loads of a group
+// touch the same cache lines: the lines are allocated in L1 (first-evicted), so that
+// the later loads of a group hit what the first one brought in instead of fetching
+// the same sectors from L2 again.
 __device__ __forceinline__ uint4 ld_stream16(const void* p)
 {
     uint4 v;
-    asm("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+    asm("ld.global.nc.L1::evict_first.v4.u32 {%0,%1,%2,%3}, [%4];"
         : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
         : "l"(p));
     return v;
@@ -84,7 +88,7 @@ __device__ __forceinline__ unsigned long long policy_evict_last()
 __device__ __forceinline__ uint4 ld_stream16_hint(const void* p, unsigned long long pol)
 {
     uint4 v;
-    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+    asm("ld.global.nc.L1::evict_first.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
         : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
         : "l"(p), "l"(pol));
     return v;
@@ -100,7 +104,7 @@ __device__ __forceinline__ void st_f4_hint(float* p, float4 v, unsigned long lon
 __device__ __forceinline__ uint2 ld_stream8(const void* p)
 {
     uint2 v;
-    asm("ld.global.nc.L1::no_allocate.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
+    asm("ld.global.nc.L1::evict_first.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p));
     return v;
 }
 

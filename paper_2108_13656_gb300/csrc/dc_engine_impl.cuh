@@ -48,9 +48,12 @@ __device__ __forceinline__ void ucoord_group(const uint32_t (&w)[12], int n, con
 // phases two 48-byte groups; the 8-bit and f16 RGB phases (more arithmetic per
 // byte) rely on the number of warps instead (measured: two groups there cost time
 // or registers).
+#ifndef DC_UNROLL_F32_RGB
+#define DC_UNROLL_F32_RGB 2
+#endif
 template <int IN_DT, bool PLANE>
 struct Unroll {
-    static constexpr int value = PLANE ? (InT<IN_DT>::G == 4 ? 4 : 2) : (IN_DT == DC_F32 ? 2 : 1);
+    static constexpr int value = PLANE ? (InT<IN_DT>::G == 4 ? 4 : 2) : (IN_DT == DC_F32 ? DC_UNROLL_F32_RGB : 1);
 };
 
 // ------------------------------------------------------------ tile geometry ---
@@ -770,13 +773,13 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
     // 8-bit input with the precise coordinate: from the raw codes of an RGB walk
     const bool precise = ldr && (im.flags & IF_UPRECISE) != 0;
     cta_sync();
-    // wp: the group's raw words (RGB walk) or null (plane walk)
-    auto group_fn = [&](int r, int c, int n, bool vec, float (&Lv)[G], const uint32_t (*wp)[12])
+    // wp: the group's raw words (RGB walk) or null (plane walk); PREC: the precise
+    // 8-bit coordinate, a literal at each (inlined) call, so that each walk's loop
+    // holds only its own path
+    auto group_fn = [&](bool PREC, int r, int c, int n, bool vec, float (&Lv)[G], const uint32_t (*wp)[12])
                         __attribute__((always_inline)) {
         float qv[G];
-        if constexpr (IN_DT == DC_U8) {
-            if (precise && wp) ucoord_group<IN_DT>(*wp, n, be, B, qv);
-        }
+        if (PREC) ucoord_group<IN_DT>(*wp, n, be, B, qv);
         const int blk0 = group_in_block ? (int)__umulhi((uint32_t)(c - t.c0), magic) : 0;
         int cur = -1;
         uint32_t rc = 0u, rf = 0u;
@@ -784,7 +787,7 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
         for (int k = 0; k < G; ++k) {
             if (k < n) {
                 int x;
-                if (ldr && precise) {
+                if (PREC) {
                     // t - 1/2 from 2^-24 to 2^-20 units, rounded (as for HDR input)
                     x = min(max(((int)__float_as_uint(qv[k]) - (1 << (kLocTS - 1)) + 8) >> (kLocTS - 20), 0), xmax);
                 } else if (ldr) {
@@ -823,19 +826,23 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
         // instead of recomputing it (an HDR plane keeps the fixed-point log, from
         // which the apply pass takes the same coordinate)
         if constexpr (!PLANE) {
-            if (plane_out) GroupIO<IN_DT>::store_plane(im, r, c, n, vec, precise ? qv : Lv);
+            if (plane_out) GroupIO<IN_DT>::store_plane(im, r, c, n, vec, PREC ? qv : Lv);
         }
     };
     if constexpr (PLANE) {
-        walk_tile<IN_DT, true>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G])
-                                              __attribute__((always_inline)) { group_fn(r, c, n, vec, Lv, nullptr); });
+        walk_tile<IN_DT, true>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+            group_fn(false, r, c, n, vec, Lv, nullptr);
+        });
     } else if (IN_DT == DC_U8 && precise) {  // the raw codes are needed
         walk_tile<IN_DT, false, true>(im, t, be,
                                       [&](int r, int c, int n, bool vec, float (&Lv)[G], const uint32_t (&w)[12])
-                                          __attribute__((always_inline)) { group_fn(r, c, n, vec, Lv, &w); });
+                                          __attribute__((always_inline)) {
+                                              group_fn(true, r, c, n, vec, Lv, &w);
+                                          });
     } else {
-        walk_tile<IN_DT, false>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G])
-                                               __attribute__((always_inline)) { group_fn(r, c, n, vec, Lv, nullptr); });
+        walk_tile<IN_DT, false>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+            group_fn(false, r, c, n, vec, Lv, nullptr);
+        });
     }
     cta_sync();
     unsigned long long* H = reinterpret_cast<unsigned long long*>(P.ws + im.ws_hist);
@@ -1122,10 +1129,6 @@ struct PassSmem {
                                     : KIND == PK_APPLY_L                   ? sizeof(SmemApplyL)
                                                                            : 16;
 };
-
-#ifndef DC_MIN_CTAS
-#define DC_MIN_CTAS 4
-#endif
 
 // Frame sequences, after the last tile of the pass: every image's stream estimate
 // m <- m + lambda (mu_t - m), mu_t the frame's log-mean from its exact log-sum.

@@ -19,6 +19,12 @@ constexpr int kCapMid = 16;
 constexpr int kCapLarge = 256;   // largest batch per launch (kernel parameter space)
 constexpr int kLogFixedShift = 24;  // logsum and fixed-point log unit is 2^-24
 
+// Resident CTAs per SM the pass kernels are compiled for (launch bounds); the host
+// sizes its automatic tiles for that many CTAs per SM.
+#ifndef DC_MIN_CTAS
+#define DC_MIN_CTAS 4
+#endif
+
 // phase kinds
 enum PhaseKind : int32_t {
     PK_DECOLOR = 0,   // L -> out
