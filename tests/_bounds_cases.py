@@ -49,6 +49,27 @@ def run():
                 out["loc_" + tag] = y.cpu().numpy().copy()
                 dc.decolorize_tonemap_local(x, y, block_s=5, radius_blocks=3, bins=7, alpha=0.6)
                 out["loc5_" + tag] = y.cpu().numpy().copy()
+                # comparison channels
+                for luma in ("y", "v"):
+                    dc.decolorize(x, y, luma=luma)
+                    out["dec%s_" % luma + tag] = y.cpu().numpy().copy()
+                    dc.decolorize_tonemap_local(x, y, luma=luma, block_s=8)
+                    out["loc%s_" % luma + tag] = y.cpu().numpy().copy()
+                # colour outputs (3 interleaved samples per pixel, padded rows)
+                y3 = torch.zeros((h, w + pad, 3), dtype=odt, device="cuda")[:, :w, :]
+                for s in (1.0, 0.6):
+                    dc.decolorize_tonemap_global(x, y3, mode="sigmoid", color_s=s)
+                    out["csig%g_" % s + tag] = y3.cpu().numpy().copy()
+                    dc.decolorize_tonemap_local(x, y3, color_s=s, block_s=8, bins=12)
+                    out["cloc%g_" % s + tag] = y3.cpu().numpy().copy()
+                dc.decolorize_tonemap_global(x, y3, mode="histeq")
+                out["che_" + tag] = y3.cpu().numpy().copy()
+                # frame sequences: a restarted frame and a running one
+                vs = dc.VideoStreams(1, lam=0.5)
+                vs(x, y)
+                out["vid0_" + tag] = y.cpu().numpy().copy()
+                vs(x, y)
+                out["vid1_" + tag] = y.cpu().numpy().copy()
     # a ragged batch of every image, each type through the same call
     xs = [to_dev(imgs[k]) for k in keys]
     ys = [torch.zeros(x.shape[:2], dtype=torch.float32, device="cuda") for x in xs]
