@@ -105,3 +105,59 @@ def test_config_8k_local_precision(dc, oracle_mod, storage):
               % (err.max(), err.mean(), e2.max(), e2.mean()))
     else:
         print("8K local f32 storage: vs oracle max %.3g mean %.3g" % (err.max(), err.mean()))
+
+
+@pytest.mark.parametrize("op", ["global", "local"])
+@pytest.mark.parametrize("variant", ["u8", "f32"])
+def test_config_4k_colour(dc, oracle_mod, variant, op):
+    # colour reconstruction of both operators at the bench's 3840x2160 workload, every
+    # sample of the interleaved output against the oracle
+    import torch
+    from paper_2108_13656_gb300 import synth
+    img = synth.s_ldr(3840, 2160, seed=1) if variant == "u8" else synth.s_hdr(3840, 2160, seed=2, decades=5.0, sigma=2.5)
+    odt = torch.uint8 if variant == "u8" else torch.float32
+    x = to_dev(img)
+    y = torch.empty(img.shape[:2] + (3,), dtype=odt, device="cuda")
+    dc.PreparedCall(op, x, y, workspace=dc.Workspace())()
+    torch.cuda.synchronize()
+    ref = oracle_mod.tonemap_global_color(img) if op == "global" else oracle_mod.tonemap_local_color(img)
+    got = y.cpu().numpy()
+    for c in range(3):
+        if variant == "u8":
+            check_u8(got[..., c], ref[..., c], "4K colour %s channel %d" % (op, c))
+        else:
+            check_f32(got[..., c], ref[..., c], what="4K colour %s channel %d" % (op, c))
+
+
+@pytest.mark.parametrize("luma", ["y", "v"])
+def test_config_4k_channels(dc, oracle_mod, luma):
+    import torch
+    from paper_2108_13656_gb300 import synth
+    img = synth.s_hdr(3840, 2160, seed=2, decades=5.0, sigma=2.5)
+    L64 = oracle_mod.decolorize(img, channel={"y": oracle_mod.LUMA_Y, "v": oracle_mod.LUMA_V}[luma])
+    for op in ("global", "local"):
+        y = _run(dc, op, img, torch.float32, luma=luma)
+        ref = (oracle_mod.tonemap_global_plane(L64, ldr=False)[0] if op == "global"
+               else oracle_mod.tonemap_local_plane(L64, ldr=False))
+        check_f32(y, ref, what="4K %s %s" % (luma, op))
+
+
+@pytest.mark.parametrize("variant", ["u8", "f32"])
+def test_config_4k_video(dc, oracle_mod, variant):
+    # three 4K frames of one stream (the scene shifted and brightened frame to frame)
+    # through the one-pass frame-sequence kernel, each against the oracle's sequence
+    import torch
+    from paper_2108_13656_gb300 import synth
+    base = synth.s_ldr(3840, 2160, seed=1) if variant == "u8" else synth.s_hdr(3840, 2160, seed=2, decades=5.0, sigma=2.5)
+    frames = []
+    for t in range(3):
+        f = synth.shifted(base, 7 * t, 11 * t).astype(np.float64) * (1.0 + 0.1 * t)
+        frames.append(np.ascontiguousarray(np.clip(f, 0, 255).astype(np.uint8) if variant == "u8" else f.astype(np.float32)))
+    ys64, ms64 = oracle_mod.tonemap_video_global(frames, lam=0.5)
+    vs = dc.VideoStreams(1, lam=0.5)
+    for t, f in enumerate(frames):
+        y = torch.empty(f.shape[:2], dtype=torch.float32, device="cuda")
+        vs(to_dev(f), y)
+        torch.cuda.synchronize()
+        check_f32(y.cpu().numpy(), ys64[t], what="4K video %s frame %d" % (variant, t))
+        assert abs(vs.states()[0]["m"] - ms64[t]) <= 1e-6 * max(1.0, abs(ms64[t]))
