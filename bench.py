@@ -547,9 +547,11 @@ def serving(dev, n_requests: int, rate: float) -> dict:
     link = host_link_gbps(dev)
     b = serve.serve_batched(trace, pool, budget_bytes=16 << 30, device=dev).summary()
     s = serve.serve_serial(trace, pool, device=dev).summary()
+    u = serve.serve_batched(trace, pool, budget_bytes=16 << 30, device=dev, inflight_cap=None).summary()
     return {"requests": n_requests, "rate_per_s": rate, "budget_gb": 16, "host_link_gbps": link,
             "offered_gpix_s": sum(r.size[0] * r.size[1] for r in trace) / (trace[-1].t_arrive - trace[0].t_arrive) / 1e9,
-            "batched": b, "serial_plain": s,
+            "inflight_cap_gb": serve.INFLIGHT_CAP_BYTES / 2 ** 30,
+            "batched": b, "serial_plain": s, "batched_budget_only": u,
             "note": "latency = host-observed completion (event after the device-to-host copy) minus arrival; "
                     "inputs start in pinned host memory, outputs end there"}
 

@@ -49,11 +49,15 @@ class Admission:
     waiting request can be cancelled; once admitted its work is on the device and it
     completes normally."""
 
-    def __init__(self, budget_bytes: int, reserved_bytes: int = 0, max_batch: int = 64):
+    def __init__(self, budget_bytes: int, reserved_bytes: int = 0, max_batch: int = 64, inflight_cap: int | None = None):
         self.capacity = int(budget_bytes) - int(reserved_bytes)
         if self.capacity <= 0:
             raise ValueError("the budget does not cover the server's own buffers")
         self.max_batch = max_batch
+        # bytes in flight beyond which later arrivals wait on the host (FIFO) instead of
+        # queueing on the device behind the copies already in flight; a request is always
+        # admitted when nothing is in flight
+        self.limit = self.capacity if inflight_cap is None else min(self.capacity, int(inflight_cap))
         self.waiting = collections.deque()  # (request, bytes)
         self.used = 0
         self.peak = 0
@@ -79,7 +83,10 @@ class Admission:
     def admit(self) -> list:
         """Requests that fit now, in arrival order, at most max_batch: [(request, bytes)]."""
         out = []
-        while self.waiting and len(out) < self.max_batch and self.used + self.waiting[0][1] <= self.capacity:
+        while self.waiting and len(out) < self.max_batch:
+            need = self.waiting[0][1]
+            if self.used + need > self.limit and self.used > 0:
+                break
             r, need = self.waiting.popleft()
             self.used += need
             out.append((r, need))
@@ -287,17 +294,22 @@ def _result(trace, lat, queued, batches, peak, outputs, rejected, cancelled) -> 
 WORKSPACE_BYTES = 128 << 20  # per stream, sized up front
 
 
+INFLIGHT_CAP_BYTES = 1 << 30  # about 5 ms of the host link's traffic
+
+
 def serve_batched(trace, pool: HostPool, budget_bytes: int = 16 << 30, n_streams: int = 4, max_batch: int = 64,
-                  keep_outputs: bool = False, device=None) -> ServeResult:
+                  keep_outputs: bool = False, device=None, inflight_cap: int | None = INFLIGHT_CAP_BYTES) -> ServeResult:
     """Continuous batching over the trace (arrival times are honoured in real time).
-    The per-stream workspaces count against the budget."""
+    The per-stream workspaces count against the budget; `inflight_cap` bounds the bytes
+    in flight (None: only the budget)."""
     import torch
     dev = torch.device(device or "cuda")
     streams = [torch.cuda.Stream(device=dev) for _ in range(n_streams)]
     wss = [_abi.Workspace(device=dev) for _ in range(n_streams)]
     for w in wss:
         w.get(WORKSPACE_BYTES)  # sized up front: growing it inside the loop would allocate
-    adm = Admission(budget_bytes, reserved_bytes=sum(w.buf.numel() for w in wss), max_batch=max_batch)
+    adm = Admission(budget_bytes, reserved_bytes=sum(w.buf.numel() for w in wss), max_batch=max_batch,
+                    inflight_cap=inflight_cap)
     outpool, devpool = pool.outpool, pool.devpool
     outputs = {} if keep_outputs else None
 

@@ -119,3 +119,16 @@ def test_admission_counts_reserved_workspaces():
     r = serve.Request(0, 0.0, "global", "u8", (4, 4), 0)
     assert not adm.arrive(r, adm.capacity + 1) and 0 in adm.rejected
     assert adm.arrive(serve.Request(1, 0.0, "global", "u8", (4, 4), 0), adm.capacity)
+
+
+def test_inflight_cap_holds_arrivals_on_the_host():
+    adm = serve.Admission(1000, max_batch=8, inflight_cap=100)
+    rs = [serve.Request(i, 0.0, "global", "u8", (4, 4), 0) for i in range(4)]
+    for r, n in zip(rs, (60, 30, 150, 20)):
+        assert adm.arrive(r, n)
+    assert [r.rid for r, _ in adm.admit()] == [0, 1]   # 90 of 100 in flight; the 150-byte one waits
+    adm.release(90)
+    assert [r.rid for r, _ in adm.admit()] == [2]      # idle: admitted alone although above the cap
+    assert adm.admit() == []                            # FIFO: the 20-byte one waits behind it
+    adm.release(150)
+    assert [r.rid for r, _ in adm.admit()] == [3]
