@@ -84,6 +84,15 @@ def _load():
                                                  ctypes.c_int32, _dp, _dp, ctypes.c_double, _dp]
         lib.oracle_video_mu_update.restype = ctypes.c_double
         lib.oracle_video_mu_update.argtypes = [ctypes.c_double] * 3
+        lib.oracle_local_tables.restype = ctypes.c_int
+        lib.oracle_local_tables.argtypes = [_dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_int32, _dp]
+        lib.oracle_local_apply.restype = ctypes.c_int
+        lib.oracle_local_apply.argtypes = [_dp, _dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_double, _dp]
+        lib.oracle_local_coord.restype = None
+        lib.oracle_local_coord.argtypes = [_dp, ctypes.c_int64, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_double, _dp]
         lib.oracle_tone_local.restype = ctypes.c_int
         lib.oracle_tone_local.argtypes = [_dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -312,3 +321,66 @@ def f16_boundary_mask(y: np.ndarray, eps: float = 1e-5) -> np.ndarray:
     mid_dn = 0.5 * (h + dn)
     tol = eps * np.maximum(1.0, np.abs(y))
     return (np.abs(y - mid_up) < tol) | (np.abs(y - mid_dn) < tol)
+
+
+# ------------------------------------------------------ local frame sequences ----
+def local_coord(L: np.ndarray, ldr: bool, delta: float = 1e-4, lmin: float = 0.0, lmax: float = 0.0) -> np.ndarray:
+    """Coordinate plane u of the local operator (L for 8-bit input, else the log
+    luminance normalised by (lmin, lmax)), clamped to [0, 1]."""
+    Lc = np.ascontiguousarray(L, dtype=np.float64)
+    u = np.empty_like(Lc)
+    _load().oracle_local_coord(_dptr(Lc), Lc.size, 1 if ldr else 0, delta, lmin, lmax, _dptr(u))
+    return u
+
+
+def local_tables(u: np.ndarray, block_s: int = 32, radius_blocks: int = 2, bins: int = 32) -> np.ndarray:
+    """Per-block cumulative tables (Hb, Wb, bins + 1) of the local operator from a coordinate plane."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    H, W = u.shape
+    Hb, Wb = -(-H // block_s), -(-W // block_s)
+    e = np.empty((Hb, Wb, bins + 1), dtype=np.float64)
+    rc = _load().oracle_local_tables(_dptr(u), W, H, block_s, radius_blocks, bins, _dptr(e))
+    if rc != 0:
+        raise ValueError("oracle_local_tables failed (%d)" % rc)
+    return e
+
+
+def local_apply(u: np.ndarray, edge: np.ndarray, block_s: int = 32, bins: int = 32, alpha: float = 1.0) -> np.ndarray:
+    """Bilinear blend of the four nearest block tables at every pixel's own u."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    edge = np.ascontiguousarray(edge, dtype=np.float64)
+    H, W = u.shape
+    y = np.empty_like(u)
+    rc = _load().oracle_local_apply(_dptr(u), _dptr(edge), W, H, block_s, bins, alpha, _dptr(y))
+    if rc != 0:
+        raise ValueError("oracle_local_apply failed (%d)" % rc)
+    return y
+
+
+def tonemap_video_local(frames, block_s: int = 32, radius_blocks: int = 2, bins: int = 32, alpha: float = 1.0,
+                        delta: float = 1e-4, beta_R: float = BETA_R, beta_k: float = BETA_K,
+                        channel: int = LUMA_OURS):
+    """A frame sequence through the local operator with the previous frame's tables:
+    frame 0 is the local operator on its own (its own log range for HDR input);
+    frame t >= 1 takes its coordinates in the previous frame's log range (HDR), is
+    mapped through the previous frame's tables, and then its own tables (from those
+    coordinates) and its own log range are carried to the next frame.  Returns [y_t]."""
+    ys = []
+    edge = None
+    rng = (0.0, 0.0)
+    for img in frames:
+        ldr = img.dtype == np.uint8
+        L = decolorize(img, beta_R, beta_k, channel)
+        own = (0.0, 0.0)
+        if not ldr:
+            _, lo, hi = log_stats(L, delta)
+            own = (lo, hi)
+        if edge is None:
+            rng = own
+        u = local_coord(L, ldr, delta, *rng)
+        if edge is None:
+            edge = local_tables(u, block_s, radius_blocks, bins)
+        ys.append(local_apply(u, edge, block_s, bins, alpha))
+        edge = local_tables(u, block_s, radius_blocks, bins)
+        rng = own
+    return ys

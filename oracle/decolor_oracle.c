@@ -38,6 +38,10 @@
  *  - frame sequences (real-time use, Sec. I; no scheme given): frame t is centred
  *    on the log-mean estimate carried from the frames before it,
  *    m_t = (1 - lambda) m_{t-1} + lambda mu_t, the first frame on its own mu_0.
+ *    For the local operator, frame t is mapped through frame t-1's block tables and,
+ *    for HDR input, takes its coordinates in frame t-1's log range (both one frame
+ *    behind); its own tables, from those coordinates, and its own range go to frame
+ *    t+1.  The first frame is the local operator on its own.
  * Parity of the tone-mapping parameters (k, delta, s, R, bins, alpha) is
  * unpinned by the paper, which prints none of them; the operators are pinned
  * by closed forms and invariants in the tests instead.
@@ -428,4 +432,108 @@ int oracle_color_reconstruct(const void* data, int32_t W, int32_t H, int64_t str
 double oracle_video_mu_update(double m_prev, double mu_frame, double lambda)
 {
     return (1.0 - lambda) * m_prev + lambda * mu_frame;
+}
+
+/*
+ * The two halves of the local operator of Sec. III-B-2 on a coordinate plane u
+ * (already in [0, 1]), for frame sequences: the per-block cumulative tables of the
+ * (2Rb+1)^2-block window of tent-binned block histograms, and the bilinear blend of
+ * the four nearest block tables at each pixel's own u.  oracle_tone_local is the two
+ * in sequence on one image; a frame of a running sequence (Sec. I, III-B-2 real-time
+ * use; no scheme in the paper) applies the previous frame's tables to its own u and
+ * then builds its own tables for the next frame.  `edge` is Hb x Wb x (bins + 1).
+ * Returns 0, 1 on bad arguments, 2 on allocation failure.
+ */
+int oracle_local_tables(const double* u, int32_t W, int32_t H, int32_t s, int32_t Rb, int32_t bins, double* edge)
+{
+    if (W <= 0 || H <= 0 || s <= 0 || Rb < 0 || bins < 1)
+        return 1;
+    int32_t Hb = (H + s - 1) / s, Wb = (W + s - 1) / s;
+    double* h = (double*)calloc((size_t)Hb * Wb * bins, sizeof(double));
+    double* win = (double*)malloc(sizeof(double) * bins);
+    if (!h || !win) {
+        free(h); free(win);
+        return 2;
+    }
+    for (int32_t py = 0; py < H; ++py)
+        for (int32_t px = 0; px < W; ++px) {
+            int j0, j1;
+            double w0, w1;
+            or_tent(u[(int64_t)py * W + px], bins, &j0, &w0, &j1, &w1);
+            double* hb = h + ((size_t)(py / s) * Wb + (px / s)) * bins;
+            hb[j0] += w0;
+            hb[j1] += w1;
+        }
+    for (int32_t I = 0; I < Hb; ++I)
+        for (int32_t J = 0; J < Wb; ++J) {
+            for (int j = 0; j < bins; ++j) win[j] = 0.0;
+            for (int32_t I2 = I - Rb; I2 <= I + Rb; ++I2) {
+                if (I2 < 0 || I2 >= Hb) continue;
+                for (int32_t J2 = J - Rb; J2 <= J + Rb; ++J2) {
+                    if (J2 < 0 || J2 >= Wb) continue;
+                    const double* hb = h + ((size_t)I2 * Wb + J2) * bins;
+                    for (int j = 0; j < bins; ++j) win[j] += hb[j];
+                }
+            }
+            double total = 0.0;
+            for (int j = 0; j < bins; ++j) total += win[j];
+            double* e = edge + ((size_t)I * Wb + J) * (bins + 1);
+            double acc = 0.0;
+            e[0] = 0.0;
+            for (int j = 0; j < bins; ++j) {
+                acc += win[j];
+                e[j + 1] = acc / total;
+            }
+        }
+    free(win);
+    free(h);
+    return 0;
+}
+
+int oracle_local_apply(const double* u, const double* edge, int32_t W, int32_t H, int32_t s, int32_t bins,
+                       double alpha, double* y)
+{
+    if (W <= 0 || H <= 0 || s <= 0 || bins < 1)
+        return 1;
+    int32_t Hb = (H + s - 1) / s, Wb = (W + s - 1) / s;
+    for (int32_t py = 0; py < H; ++py) {
+        double fy = (py + 0.5) / s - 0.5;
+        int32_t I0 = (int32_t)floor(fy);
+        double wy = fy - I0;
+        int32_t I1 = I0 + 1;
+        if (I0 < 0) I0 = 0;
+        if (I1 < 0) I1 = 0;
+        if (I0 > Hb - 1) I0 = Hb - 1;
+        if (I1 > Hb - 1) I1 = Hb - 1;
+        for (int32_t px = 0; px < W; ++px) {
+            double fx = (px + 0.5) / s - 0.5;
+            int32_t J0 = (int32_t)floor(fx);
+            double wx = fx - J0;
+            int32_t J1 = J0 + 1;
+            if (J0 < 0) J0 = 0;
+            if (J1 < 0) J1 = 0;
+            if (J0 > Wb - 1) J0 = Wb - 1;
+            if (J1 > Wb - 1) J1 = Wb - 1;
+            double up = u[(int64_t)py * W + px];
+            double f00 = or_cdf_eval(edge + ((size_t)I0 * Wb + J0) * (bins + 1), bins, up);
+            double f01 = or_cdf_eval(edge + ((size_t)I0 * Wb + J1) * (bins + 1), bins, up);
+            double f10 = or_cdf_eval(edge + ((size_t)I1 * Wb + J0) * (bins + 1), bins, up);
+            double f11 = or_cdf_eval(edge + ((size_t)I1 * Wb + J1) * (bins + 1), bins, up);
+            double F = (1.0 - wy) * ((1.0 - wx) * f00 + wx * f01) + wy * ((1.0 - wx) * f10 + wx * f11);
+            y[(int64_t)py * W + px] = alpha * F + (1.0 - alpha) * up;
+        }
+    }
+    return 0;
+}
+
+/* The coordinate plane of the local operator: u = L clamped to [0, 1] (8-bit input)
+ * or the normalised log luminance in the range (lmin, lmax), clamped (HDR input). */
+void oracle_local_coord(const double* L, int64_t n, int32_t ldr, double delta, double lmin, double lmax, double* u)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        double v = ldr ? L[i] : or_log_u(L[i], delta, lmin, lmax);
+        if (v < 0.0) v = 0.0;
+        if (v > 1.0) v = 1.0;
+        u[i] = v;
+    }
 }

@@ -158,3 +158,50 @@ def test_still_sequence_equals_per_frame_global():
     for y, m in zip(ys, ms):
         np.testing.assert_allclose(y, y_ref, rtol=0, atol=1e-15)
         assert m == pytest.approx(st["mu"], rel=1e-14)
+
+
+# ------------------------------------------------- local frame sequences ----
+@pytest.mark.parametrize("kind", ["u8", "f32"])
+def test_local_still_sequence_equals_per_frame(kind):
+    from paper_2108_13656_gb300 import synth
+    img = synth.s_ldr(70, 45, 3) if kind == "u8" else synth.s_hdr(70, 45, 3)
+    ref = oracle.tonemap_local(img, block_s=16, bins=12)
+    for y in oracle.tonemap_video_local([img] * 3, block_s=16, bins=12):
+        np.testing.assert_array_equal(y, ref)
+
+
+def test_local_sequence_through_a_constant_frame_closed_form():
+    # frame 0 is a constant gray u0 = 100/255: every block histogram has its tent mass
+    # split (1 - f, f) between bins j, j+1 (x0 = B u0 - 1/2 = j + f), so every block's
+    # cumulative table is 0 up to bin j, rises by 1 - f over bin j and by f over bin
+    # j+1; frame 1 (a gray ramp) is mapped through that single curve
+    B, c0 = 8, 100
+    u0 = c0 / 255
+    x0 = B * u0 - 0.5
+    j, f = int(math.floor(x0)), x0 - math.floor(x0)
+    H, W = 24, 64
+    ramp = np.tile(np.arange(W, dtype=np.float64)[None, :] * 4.0, (H, 1)).astype(np.uint8)
+    frame1 = np.repeat(ramp[:, :, None], 3, axis=2)
+    ys = oracle.tonemap_video_local([_gray_frame(c0, H, W), frame1], block_s=8, radius_blocks=1, bins=B)
+    u = ramp.astype(np.float64) / 255
+    x = B * u
+    expect = np.where(x < j, 0.0, np.where(x < j + 1, (1 - f) * (x - j),
+                      np.where(x < j + 2, (1 - f) + f * (x - j - 1), 1.0)))
+    np.testing.assert_allclose(ys[1], expect, rtol=0, atol=1e-12)
+
+
+def test_local_sequence_range_follows_one_frame_behind():
+    # HDR frame 1 = frame 0 with one pixel far brighter: its coordinates are taken in
+    # frame 0's log range and it is mapped through frame 0's tables, so every other
+    # pixel gives exactly frame 0's output and the bright one clamps to u = 1, F = 1;
+    # frame 2 (the same as frame 1) is taken in frame 1's own, wider range
+    from paper_2108_13656_gb300 import synth
+    f0 = synth.s_hdr(48, 32, 5)
+    f1 = f0.copy()
+    f1[7, 9] = f0.max() * 1e3
+    ys = oracle.tonemap_video_local([f0, f1, f1], block_s=8, bins=16)
+    other = np.ones(f0.shape[:2], bool)
+    other[7, 9] = False
+    np.testing.assert_array_equal(ys[1][other], ys[0][other])
+    assert ys[1][7, 9] == 1.0
+    assert np.abs(ys[2][other] - ys[1][other]).max() > 1e-3
