@@ -220,7 +220,8 @@ DC_API int dc_decolorize_tonemap_local(const dc_image_in* in, const dc_image_out
  * restart = 1 starts the streams afresh: each frame is centred on its own log-mean
  * (two passes, the global call's result) and m = mu.  Records must be restarted
  * before their first use.  lambda in (0, 1]; gparams->mode must be DC_SIGMOID.
- * The outputs of a restarted frame equal dc_decolorize_tonemap_global's. */
+ * The outputs of a restarted frame equal dc_decolorize_tonemap_global's.  Outputs
+ * are gray (channels 0 or 1). */
 typedef struct {
     float m;           /* carried log-mean estimate */
     float mu_last;     /* log-mean of the last frame */
@@ -231,6 +232,27 @@ DC_API int dc_decolorize_tonemap_video(const dc_image_in* in, const dc_image_out
                                        const dc_decolor_params* params, const dc_global_params* gparams,
                                        float lambda, int32_t restart, dc_video_state* state, void* ws,
                                        size_t ws_bytes, void* stream);
+
+/* Local tone mapping of frame sequences (the real-time use of Sec. III-B-2 and
+ * Fig. SLHE_TMO(a); the paper names no temporal scheme).  A frame of a running
+ * sequence is mapped through the block tables of the previous frame of its stream
+ * (Sec. III-B-2's operator, dc_local_params) and, for HDR input, takes its
+ * coordinates in the previous frame's log range (clamped): so the frame is read once,
+ * in one pass that also bins it into its own block histograms, and a second, small
+ * pass builds the tables (and records the range) the next frame is mapped through.
+ * A restarted frame (restart = 1, required for a record's first use) is the local
+ * operator on its own (dc_decolorize_tonemap_local's result) and starts the record.
+ * `state` is a caller-owned device buffer of dc_video_local_state_bytes() bytes
+ * (256-byte aligned) holding one record per image of the batch in input order (a
+ * 256-byte header and the image's tables); keep it, the images' sizes and lparams
+ * unchanged between the frames of a sequence.  ws: as for DC_OP_LOCAL.  Outputs are
+ * gray (channels 0 or 1).  Errors: DC_ERR_INVALID_ARG for a NULL, misaligned or
+ * too small state buffer, restart not 0 or 1, or the local call's argument errors. */
+DC_API size_t dc_video_local_state_bytes(const dc_image_in* in, int32_t n, const dc_local_params* lparams);
+DC_API int dc_decolorize_tonemap_local_video(const dc_image_in* in, const dc_image_out* out, int32_t n,
+                                             const dc_decolor_params* params, const dc_local_params* lparams,
+                                             int32_t restart, void* state, size_t state_bytes, void* ws,
+                                             size_t ws_bytes, void* stream);
 
 /* Parameter presets (host only).  DC_PRESET_PAPER: beta_r = 0.55, beta_k = 0.8
  * (Sec. II-B).  Fig. SLHE_TMO(c) shows the paper's luminance controlling the

@@ -24,6 +24,7 @@ from ._abi import (  # noqa: F401
     STATS_BYTES,
     DcError,
     PreparedCall,
+    VideoLocalStreams,
     VideoStreams,
     Workspace,
     debug_bounds,

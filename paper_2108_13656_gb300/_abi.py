@@ -90,6 +90,11 @@ _SIGS = {
                                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t,
                                                    ctypes.c_void_p]),
     "dc_preset": (ctypes.c_int, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p]),
+    "dc_video_local_state_bytes": (ctypes.c_size_t, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "dc_decolorize_tonemap_local_video": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                                         ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                                         ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p,
+                                                         ctypes.c_size_t, ctypes.c_void_p]),
     "dc_workspace_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "dc_workspace_min_bytes": (ctypes.c_size_t, [ctypes.c_int32, ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
     "dc_workspace_prepare": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p]),
@@ -534,3 +539,63 @@ def parse_stats(buf, n: int) -> list[dict]:
         out.append({"mu": float(f[0]), "lmin": float(f[1]), "lmax": float(f[2]), "logsum_fixed": int(q[0]),
                     "npix": int(q[1]), "hist": h})
     return out
+
+
+class VideoLocalStreams:
+    """n video streams through the local operator frame by frame
+    (dc_decolorize_tonemap_local_video): the first call (or one after restart()) is
+    the local operator on each frame alone; later calls map each frame through its
+    stream's previous tables in one pass over the frame and build the next tables.
+    The state buffer (one record per stream) is a device tensor owned here, sized for
+    the frame sizes of the first call; frames must keep those sizes."""
+
+    def __init__(self, n: int, block_s: int = 32, radius_blocks: int = 2, bins: int = 32, alpha: float = 1.0,
+                 delta: float = 1e-4, beta_r: float = BETA_R, beta_k: float = BETA_K, luma="ours", device=None,
+                 workspace=None):
+        self.lib = load()
+        self.n = int(n)
+        self.lp = local_params(block_s, radius_blocks, bins, alpha, delta)
+        self.p = dc_decolor_params(beta_r, beta_k, LUMA.get(luma, luma), 1.0)
+        self.ws = workspace
+        self.device = device
+        self.state = None
+        self._restart = True
+
+    def restart(self):
+        self._restart = True
+
+    def prepare(self, frames, outputs):
+        """The call for these buffers, descriptors and workspace resolved once:
+        `call(restart=None, stream=None)` enqueues one frame per stream."""
+        torch = _torch()
+        frames, outputs = _as_list(frames), _as_list(outputs)
+        if len(frames) != self.n:
+            raise ValueError("expected %d frames (one per stream)" % self.n)
+        ins, outs = _arrays(frames, outputs)
+        need = int(self.lib.dc_video_local_state_bytes(ins, self.n, ctypes.byref(self.lp)))
+        if need == 0:
+            raise DcError(DC_ERR_INVALID_ARG, "dc_video_local_state_bytes")
+        if self.state is None:
+            self.state = torch.zeros(need + 256, dtype=torch.uint8, device=self.device or frames[0].device)
+        off = (-self.state.data_ptr()) % 256
+        if self.state.numel() - off < need:
+            raise ValueError("frame sizes changed: the state was sized for the first frames")
+        st = ctypes.c_void_p(self.state.data_ptr() + off)
+        ptr, size, buf = _workspace(DC_OP_LOCAL, ins, self.n, self.lp, self.ws)
+        wsp = ctypes.c_void_p(ptr)
+
+        def call(restart=None, stream=None):
+            r = self._restart if restart is None else bool(restart)
+            rc = self.lib.dc_decolorize_tonemap_local_video(ins, outs, self.n, ctypes.byref(self.p),
+                                                            ctypes.byref(self.lp), 1 if r else 0, st, need, wsp,
+                                                            size, _stream_handle(stream))
+            if rc != DC_OK:
+                raise DcError(rc, "dc_decolorize_tonemap_local_video")
+            self._restart = False
+            return outputs
+
+        call.keep = (frames, outputs, buf)
+        return call
+
+    def __call__(self, frames, outputs, stream=None):
+        return self.prepare(frames, outputs)(stream=stream)

@@ -112,11 +112,23 @@ struct OpArgs {
     dc_video_state* vstate = nullptr;  // frame sequences (global sigmoid only)
     bool restart = false;              // frame sequences: centre each frame on its own log-mean
     float lambda = 1.0f;
+    uint8_t* lvs = nullptr;            // local frame sequences: the state buffer
+    int64_t lvs_bytes = 0;
+    const std::vector<int64_t>* lvs_off = nullptr;  // per input image: offset of its record
+    bool video() const { return vstate != nullptr || lvs != nullptr; }
 };
+
+// Bytes of an image's local frame-sequence record: a 256-byte header and its block
+// tables (f32, Hb x Wb x (bins + 1)), 256-byte aligned.
+int64_t lvs_record_bytes(const dc_image_in& in, const dc_local_params& l)
+{
+    const int64_t Hb = (in.height + l.block_s - 1) / l.block_s, Wb = (in.width + l.block_s - 1) / l.block_s;
+    return 256 + align_up(Hb * Wb * (l.bins + 1) * 4, 256);
+}
 
 int out_channels(const dc_image_out& o) { return o.channels == 3 ? 3 : 1; }
 
-int validate_image(const dc_image_in& in, const dc_image_out* out, bool local, bool tonemap)
+int validate_image(const dc_image_in& in, const dc_image_out* out, bool local, bool tonemap, bool video)
 {
     if (!dt_ok(in.dtype)) return DC_ERR_UNSUPPORTED_DTYPE;
     if (in.reserved != 0 || in.width < 1 || in.height < 1) return DC_ERR_INVALID_ARG;
@@ -129,7 +141,7 @@ int validate_image(const dc_image_in& in, const dc_image_out* out, bool local, b
         if (!dt_ok(out->dtype)) return DC_ERR_UNSUPPORTED_DTYPE;
         if (out->data == nullptr || (out->channels != 0 && out->channels != 1 && out->channels != 3))
             return DC_ERR_INVALID_ARG;
-        if (out->channels == 3 && !tonemap) return DC_ERR_INVALID_ARG;  // colour needs a tone-mapped y
+        if (out->channels == 3 && (!tonemap || video)) return DC_ERR_INVALID_ARG;  // colour needs a tone-mapped y
         const int oe = esz(out->dtype) * out_channels(*out);
         if (out->stride_bytes < (int64_t)in.width * oe) return DC_ERR_INVALID_ARG;
         if ((reinterpret_cast<uintptr_t>(out->data) % esz(out->dtype)) != 0 || (out->stride_bytes % esz(out->dtype)) != 0)
@@ -142,11 +154,11 @@ int validate_params(const dc_decolor_params* p, const OpArgs& op)
 {
     if (!p || !finite_in(p->beta_r, 0.f, 1.f) || !finite_in(p->beta_k, 0.f, 1.f)) return DC_ERR_INVALID_ARG;
     if (p->luma < DC_LUMA_OURS || p->luma > DC_LUMA_V || !finite_in(p->color_s, 0.f, 8.f)) return DC_ERR_INVALID_ARG;
-    if (op.vstate || op.restart) {
-        if (op.opk != kOpkGlobal || !op.vstate || !finite_in(op.lambda, 0.f, 1.f) || !(op.lambda > 0.f))
-            return DC_ERR_INVALID_ARG;
+    if (op.vstate) {
+        if (op.opk != kOpkGlobal || !finite_in(op.lambda, 0.f, 1.f) || !(op.lambda > 0.f)) return DC_ERR_INVALID_ARG;
         if (op.g && op.g->mode != DC_SIGMOID) return DC_ERR_INVALID_ARG;
     }
+    if (op.lvs && op.opk != kOpkLocal) return DC_ERR_INVALID_ARG;
     if (op.opk == kOpkGlobal) {
         const dc_global_params* g = op.g;
         if (!g || (g->mode != DC_SIGMOID && g->mode != DC_HISTEQ) || g->reserved != 0) return DC_ERR_INVALID_ARG;
@@ -301,6 +313,11 @@ int phase_list(const OpArgs& op, bool ldr, int32_t* kinds)
         return 2;
     }
     int n = 0;
+    if (op.lvs && !op.restart) {  // a frame of a running local sequence: fused pass, then its tables
+        kinds[0] = PK_VIDEO_L;
+        kinds[1] = PK_CDF;
+        return 2;
+    }
     if (!ldr) kinds[n++] = PK_STATS_LOG;
     kinds[n++] = PK_BLOCKH;
     kinds[n++] = PK_CDF;
@@ -383,7 +400,7 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
     bool u8_plane = false;
     // (not for colour outputs, whose apply pass re-reads RGB anyway, nor for a frame of
     // a running sequence, which is a single pass)
-    if (allow_u8_plane && ldr && op.opk != kOpkDecolor && !color && !(op.vstate && !op.restart)) {
+    if (allow_u8_plane && ldr && op.opk != kOpkDecolor && !color && !(op.video() && !op.restart)) {
         int64_t px = 0;
         for (int k = 0; k < n; ++k) px += (int64_t)in[idx[k]].width * in[idx[k]].height;
         u8_plane = px <= kU8PlaneMaxPixels;
@@ -472,6 +489,7 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
             geo[k].im.plane = ws ? ws + off : nullptr;
             off += geo[k].plane_bytes;
         }
+        if (op.lvs && ws) geo[k].im.lvs = op.lvs + (*op.lvs_off)[(size_t)idx[k]];
         b->img[k] = geo[k].im;
         b->stats_index[k] = idx[k];
     }
@@ -506,6 +524,8 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
     }
     b->ws = ws;
     b->ws_bytes = ws_bytes_total;
+    b->lvs_buf = op.lvs;
+    b->lvs_bytes = op.lvs_bytes;
     b->err = reinterpret_cast<uint32_t*>(ws);
     b->ctrl = reinterpret_cast<DcCtrl*>(ws + kHeaderBytes);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -569,7 +589,7 @@ int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_deco
     int rc = validate_params(p, op);
     if (rc != DC_OK) return rc;
     for (int k = 0; k < n; ++k) {
-        rc = validate_image(in[k], query ? nullptr : &out[k], op.opk == kOpkLocal, op.opk != kOpkDecolor);
+        rc = validate_image(in[k], query ? nullptr : &out[k], op.opk == kOpkLocal, op.opk != kOpkDecolor, op.video());
         if (rc != DC_OK) return rc;
     }
     if (!query) {
@@ -723,6 +743,44 @@ DC_API int dc_decolorize_tonemap_video(const dc_image_in* in, const dc_image_out
     op.vstate = state;
     op.restart = restart != 0;
     op.lambda = lambda;
+    return run(in, out, n, params, op, ws, ws_bytes, stream, nullptr);
+}
+
+DC_API size_t dc_video_local_state_bytes(const dc_image_in* in, int32_t n, const dc_local_params* lparams)
+{
+    if (!in || !lparams || n < 1 || n > DC_MAX_BATCH || lparams->block_s < 1 || lparams->block_s > 64 ||
+        lparams->bins < 2 || lparams->bins > DC_MAX_BINS)
+        return 0;
+    int64_t total = 0;
+    for (int k = 0; k < n; ++k) {
+        if (in[k].width < 1 || in[k].height < 1) return 0;
+        total += lvs_record_bytes(in[k], *lparams);
+    }
+    return (size_t)total;
+}
+
+DC_API int dc_decolorize_tonemap_local_video(const dc_image_in* in, const dc_image_out* out, int32_t n,
+                                             const dc_decolor_params* params, const dc_local_params* lparams,
+                                             int32_t restart, void* state, size_t state_bytes, void* ws,
+                                             size_t ws_bytes, void* stream)
+{
+    if (!in || n < 1) return DC_ERR_INVALID_ARG;
+    if (n > DC_MAX_BATCH) return DC_ERR_TOO_MANY;
+    if (!state || (reinterpret_cast<uintptr_t>(state) & 255u) != 0 || (restart != 0 && restart != 1))
+        return DC_ERR_INVALID_ARG;
+    const size_t need = dc_video_local_state_bytes(in, n, lparams);
+    if (need == 0 || state_bytes < need) return DC_ERR_INVALID_ARG;
+    std::vector<int64_t> off((size_t)n);
+    int64_t o = 0;
+    for (int k = 0; k < n; ++k) {
+        off[(size_t)k] = o;
+        o += lvs_record_bytes(in[k], *lparams);
+    }
+    OpArgs op{kOpkLocal, nullptr, lparams, nullptr};
+    op.lvs = static_cast<uint8_t*>(state);
+    op.lvs_bytes = (int64_t)state_bytes;
+    op.lvs_off = &off;
+    op.restart = restart != 0;
     return run(in, out, n, params, op, ws, ws_bytes, stream, nullptr);
 }
 

@@ -107,6 +107,35 @@ __device__ __forceinline__ TileRect tile_rect(const DcBatch<CAP>& P, const DcIma
 }
 
 
+// The coordinate parameters of a fixed-point log range [vmin, vmax] (see Derived).
+__device__ __forceinline__ void derive_range(Derived& d, int vmin, int vmax, bool local, int bins)
+{
+    constexpr float unit = 1.0f / (float)(1 << kLogFixedShift);
+    d.sh = 0;
+    d.Rs = 2u;
+    d.m_loc = d.m_glob = 0ull;
+    d.lmin = (float)vmin * unit;
+    d.lmax = (float)vmax * unit;
+    if (vmax > vmin) {
+        d.vmin = vmin;
+        d.vmax = vmax;
+        uint32_t R = (uint32_t)vmax - (uint32_t)vmin;
+        while (R >= (1u << 30)) {
+            R >>= 1;
+            ++d.sh;
+        }
+        d.Rs = R;
+    } else {
+        d.vmin = vmin - 1;
+        d.vmax = vmin + 1;
+    }
+    static_assert(DC_MAX_BINS <= 32 && 32 + kLocTS + 5 <= 63 && 32 + kGlobTS + 8 <= 63, "reciprocals fit in 64 bits");
+    if (local)
+        d.m_loc = ((unsigned long long)(unsigned)max(bins, 1) << (32 + kLocTS)) / d.Rs;
+    else
+        d.m_glob = (256ull << (32 + kGlobTS)) / d.Rs;
+}
+
 // mu, lmin, lmax from the exact integer accumulators of a finished stats pass
 // (fixed_log: the min and max are of the 2^-24 fixed-point logarithms), and the
 // fixed-point reciprocal of the log range for the operator's histogram: the local
@@ -132,26 +161,7 @@ __device__ __forceinline__ Derived derive(const DcImgCtrl* ic, long long N, bool
     if (fixed_log) {
         const int vmax = (int)(ld_cg_u32(&ic->lmax_ord) ^ 0x80000000u);
         const int vmin = (int)(~ld_cg_u32(&ic->lmin_nord) ^ 0x80000000u);
-        d.lmin = (float)vmin * unit;
-        d.lmax = (float)vmax * unit;
-        if (vmax > vmin) {
-            d.vmin = vmin;
-            d.vmax = vmax;
-            uint32_t R = (uint32_t)vmax - (uint32_t)vmin;
-            while (R >= (1u << 30)) {
-                R >>= 1;
-                ++d.sh;
-            }
-            d.Rs = R;
-        } else {
-            d.vmin = vmin - 1;
-            d.vmax = vmin + 1;
-        }
-        static_assert(DC_MAX_BINS <= 32 && 32 + kLocTS + 5 <= 63 && 32 + kGlobTS + 8 <= 63, "reciprocals fit in 64 bits");
-        if (local)
-            d.m_loc = ((unsigned long long)(unsigned)max(bins, 1) << (32 + kLocTS)) / d.Rs;
-        else
-            d.m_glob = (256ull << (32 + kGlobTS)) / d.Rs;
+        derive_range(d, vmin, vmax, local, bins);
     } else {
         d.lmin = ord_dec(~ld_cg_u32(&ic->lmin_nord));
         d.lmax = ord_dec(ld_cg_u32(&ic->lmax_ord));
@@ -859,13 +869,40 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
 
 // ------------------------------------------------ phase: window sums and CDF --
 // Tile: block row I, block columns [t.c0, t.c1).
+// The block tables of an image: in its local frame-sequence record (after the
+// 256-byte header) when it has one, else in the workspace after its block histograms.
 template <int CAP>
-__device__ void tile_cdf(const DcBatch<CAP>& P, const DcImage& im, int I, const TileRect& t, unsigned char* smem)
+__device__ __forceinline__ float* local_tables(const DcBatch<CAP>& P, const DcImage& im)
+{
+    if (im.lvs) return reinterpret_cast<float*>(im.lvs + sizeof(DcVideoLocalHead));
+    return reinterpret_cast<float*>(P.ws + im.ws_hist + align_up((int64_t)im.Hb * im.Wb * P.bins * 8, 256));
+}
+
+// Bounds check of an access to an image's block tables (bounds-checked build).
+template <int CAP>
+__device__ __forceinline__ bool tables_ok(const DcBatch<CAP>& P, const DcImage& im, const void* p, int64_t bytes)
+{
+    return im.lvs ? bc_ok(p, bytes, P.lvs_buf, P.lvs_bytes, BC_WS) : bc_ok(p, bytes, P.ws, P.ws_bytes, BC_WS);
+}
+
+template <int CAP>
+__device__ void tile_cdf(const DcBatch<CAP>& P, const DcImage& im, const DcImgCtrl* ic, int I, int lt,
+                         const TileRect& t, unsigned char* smem)
 {
     SmemCdf& S = *reinterpret_cast<SmemCdf*>(smem);
     const int B = P.bins, R = P.radius, Hb = im.Hb, Wb = im.Wb;
     const unsigned long long* H = reinterpret_cast<const unsigned long long*>(P.ws + im.ws_hist);
-    float* E = reinterpret_cast<float*>(P.ws + im.ws_hist + align_up((int64_t)Hb * Wb * B * 8, 256));
+    float* E = local_tables(P, im);
+    // a local frame sequence: the record carries this frame's own log range (its
+    // statistics or fused pass accumulated it) and counts the frame
+    if (im.lvs && lt == 0 && threadIdx.x == 0) {
+        DcVideoLocalHead* h = reinterpret_cast<DcVideoLocalHead*>(im.lvs);
+        if (!P.ldr) {
+            h->vmax = (int)(ld_cg_u32(&ic->lmax_ord) ^ 0x80000000u);
+            h->vmin = (int)(~ld_cg_u32(&ic->lmin_nord) ^ 0x80000000u);
+        }
+        h->frames = P.phase_kind[0] == PK_VIDEO_L ? h->frames + 1 : 1;
+    }
     const int i0 = max(0, I - R), i1 = min(Hb - 1, I + R);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int J0 = t.c0;
@@ -911,7 +948,7 @@ __device__ void tile_cdf(const DcBatch<CAP>& P, const DcImage& im, int I, const 
         }
         const unsigned long long total = __shfl_sync(0xffffffffu, w, 31);
         float* e = E + ((size_t)I * Wb + J) * (B + 1);
-        if (!bc_ok(e, (int64_t)(B + 1) * 4, P.ws, P.ws_bytes, BC_WS)) continue;
+        if (!tables_ok(P, im, e, (int64_t)(B + 1) * 4)) continue;
         if (lane < B) e[lane + 1] = __ull2float_rn(w) / __ull2float_rn(total);
         if (lane == 0) e[0] = 0.0f;
     }
@@ -943,7 +980,7 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
     // lands 16 banks away (lanes of a warp read neighbouring blocks' curves at
     // similar bins)
     constexpr int SB = kTabSlot;
-    const float* E = reinterpret_cast<const float*>(P.ws + im.ws_hist + align_up((int64_t)Hb * Wb * B * 8, 256));
+    const float* E = local_tables(P, im);
     {
         static_assert(DC_MAX_BINS <= 32, "one lane per bin");
         // one warp per slot column and lane j per bin, two columns per
@@ -963,7 +1000,7 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
 #pragma unroll
                     for (int sr = 0; sr < 3; ++sr) {
                         const float* e = E + (size_t)(rowoff[sr] + J2) * B1 + j;
-                        const bool ok = sc < W2 && bc_ok(e, 8, P.ws, P.ws_bytes, BC_WS);
+                        const bool ok = sc < W2 && tables_ok(P, im, e, 8);
                         e0[h][sr] = ok ? ld_cg_f(e) : 0.0f;
                         e1[h][sr] = ok ? ld_cg_f(e + 1) : 0.0f;
                     }
@@ -1116,6 +1153,226 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
         by_out(std::false_type{});
 }
 
+// ------------------------------------------------- phase: local frame sequence --
+// Bin coordinate of a fixed-point log value in a carried range, clamped to it (a
+// frame's own values may lie outside the previous frame's range).
+template <int S>
+__device__ __forceinline__ uint32_t bin_coord_clamped(int v, const Derived& d)
+{
+    return bin_coord<S>(min(max(v, d.vmin), d.vmax), d);
+}
+
+// Staging of the tables of block row I and its neighbours (value, slope pairs) and
+// of the tile's bilinear geometry, as the apply pass does it.
+template <int IN_DT, int CAP>
+__device__ __forceinline__ void stage_curves(const DcBatch<CAP>& P, const DcImage& im, const TileRect& t, int I,
+                                             SmemApplyL& S)
+{
+    constexpr int G = InT<IN_DT>::G;
+    constexpr int kColGroups = (kLocMaxCols + 16) / G;
+    constexpr int NW = kThreads / 32;
+    const int s = P.block_s, B = P.bins, Hb = im.Hb, Wb = im.Wb;
+    const int nbx = (t.c1 - t.c0 + s - 1) / s;
+    const int J0 = t.c0 / s;
+    const int W2 = nbx + 2, B1 = B + 1;
+    const float* E = local_tables(P, im);
+    const int j = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int rowoff[3];
+#pragma unroll
+    for (int sr = 0; sr < 3; ++sr) rowoff[sr] = min(max(I - 1 + sr, 0), Hb - 1) * Wb;
+    if (j < B) {
+        for (int sc = w; sc < W2; sc += NW) {
+            const int J2 = min(max(J0 - 1 + sc, 0), Wb - 1);
+#pragma unroll
+            for (int sr = 0; sr < 3; ++sr) {
+                const float* e = E + (size_t)(rowoff[sr] + J2) * B1 + j;
+                const bool ok = tables_ok(P, im, e, 8);
+                const float e0 = ok ? ld_cg_f(e) : 0.0f, e1 = ok ? ld_cg_f(e + 1) : 0.0f;
+                S.tab[sr * kTabRow + sc * kTabSlot + j] = make_float2(e0, e1 - e0);
+            }
+        }
+    }
+    const float inv_s = 1.0f / (float)s;
+    for (int k = threadIdx.x; k < t.c1 - t.c0 + G; k += kThreads) {
+        const float fx = fmaf((float)(min(t.c0 + k, t.c1 - 1)) + 0.5f, inv_s, -0.5f);
+        const float flx = floorf(fx);
+        S.col[(k % G) * kColGroups + k / G] = make_int2(((int)flx - (J0 - 1)) * kTabSlot, __float_as_int(fx - flx));
+    }
+    for (int k = threadIdx.x; k < t.r1 - t.r0; k += kThreads) {
+        const float fy = fmaf((float)(t.r0 + k) + 0.5f, inv_s, -0.5f);
+        const float fly = floorf(fy);
+        S.row[k] = make_int2(((int)fly - (I - 1)) * kTabRow, __float_as_int(fy - fly));
+    }
+}
+
+// One pass per frame of a running local sequence: the tile stages the previous
+// frame's tables of its block row and neighbours, then every pixel (RGB read once)
+// goes into the tent histograms of its block (this frame's tables, built by the next
+// pass) and through the bilinear blend of the staged curves (the output).  HDR
+// coordinates are taken in the carried range, clamped; the frame's own range is
+// accumulated for the next frame.
+template <int IN_DT, int CAP>
+__device__ void tile_video_local(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* ic, const TileRect& t, int I,
+                                 const Beta& be, const Derived& d, unsigned char* smem)
+{
+    constexpr int G = InT<IN_DT>::G;
+    constexpr int kColGroups = (kLocMaxCols + 16) / G;
+    constexpr bool ldr = IN_DT == DC_U8;
+    SmemApplyL& S = *reinterpret_cast<SmemApplyL*>(smem);
+    SmemBlockH& Hs = *reinterpret_cast<SmemBlockH*>(smem + sizeof(SmemApplyL));
+    const int s = P.block_s, B = P.bins;
+    const int nbx = (t.c1 - t.c0 + s - 1) / s;
+    const int BS = blockh_stride(B);
+    stage_curves<IN_DT>(P, im, t, I, S);
+    for (int k = threadIdx.x; k < nbx * BS; k += kThreads) {
+        Hs.cnt[k] = 0u;
+        Hs.fs[k] = 0u;
+    }
+    const float delta = P.delta, Bf = (float)B, alpha = P.alpha, scale = Bf * 1048576.0f;
+    const bool alpha_one = alpha == 1.0f;
+    const int xmax = (B - 1) << 20;
+    const uint32_t magic = P.s_magic;
+    const bool group_in_block = magic != 0u && s % G == 0;
+    const bool precise = ldr && (im.flags & IF_UPRECISE) != 0;
+    int qmin = INT_MAX, qmax = INT_MIN;
+    cta_sync();
+    // PREC: the precise 8-bit coordinate (a literal at each inlined call)
+    auto group_fn = [&](bool PREC, int r, int c, int n, bool vec, float (&Lv)[G], const uint32_t (*wp)[12])
+                        __attribute__((always_inline)) {
+        uint32_t q[G];  // coordinate t = bins u in 2^-24 units (precise 8-bit, HDR)
+        if (PREC) {
+            float qf[G];
+            ucoord_group<IN_DT>(*wp, n, be, B, qf);
+#pragma unroll
+            for (int k = 0; k < G; ++k) q[k] = __float_as_uint(qf[k]);
+        } else if (!ldr) {
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                const int v = ln_q24(Lv[k] + delta);
+                if (k < n) {
+                    qmin = min(qmin, v);
+                    qmax = max(qmax, v);
+                }
+                q[k] = bin_coord_clamped<kLocTS>(v, d);
+            }
+        }
+        // tent histograms (run-length merged shared atomics, as the histogram pass)
+        const int blk0 = group_in_block ? (int)__umulhi((uint32_t)(c - t.c0), magic) : 0;
+        int cur = -1;
+        uint32_t rc = 0u, rf = 0u;
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            if (k < n) {
+                int x;
+                if (ldr && !PREC)
+                    x = min(max(__float2int_rn(fmaf(fminf(fmaxf(Lv[k], 0.0f), 1.0f), scale, -524288.0f)), 0), xmax);
+                else
+                    x = min(max(((int)q[k] - (1 << (kLocTS - 1)) + 8) >> (kLocTS - 20), 0), xmax);
+                int blk = blk0;
+                if (!group_in_block) {
+                    const uint32_t off = (uint32_t)(c + k - t.c0);
+                    blk = magic ? (int)__umulhi(off, magic) : (int)off;
+                }
+                const int key = blk * BS + (x >> 20);
+                const uint32_t f = (uint32_t)x & 0xFFFFFu;
+                if (key == cur) {
+                    ++rc;
+                    rf += f;
+                } else {
+                    if (cur >= 0) {
+                        atomicAdd(&Hs.cnt[cur], rc);
+                        atomicAdd(&Hs.fs[cur], rf);
+                    }
+                    cur = key;
+                    rc = 1u;
+                    rf = f;
+                }
+            }
+        }
+        if (cur >= 0) {
+            atomicAdd(&Hs.cnt[cur], rc);
+            atomicAdd(&Hs.fs[cur], rf);
+        }
+        // the previous frame's curves (bilinear blend, as the apply pass)
+        const int2 ri = S.row[r - t.r0];
+        const float2* rowp = S.tab + ri.x;
+        const float wy = __int_as_float(ri.y);
+        const int2* colp = S.col + (c - t.c0) / G;
+#pragma unroll
+        for (int k = 0; k < G; ++k) {
+            int j;
+            float tt, u;
+            if (ldr && !PREC) {
+                u = fminf(fmaxf(Lv[k], 0.0f), 1.0f);
+                const float Bu = Bf * u;
+                const float jf = fminf(__fadd_rd(Bu, 8388608.0f), 8388608.0f + (float)(B - 1));
+                j = (int)(__float_as_uint(jf) - 0x4B000000u);
+                tt = Bu - (jf - 8388608.0f);
+            } else {
+                const uint32_t jq = min(q[k] >> kLocTS, (uint32_t)(B - 1));
+                j = (int)jq;
+                tt = __uint_as_float(0x3F800000u + ((q[k] - (jq << kLocTS)) >> (kLocTS - 23))) - 1.0f;
+                u = (float)q[k] * (1.0f / (Bf * (float)(1u << kLocTS)));
+            }
+            const int2 ci = colp[k * kColGroups];
+            const float wx = __int_as_float(ci.y);
+            const float2* p = rowp + ci.x + j;
+            const float2 a = p[0], b = p[kTabSlot], cc = p[kTabRow], dd = p[kTabRow + kTabSlot];
+            const float f00 = fmaf(tt, a.y, a.x), f01 = fmaf(tt, b.y, b.x);
+            const float f10 = fmaf(tt, cc.y, cc.x), f11 = fmaf(tt, dd.y, dd.x);
+            const float top = fmaf(wx, f01 - f00, f00);
+            const float bot = fmaf(wx, f11 - f10, f10);
+            const float F = fmaf(wy, bot - top, top);
+            Lv[k] = alpha_one ? F : fmaf(alpha, F - u, u);
+        }
+        GroupIO<IN_DT>::store(im, r, c, n, vec, Lv);
+    };
+    if (precise) {
+        walk_block_patches<IN_DT, false, true>(im, t, s, be,
+                                               [&](int r, int c, int n, bool vec, float (&Lv)[G], const uint32_t (&w)[12])
+                                                   __attribute__((always_inline)) { group_fn(true, r, c, n, vec, Lv, &w); });
+    } else {
+        walk_block_patches<IN_DT, false>(im, t, s, be, [&](int r, int c, int n, bool vec, float (&Lv)[G])
+                                                            __attribute__((always_inline)) {
+                                                                group_fn(false, r, c, n, vec, Lv, nullptr);
+                                                            });
+    }
+    cta_sync();
+    // this frame's block histograms (the next pass builds the tables from them)
+    unsigned long long* H = reinterpret_cast<unsigned long long*>(P.ws + im.ws_hist);
+    const int J0 = t.c0 / s;
+    for (int k = threadIdx.x; k < nbx * B; k += kThreads) {
+        const int blk = k / B, j = k - blk * B;
+        const int e = blk * BS + j;
+        const unsigned long long fprev = j > 0 ? Hs.fs[e - 1] : 0u;
+        const unsigned long long h = ((unsigned long long)Hs.cnt[e] << 20) - Hs.fs[e] + fprev;
+        unsigned long long* qh = &H[((size_t)I * im.Wb + (J0 + blk)) * B + j];
+        if (bc_ok(qh, 8, P.ws, P.ws_bytes, BC_WS)) *qh = h;
+    }
+    // HDR: this frame's own range, for the next frame
+    if constexpr (!ldr) {
+        __shared__ int s_min[kThreads / 32], s_max[kThreads / 32];
+        qmin = __reduce_min_sync(0xffffffffu, qmin);
+        qmax = __reduce_max_sync(0xffffffffu, qmax);
+        if ((threadIdx.x & 31) == 0) {
+            s_min[threadIdx.x >> 5] = qmin;
+            s_max[threadIdx.x >> 5] = qmax;
+        }
+        cta_sync();
+        if (threadIdx.x == 0) {
+            int mn = INT_MAX, mx = INT_MIN;
+            for (int w = 0; w < kThreads / 32; ++w) {
+                mn = min(mn, s_min[w]);
+                mx = max(mx, s_max[w]);
+            }
+            if (mx >= mn) {
+                atomicMax(&ic->lmax_ord, (uint32_t)mx ^ 0x80000000u);
+                atomicMax(&ic->lmin_nord, ~((uint32_t)mn ^ 0x80000000u));
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------ the engine -----
 static_assert(kThreads == 256, "per-bin work uses one consumer thread per histogram bin");
 
@@ -1127,7 +1384,10 @@ struct PassSmem {
                                     : KIND == PK_BLOCKH                    ? sizeof(SmemBlockH)
                                     : KIND == PK_CDF                       ? sizeof(SmemCdf)
                                     : KIND == PK_APPLY_L                   ? sizeof(SmemApplyL)
+                                    : KIND == PK_VIDEO_L                   ? sizeof(SmemApplyL) + sizeof(SmemBlockH)
                                                                            : 16;
+    // above the static limit the pass takes its shared memory dynamically
+    static constexpr bool dynamic = value > 40 * 1024;
 };
 
 // Frame sequences, after the last tile of the pass: every image's stream estimate
@@ -1157,7 +1417,9 @@ __device__ void video_update(const DcBatch<CAP>& P)
 template <int IN_DT, int OPK, int KIND, int CAP, int PL>
 __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __grid_constant__ DcBatch<CAP> P, int ph)
 {
-    __shared__ __align__(16) unsigned char smem[PassSmem<KIND>::value];
+    __shared__ __align__(16) unsigned char smem_static[PassSmem<KIND>::dynamic ? 16 : PassSmem<KIND>::value];
+    extern __shared__ __align__(16) unsigned char smem_dynamic[];
+    unsigned char* const smem = PassSmem<KIND>::dynamic ? smem_dynamic : smem_static;
     __shared__ Derived s_d;
     const Beta be = {P.beta_r, 1.0f - P.beta_r, P.beta_k, 1.0f - P.beta_k, P.luma};
     const int total = P.seg_start[ph][P.n_img];
@@ -1190,6 +1452,17 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
                              OPK == OPK_LOCAL, P.bins);
             cta_sync();
             cached = img;
+        }
+        if constexpr (KIND == PK_VIDEO_L) {
+            if (img != cached) {  // HDR: coordinates in the range the previous frame left in the record
+                if (threadIdx.x == 0 && !P.ldr) {
+                    const DcVideoLocalHead* h = reinterpret_cast<const DcVideoLocalHead*>(im.lvs);
+                    derive_range(s_d, ld_cg_u32(reinterpret_cast<const uint32_t*>(&h->vmin)),
+                                 ld_cg_u32(reinterpret_cast<const uint32_t*>(&h->vmax)), true, P.bins);
+                }
+                cta_sync();
+                cached = img;
+            }
         }
         if constexpr (KIND == PK_VIDEO) {
             if (img != cached) {  // the stream's carried estimate (updated only after the pass)
@@ -1230,9 +1503,11 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
         } else if constexpr (KIND == PK_BLOCKH) {
             tile_blockh<IN_DT, PL == 1>(P, im, tr, I, be, s_d, smem);
         } else if constexpr (KIND == PK_CDF) {
-            tile_cdf(P, im, I, tr, smem);
+            tile_cdf(P, im, ic, I, lt, tr, smem);
         } else if constexpr (KIND == PK_VIDEO) {
             tile_video<IN_DT>(P, im, ic, tr, be, s_d, smem);
+        } else if constexpr (KIND == PK_VIDEO_L) {
+            tile_video_local<IN_DT>(P, im, ic, tr, I, be, s_d, smem);
         } else {
             tile_apply_local<IN_DT, PL>(P, im, tr, I, be, s_d, smem);
         }
@@ -1278,6 +1553,13 @@ int launch_one(const void* batch, int ph, LaunchShape ls, void* stream)
     cfg.gridDim = dim3((unsigned)ls.grid);
     cfg.blockDim = dim3(kThreads);
     cfg.dynamicSmemBytes = 0;
+    if constexpr (PassSmem<KIND>::dynamic) {
+        // (once per kernel: allow its dynamic shared memory)
+        static const cudaError_t attr_rc = cudaFuncSetAttribute(
+            pass_kernel<IN_DT, OPK, KIND, CAP, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassSmem<KIND>::value);
+        if (attr_rc != cudaSuccess) return DC_ERR_CUDA;
+        cfg.dynamicSmemBytes = PassSmem<KIND>::value;
+    }
     cfg.stream = (cudaStream_t)stream;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -1292,8 +1574,13 @@ template <int IN_DT, int OPK, int KIND, int CAP, int PL>
 int occupancy_one()
 {
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<IN_DT, OPK, KIND, CAP, PL>, kThreads, 0) !=
-        cudaSuccess)
+    if constexpr (PassSmem<KIND>::dynamic) {
+        static const cudaError_t attr_rc = cudaFuncSetAttribute(
+            pass_kernel<IN_DT, OPK, KIND, CAP, PL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PassSmem<KIND>::value);
+        if (attr_rc != cudaSuccess) return 0;
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pass_kernel<IN_DT, OPK, KIND, CAP, PL>, kThreads,
+                                                      PassSmem<KIND>::dynamic ? PassSmem<KIND>::value : 0) != cudaSuccess)
         return 0;
     return nb;
 }
@@ -1309,7 +1596,7 @@ int occupancy_one()
         X(OPK_GLOBAL, PK_APPLY_G, 2) X(OPK_GLOBAL, PK_VIDEO, 0) X(OPK_LOCAL, PK_STATS_LOG, 0)         \
         X(OPK_LOCAL, PK_STATS_LOG, 1) X(OPK_LOCAL, PK_BLOCKH, 0) X(OPK_LOCAL, PK_BLOCKH, 1)           \
         X(OPK_LOCAL, PK_CDF, 0) X(OPK_LOCAL, PK_APPLY_L, 0) X(OPK_LOCAL, PK_APPLY_L, 1)               \
-        X(OPK_LOCAL, PK_APPLY_L, 2)
+        X(OPK_LOCAL, PK_APPLY_L, 2) X(OPK_LOCAL, PK_VIDEO_L, 0)
 
 template <int IN_DT>
 int launch_dispatch(const void* batch, int cap, int opk, int kind, int ph, int pl, LaunchShape ls, void* stream)

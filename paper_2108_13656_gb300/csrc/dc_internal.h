@@ -36,7 +36,18 @@ enum PhaseKind : int32_t {
     PK_APPLY_L = 6,   // local: bilinear blend of block curves -> out
     PK_STATS_LOG = 7, // HDR histogram forms: exact fixed-point log statistics (+ plane)
     PK_VIDEO = 8,     // frame sequences: sigmoid around the carried log-mean + this frame's log-sum
+    PK_VIDEO_L = 9,   // local frame sequences: block histograms of the frame and its mapping
+                      // through the previous frame's tables, in one pass
 };
+
+// Per-image record of a local frame sequence (caller-owned state buffer): this header,
+// then the block tables (f32, Hb x Wb x (bins + 1)) the next frame is mapped through.
+struct DcVideoLocalHead {
+    int32_t vmin, vmax;   // the last frame's range of round(ln(L + delta) 2^24) (HDR input)
+    int64_t frames;       // frames since the restart
+    uint32_t pad[60];
+};
+static_assert(sizeof(DcVideoLocalHead) == 256, "state header is 256 bytes");
 
 // per-image flags
 enum : uint32_t {
@@ -48,7 +59,7 @@ enum : uint32_t {
                         // luminance (f32 outputs); a plane, if kept, holds that coordinate as int32 bits
 };
 
-struct DcImage {                 // 96 bytes
+struct DcImage {                 // 104 bytes
     const uint8_t* in;
     uint8_t* out;
     int64_t in_stride;           // bytes between (logical) rows
@@ -63,6 +74,7 @@ struct DcImage {                 // 96 bytes
     int32_t tiles_x_loc;         // tiles per block row, local phases
     int32_t Hb, Wb;              // local: blocks
     int64_t ws_hist;             // byte offsets into the workspace (local)
+    uint8_t* lvs;                // local frame sequences: the image's state record, or NULL
 };
 
 // Per-image control block, cleared (memset) before the first pass of a call.  The
@@ -144,6 +156,8 @@ struct DcBatch {
     dc_global_stats* stats;            // nullable; indexed by img_stats_index
     uint8_t* ws;
     int64_t ws_bytes;                  // workspace size (bounds-checked build)
+    uint8_t* lvs_buf;                  // local frame sequences: the caller's state buffer
+    int64_t lvs_bytes;                 // ... and its size (bounds-checked build)
     int32_t stats_index[CAP];
     DcImage img[CAP];
     int32_t reverse[kMaxPhases];         // hand a pass's tiles out last-first (L2 reuse)

@@ -70,6 +70,11 @@ def run():
                 out["vid0_" + tag] = y.cpu().numpy().copy()
                 vs(x, y)
                 out["vid1_" + tag] = y.cpu().numpy().copy()
+                lv = dc.VideoLocalStreams(1, block_s=8, bins=12)
+                lv(x, y)
+                out["lvid0_" + tag] = y.cpu().numpy().copy()
+                lv(x, y)
+                out["lvid1_" + tag] = y.cpu().numpy().copy()
     # a ragged batch of every image, each type through the same call
     xs = [to_dev(imgs[k]) for k in keys]
     ys = [torch.zeros(x.shape[:2], dtype=torch.float32, device="cuda") for x in xs]

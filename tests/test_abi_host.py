@@ -282,3 +282,31 @@ def test_presets(abi):
         assert (lp.block_s, lp.radius_blocks, lp.bins, lp.alpha) == (32, 2, 32, 1.0)
     assert lib.dc_preset(3, ctypes.byref(p), None) == abi.DC_ERR_INVALID_ARG
     assert lib.dc_preset(abi.DC_PRESET_TM1, None, None) == 0
+
+
+def test_local_video_arguments_validated(abi):
+    lib = abi.load()
+    ins = (abi.dc_image_in * 1)(_img(100, 70))
+    out = (abi.dc_image_out * 1)(abi.dc_image_out(1 << 24, 400, 2, 0))
+    lp = abi.dc_local_params(32, 2, 32, 1.0, 1e-4, 0)
+    # a 256-byte header and 3 x 4 blocks x 33 tables of 4 bytes, 256-aligned
+    assert lib.dc_video_local_state_bytes(ins, 1, ctypes.byref(lp)) == 256 + ((3 * 4 * 33 * 4 + 255) // 256) * 256
+    assert lib.dc_video_local_state_bytes(ins, 1, None) == 0
+    p = abi.dc_decolor_params(0.55, 0.8, 0, 1.0)
+    ws = ctypes.c_void_p(1 << 12)
+    st = 1 << 26
+    need = lib.dc_video_local_state_bytes(ins, 1, ctypes.byref(lp))
+    call = lib.dc_decolorize_tonemap_local_video
+    assert call(ins, out, 1, ctypes.byref(p), ctypes.byref(lp), 0, None, need, ws, 1 << 20, None) == abi.DC_ERR_INVALID_ARG
+    assert call(ins, out, 1, ctypes.byref(p), ctypes.byref(lp), 0, ctypes.c_void_p(st + 16), need, ws, 1 << 20,
+                None) == abi.DC_ERR_INVALID_ARG   # misaligned state
+    assert call(ins, out, 1, ctypes.byref(p), ctypes.byref(lp), 0, ctypes.c_void_p(st), need - 1, ws, 1 << 20,
+                None) == abi.DC_ERR_INVALID_ARG   # too small
+    assert call(ins, out, 1, ctypes.byref(p), ctypes.byref(lp), 3, ctypes.c_void_p(st), need, ws, 1 << 20,
+                None) == abi.DC_ERR_INVALID_ARG   # restart not 0 / 1
+    col = (abi.dc_image_out * 1)(abi.dc_image_out(1 << 24, 1200, 2, 3))
+    assert call(ins, col, 1, ctypes.byref(p), ctypes.byref(lp), 1, ctypes.c_void_p(st), need, ws, 1 << 20,
+                None) == abi.DC_ERR_INVALID_ARG   # frame sequences give gray outputs
+    g = abi.dc_global_params(0, 1.0, 1e-4, 0)
+    assert lib.dc_decolorize_tonemap_video(ins, col, 1, ctypes.byref(p), ctypes.byref(g), 1.0, 1,
+                                           ctypes.c_void_p(st), ws, 1 << 20, None) == abi.DC_ERR_INVALID_ARG

@@ -265,3 +265,58 @@ def test_presets_boost_and_suppress_the_background(dc):
         L = y.cpu().numpy()
         res[name] = L[~fg].mean() - L[fg].mean()
     assert res["tm1"] > res["tm2"]
+
+
+# ------------------------------------------------- local frame sequences ----
+@pytest.mark.parametrize("kind,odt", [("u8", "u8"), ("u8", "f32"), ("f16", "f32"), ("f32", "f32"), ("f32", "u8")])
+def test_local_video_sequence(dc, oracle_mod, kind, odt):
+    import torch
+    frames = _frames(kind, 4, 330, 190)
+    kw = dict(block_s=16, radius_blocks=2, bins=24)
+    ys64 = oracle_mod.tonemap_video_local(frames, **kw)
+    vs = dc.VideoLocalStreams(1, **kw)
+    for t, f in enumerate(frames):
+        y = _empty(f.shape[:2], odt)
+        vs(to_dev(f), y)
+        assert dc.last_launch_count() == ((3 if kind == "u8" else 4) if t == 0 else 2)
+        torch.cuda.synchronize()
+        check_out(y.cpu().numpy(), ys64[t], odt, what="local video %s -> %s frame %d" % (kind, odt, t))
+
+
+def test_local_video_restart_equals_local_call_and_batches(dc, oracle_mod):
+    import torch
+    seqs = [_frames("u8", 3, 256, 120), _frames("f32", 3, 200, 96)]
+    kw = dict(block_s=8, radius_blocks=1, bins=16, alpha=0.7)
+    refs = [oracle_mod.tonemap_video_local(sq, **kw) for sq in seqs]
+    vs = dc.VideoLocalStreams(2, **kw)
+    for t in range(3):
+        outs = [_empty(seqs[0][t].shape[:2], "u8"), _empty(seqs[1][t].shape[:2], "f32")]
+        vs([to_dev(seqs[0][t]), to_dev(seqs[1][t])], outs)
+        torch.cuda.synchronize()
+        check_out(outs[0].cpu().numpy(), refs[0][t], "u8", what="stream 0 frame %d" % t)
+        check_out(outs[1].cpu().numpy(), refs[1][t], "f32", what="stream 1 frame %d" % t)
+    vs.restart()
+    f = seqs[1][2]
+    a, b = _empty(f.shape[:2], "f32"), _empty(f.shape[:2], "f32")
+    vs([to_dev(seqs[0][2]), to_dev(f)], [_empty(seqs[0][2].shape[:2], "u8"), a])
+    dc.decolorize_tonemap_local(to_dev(f), b, **kw)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("H,W,pad,off", [(1, 1, 0, 0), (7, 33, 1, 1), (70, 17, 0, 5)])
+def test_local_video_odd_layouts(dc, oracle_mod, H, W, pad, off):
+    import torch
+    kw = dict(block_s=5, radius_blocks=3, bins=7)
+    for kind in ("u8", "f32"):
+        base = _img(kind, max(W, 4), max(H, 4), H + W)[:H, :W]
+        frames = [base.copy(), base[:, ::-1].copy()]
+        ys64 = oracle_mod.tonemap_video_local(frames, **kw)
+        vs = dc.VideoLocalStreams(1, **kw)
+        for t, f in enumerate(frames):
+            x = to_dev(f, pad_px=pad, offset_elems=off)
+            buf = _empty((off + H * (W + pad) + 64,), "f32")
+            y = buf[off:off + H * (W + pad)].view(H, W + pad)[:, :W]
+            vs(x, y)
+            torch.cuda.synchronize()
+            check_f32(y.cpu().numpy(), ys64[t], what="local video odd %dx%d %s frame %d" % (H, W, kind, t))
