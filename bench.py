@@ -429,19 +429,25 @@ def _alone_ms(calls, flush, reps: int) -> list:
 
 # ------------------------------------------------------------ frame sequences ----
 def video_4k(dev, peak: float) -> dict:
-    """Frame sequences at 3840x2160: a frame of a running stream is ONE pass (Eq. 1-6,
-    the sigmoid around the carried log-mean, and the frame's own log-sum).  Each
-    variant alone after an L2-flushing write, and frames back to back: 8 frames on
-    rotating buffers captured in one CUDA graph and replayed (inputs far above L2)."""
+    """Frame sequences at 3840x2160: a frame of a running stream is ONE pass for the
+    global curve (Eq. 1-6, the sigmoid around the carried log-mean, and the frame's own
+    log-sum) and two for the local operator (the fused block-histogram and mapping
+    pass, then the table pass).  Each variant alone after an L2-flushing write, and
+    frames back to back: 8 frames on rotating buffers captured in one CUDA graph and
+    replayed (inputs far above L2)."""
     import torch
     import paper_2108_13656_gb300 as dc
     imgs = make_inputs()
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     out = {}
-    for var, odt, bpp in (("u8", torch.uint8, 4), ("f32", torch.float32, 16)):
+    for var, op, odt, bpp in (("u8", "global", torch.uint8, 4), ("f32", "global", torch.float32, 16),
+                              ("u8", "local", torch.uint8, 4), ("f32", "local", torch.float32, 16)):
         xs = [torch.from_numpy(imgs[var]).to(dev) for _ in range(ROT)]
         ys = [torch.empty((H, W), dtype=odt, device=dev) for _ in range(ROT)]
-        vs = dc.VideoStreams(1, lam=0.5, device=dev, workspace=dc.Workspace(device=dev))
+        if op == "global":
+            vs = dc.VideoStreams(1, lam=0.5, device=dev, workspace=dc.Workspace(device=dev))
+        else:
+            vs = dc.VideoLocalStreams(1, device=dev, workspace=dc.Workspace(device=dev))
         calls = [vs.prepare(xs[r], ys[r]) for r in range(ROT)]
         calls[0](restart=True)
         for r in range(ROT):
@@ -468,7 +474,7 @@ def video_4k(dev, peak: float) -> dict:
         e1.record(main)
         torch.cuda.synchronize()
         ms_b2b = e0.elapsed_time(e1) / (reps * ROT)
-        out[var] = {"launches_per_frame": launches, "bytes_per_px": bpp,
+        out[var if op == "global" else var + "_local"] = {"launches_per_frame": launches, "bytes_per_px": bpp,
                     "alone_us": ms_alone * 1e3, "alone_GBps": bpp * NPIX / ms_alone / 1e6,
                     "alone_frac_of_measured_hbm": bpp * NPIX / ms_alone / 1e6 / peak,
                     "back_to_back_us": ms_b2b * 1e3, "back_to_back_gpix_s": NPIX / ms_b2b / 1e6,
