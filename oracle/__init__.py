@@ -29,7 +29,7 @@ _lock = threading.Lock()
 _lib = None
 
 DT_U8, DT_F16, DT_F32 = 0, 1, 2
-LUMA_OURS, LUMA_Y, LUMA_V = 0, 1, 2  # Eq. 1-6; rgb2gray Y of Sec. I; V of HSV (Fig. GTMO)
+LUMA_OURS, LUMA_Y, LUMA_V, LUMA_LSTAR = 0, 1, 2, 3  # Eq. 1-6; rgb2gray Y of Sec. I; V of HSV (Fig. GTMO); CIE L*/100
 BETA_R, BETA_K = 0.55, 0.8  # Sec. II-B: "(beta_R = 0.55; beta_k = 0.8)"
 MODE_SIGMOID, MODE_HISTEQ = 0, 1
 

@@ -32,7 +32,9 @@
  *    four nearest nominal block centres ((I+1/2)s, (J+1/2)s), clamped at the
  *    border.  Output alpha*F + (1-alpha)*u.
  *  - comparison channels (Sec. I, Fig. GTMO): MATLAB's rgb2gray weights as the
- *    paper quotes them, and V of HSV = max(R, G, B), on the same decoded samples.
+ *    paper quotes them, and V of HSV = max(R, G, B), on the same decoded samples;
+ *    CIE L* / 100 from Rec. 709 relative luminance (D65 white), 8-bit codes decoded
+ *    with the sRGB transfer function first (CIELAB is defined on linear light).
  *  - colour reconstruction (colour outputs of Fig. tmo_1 and Fig. GTMO, no formula):
  *    C_out = min(1, y (C_in / L)^s), a black pixel taken as achromatic.
  *  - frame sequences (real-time use, Sec. I; no scheme given): frame t is centred
@@ -343,13 +345,34 @@ int oracle_tone_local(const double* L, int32_t W, int32_t H, int32_t ldr, int32_
  *   luma 0: the colour-temperature luminance of Eq. 1-6;
  *   luma 1: MATLAB's rgb2gray weighted sum quoted in Sec. I,
  *           Gray = 0.2989 R + 0.5870 G + 0.1140 B;
- *   luma 2: V of HSV, the largest channel.
+ *   luma 2: V of HSV, the largest channel;
+ *   luma 3: CIE L* of CIELAB / 100 (Sec. I, Fig. 2, Table 1), of linear samples
+ *           (oracle_decolorize_luma decodes 8-bit sRGB codes to linear first).
  * Returns NAN for an unknown luma code.
  */
+/* CIE 1976 lightness of linear RGB (Rec. 709 / sRGB primaries, D65 white, Yn = 1),
+ * divided by 100: L* = 116 f(Y) - 16, f(t) = cbrt(t) above (6/29)^3, else
+ * t / (3 (6/29)^2) + 4/29, with Y = 0.2126 R + 0.7152 G + 0.0722 B. */
+static double or_lstar(double R, double G, double B)
+{
+    double Y = 0.2126 * R + 0.7152 * G + 0.0722 * B;
+    double d = 6.0 / 29.0;
+    double f = Y > d * d * d ? cbrt(Y) : Y / (3.0 * d * d) + 4.0 / 29.0;
+    return (116.0 * f - 16.0) / 100.0;
+}
+
+/* sRGB-encoded value in [0, 1] to linear light (the sRGB transfer function). */
+static double or_srgb_linear(double c)
+{
+    return c <= 0.04045 ? c / 12.92 : pow((c + 0.055) / 1.055, 2.4);
+}
+
 double oracle_luma(double R, double G, double B, int32_t luma, double beta_R, double beta_k)
 {
     if (luma == 0)
         return oracle_luminance(R, G, B, beta_R, beta_k);
+    if (luma == 3)
+        return or_lstar(R, G, B);  /* linear samples */
     if (luma == 1)
         return 0.2989 * R + 0.5870 * G + 0.1140 * B;
     if (luma == 2) {
@@ -365,7 +388,7 @@ double oracle_luma(double R, double G, double B, int32_t luma, double beta_R, do
 int oracle_decolorize_luma(const void* data, int32_t W, int32_t H, int64_t stride_bytes, int32_t dtype,
                            int32_t luma, double beta_R, double beta_k, double* L)
 {
-    if (W < 0 || H < 0 || dtype < OR_U8 || dtype > OR_F32 || luma < 0 || luma > 2)
+    if (W < 0 || H < 0 || dtype < OR_U8 || dtype > OR_F32 || luma < 0 || luma > 3)
         return 1;
     int esz = dtype == OR_U8 ? 1 : (dtype == OR_F16 ? 2 : 4);
     const unsigned char* base = (const unsigned char*)data;
@@ -376,6 +399,11 @@ int oracle_decolorize_luma(const void* data, int32_t W, int32_t H, int64_t strid
             double R = or_sample(px, dtype, 0);
             double G = or_sample(px, dtype, 1);
             double B = or_sample(px, dtype, 2);
+            if (luma == 3 && dtype == OR_U8) {  /* CIELAB is defined on linear light */
+                R = or_srgb_linear(R);
+                G = or_srgb_linear(G);
+                B = or_srgb_linear(B);
+            }
             L[(int64_t)y * W + x] = oracle_luma(R, G, B, luma, beta_R, beta_k);
         }
     }

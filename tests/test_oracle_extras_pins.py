@@ -60,7 +60,7 @@ def test_decolorize_channel_on_an_image():
 
 def test_unknown_channel_rejected():
     with pytest.raises(ValueError):
-        oracle.decolorize(np.zeros((2, 2, 3), np.uint8), channel=3)
+        oracle.decolorize(np.zeros((2, 2, 3), np.uint8), channel=4)
     assert math.isnan(oracle.luma(1, 0, 0, 7))
 
 
@@ -205,3 +205,35 @@ def test_local_sequence_range_follows_one_frame_behind():
     np.testing.assert_array_equal(ys[1][other], ys[0][other])
     assert ys[1][7, 9] == 1.0
     assert np.abs(ys[2][other] - ys[1][other]).max() > 1e-3
+
+
+# ------------------------------------------------------------ CIE L* ----
+D = 6.0 / 29.0
+
+
+@pytest.mark.parametrize("Y,lstar", [
+    (1.0, 1.0),                       # reference white: L* = 100
+    (0.0, 0.0),
+    ((66.0 / 116.0) ** 3, 0.5),       # f(Y) = 66/116 on the cube-root branch: L* = 50
+    (D ** 3, 0.08),                   # the branch point: f = 6/29 on both sides, L* = 8
+    (D ** 3 / 2, 0.04),               # linear branch: f = 1/29 + 4/29 = 5/29, L* = 4
+])
+def test_lstar_closed_forms(Y, lstar):
+    # achromatic linear samples: Rec. 709 luminance Y equals the sample (weights sum to 1)
+    assert oracle.luma(Y, Y, Y, oracle.LUMA_LSTAR) == pytest.approx(lstar, abs=1e-12)
+
+
+def test_lstar_of_srgb_red():
+    # Y = 0.2126 for linear red: L* = 116 cbrt(0.2126) - 16
+    assert oracle.luma(1, 0, 0, oracle.LUMA_LSTAR) == pytest.approx((116 * 0.2126 ** (1 / 3) - 16) / 100, abs=1e-14)
+
+
+def test_lstar_decodes_8bit_srgb():
+    img = np.array([[[255, 255, 255], [0, 0, 0], [10, 10, 10], [200, 200, 200]]], dtype=np.uint8)
+    L = oracle.decolorize(img, channel=oracle.LUMA_LSTAR)[0]
+    assert L[0] == pytest.approx(1.0, abs=1e-15) and L[1] == 0.0
+    c = 10 / 255  # on the linear segment of the sRGB curve (c <= 0.04045): Y = c / 12.92 < (6/29)^3
+    Y = c / 12.92
+    assert L[2] == pytest.approx(116 * (Y / (3 * D * D)) / 100, rel=1e-12)
+    Y = ((200 / 255 + 0.055) / 1.055) ** 2.4
+    assert L[3] == pytest.approx((116 * Y ** (1 / 3) - 16) / 100, rel=1e-12)
