@@ -109,6 +109,11 @@ typedef struct {
 #define DC_LUMA_OURS 0 /* Eq. 1-6 (Sec. II-B) */
 #define DC_LUMA_Y 1    /* Gray = 0.2989 R + 0.5870 G + 0.1140 B (MATLAB rgb2gray, quoted in Sec. I) */
 #define DC_LUMA_V 2    /* V of HSV = max(R, G, B) */
+#define DC_LUMA_LSTAR 3 /* CIE L* of CIELAB / 100 (Sec. I, Fig. 2, Table 1): 116 f(Y) - 16 of the
+                          Rec. 709 / sRGB luminance Y (D65 white), 8-bit codes decoded with
+                          the sRGB transfer function first; not offered for 8-bit input with
+                          an f32 output through the local operator (DC_ERR_UNSUPPORTED_DTYPE:
+                          its binary32 cube root is too coarse for that output's tolerance) */
 
 /* Eq. 3 and Eq. 6 weights; the paper uses beta_r = 0.55 and beta_k = 0.8
  * (Sec. II-B).  The paper states 0.5 < beta < 1; the library accepts [0, 1].

@@ -20,10 +20,10 @@ DC_ERR_CUDA, DC_ERR_TIMEOUT, DC_ERR_TOO_MANY = 4, 5, 6
 DC_U8, DC_F16, DC_F32 = 0, 1, 2
 DC_OP_DECOLORIZE, DC_OP_GLOBAL, DC_OP_LOCAL = 0, 1, 2
 DC_SIGMOID, DC_HISTEQ = 0, 1
-DC_LUMA_OURS, DC_LUMA_Y, DC_LUMA_V = 0, 1, 2
+DC_LUMA_OURS, DC_LUMA_Y, DC_LUMA_V, DC_LUMA_LSTAR = 0, 1, 2, 3
 DC_PRESET_PAPER, DC_PRESET_TM1, DC_PRESET_TM2 = 0, 1, 2
 BETA_R, BETA_K = 0.55, 0.8
-LUMA = {"ours": DC_LUMA_OURS, "y": DC_LUMA_Y, "v": DC_LUMA_V}
+LUMA = {"ours": DC_LUMA_OURS, "y": DC_LUMA_Y, "v": DC_LUMA_V, "lstar": DC_LUMA_LSTAR}
 VIDEO_STATE_BYTES = 16  # sizeof(dc_video_state)
 
 

@@ -153,7 +153,7 @@ int validate_image(const dc_image_in& in, const dc_image_out* out, bool local, b
 int validate_params(const dc_decolor_params* p, const OpArgs& op)
 {
     if (!p || !finite_in(p->beta_r, 0.f, 1.f) || !finite_in(p->beta_k, 0.f, 1.f)) return DC_ERR_INVALID_ARG;
-    if (p->luma < DC_LUMA_OURS || p->luma > DC_LUMA_V || !finite_in(p->color_s, 0.f, 8.f)) return DC_ERR_INVALID_ARG;
+    if (p->luma < DC_LUMA_OURS || p->luma > DC_LUMA_LSTAR || !finite_in(p->color_s, 0.f, 8.f)) return DC_ERR_INVALID_ARG;
     if (op.vstate) {
         if (op.opk != kOpkGlobal || !finite_in(op.lambda, 0.f, 1.f) || !(op.lambda > 0.f)) return DC_ERR_INVALID_ARG;
         if (op.g && op.g->mode != DC_SIGMOID) return DC_ERR_INVALID_ARG;
@@ -591,6 +591,10 @@ int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_deco
     for (int k = 0; k < n; ++k) {
         rc = validate_image(in[k], query ? nullptr : &out[k], op.opk == kOpkLocal, op.opk != kOpkDecolor, op.video());
         if (rc != DC_OK) return rc;
+    }
+    if (!query && p->luma == DC_LUMA_LSTAR && op.opk == kOpkLocal) {
+        for (int k = 0; k < n; ++k)
+            if (in[k].dtype == DC_U8 && out[k].dtype == DC_F32) return DC_ERR_UNSUPPORTED_DTYPE;
     }
     if (!query) {
         // input must not overlap output

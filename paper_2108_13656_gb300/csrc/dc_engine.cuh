@@ -175,10 +175,25 @@ struct Beta {
     int luma;  // DC_LUMA_OURS (Eq. 1-6), DC_LUMA_Y or DC_LUMA_V
 };
 
+// CIE 1976 lightness / 100 of linear samples (Rec. 709 luminance, D65 white, Yn = 1):
+// 116 f(Y) - 16 with f the cube root above (6/29)^3 and the linear segment below.
+__device__ __forceinline__ float lstar_linear(float R, float G, float B)
+{
+    const float Y = fmaf(0.0722f, B, fmaf(0.7152f, G, 0.2126f * R));
+    const float f = Y > 0.008856451679f ? cbrtf(Y) : fmaf(Y, 841.0f / 108.0f, 4.0f / 29.0f);
+    return fmaf(116.0f, f, -16.0f) * 0.01f;
+}
+// An sRGB-encoded value in [0, 1] to linear light.
+__device__ __forceinline__ float srgb_to_linear(float c)
+{
+    return c <= 0.04045f ? c * (1.0f / 12.92f) : powf((c + 0.055f) * (1.0f / 1.055f), 2.4f);
+}
+
 // The comparison channels of Sec. I / Fig. GTMO on non-negative samples: MATLAB's
-// rgb2gray weights, or V of HSV.
+// rgb2gray weights, V of HSV, or CIE L* (linear samples).
 __device__ __forceinline__ float luma_other(float R, float G, float B, int luma)
 {
+    if (luma == DC_LUMA_LSTAR) return lstar_linear(R, G, B);
     return luma == DC_LUMA_Y ? fmaf(0.1140f, B, fmaf(0.5870f, G, 0.2989f * R)) : fmaxf(R, fmaxf(G, B));
 }
 
@@ -419,6 +434,10 @@ __device__ __forceinline__ FF luma_ff(float R, float G, float B, const Beta& be)
 {
     if (be.luma == DC_LUMA_OURS) return luminance_ff(R, G, B, be);
     if (be.luma == DC_LUMA_Y) return ff_add(ff_add(ff_prod(0.2989f, R), ff_prod(0.5870f, G)), ff_prod(0.1140f, B));
+    if (be.luma == DC_LUMA_LSTAR)  // (binary32 only; the host does not route L* here)
+        return {255.0f * lstar_linear(srgb_to_linear(R * (1.0f / 255.0f)), srgb_to_linear(G * (1.0f / 255.0f)),
+                                      srgb_to_linear(B * (1.0f / 255.0f))),
+                0.0f};
     return {fmaxf(R, fmaxf(G, B)), 0.0f};
 }
 
@@ -530,8 +549,16 @@ struct GroupIO {
     {
 #pragma unroll
         for (int k = 0; k < G; ++k) {
-            const float v = luma_other(sample(w, 3 * k), sample(w, 3 * k + 1), sample(w, 3 * k + 2), luma);
-            Lv[k] = IN_DT == DC_U8 ? v * (1.0f / 255.0f) : v;
+            float R = sample(w, 3 * k), Gc = sample(w, 3 * k + 1), B = sample(w, 3 * k + 2);
+            if (IN_DT == DC_U8 && luma == DC_LUMA_LSTAR) {  // CIELAB is defined on linear light
+                R = srgb_to_linear(R * (1.0f / 255.0f));
+                Gc = srgb_to_linear(Gc * (1.0f / 255.0f));
+                B = srgb_to_linear(B * (1.0f / 255.0f));
+                Lv[k] = lstar_linear(R, Gc, B);
+            } else {
+                const float v = luma_other(R, Gc, B, luma);
+                Lv[k] = IN_DT == DC_U8 ? v * (1.0f / 255.0f) : v;
+            }
         }
     }
 
@@ -733,6 +760,9 @@ struct GroupIO {
                     c[i] = fmaxf(__ldg(reinterpret_cast<const float*>(q) + i), 0.0f);
                 }
             }
+            if (IN_DT == DC_U8 && be.luma == DC_LUMA_LSTAR)
+                return lstar_linear(srgb_to_linear(c[0] * (1.0f / 255.0f)), srgb_to_linear(c[1] * (1.0f / 255.0f)),
+                                    srgb_to_linear(c[2] * (1.0f / 255.0f)));
             const float v = luma_other(c[0], c[1], c[2], be.luma);
             return IN_DT == DC_U8 ? v * (1.0f / 255.0f) : v;
         }

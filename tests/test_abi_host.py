@@ -232,7 +232,7 @@ def test_new_fields_validated(abi):
     out = (abi.dc_image_out * 1)(abi.dc_image_out(1 << 22, 16, 0, 0))
     ws = ctypes.c_void_p(1 << 12)
     g = abi.dc_global_params(0, 1.0, 1e-4, 0)
-    for bad in (abi.dc_decolor_params(0.55, 0.8, 3, 1.0), abi.dc_decolor_params(0.55, 0.8, -1, 1.0),
+    for bad in (abi.dc_decolor_params(0.55, 0.8, 4, 1.0), abi.dc_decolor_params(0.55, 0.8, -1, 1.0),
                 abi.dc_decolor_params(0.55, 0.8, 0, -0.5), abi.dc_decolor_params(0.55, 0.8, 0, 9.0),
                 abi.dc_decolor_params(0.55, 0.8, 0, float("nan"))):
         assert lib.dc_decolorize_tonemap_global(ins, out, 1, ctypes.byref(bad), ctypes.byref(g), None, ws,

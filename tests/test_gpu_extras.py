@@ -51,12 +51,15 @@ def _check_rgb(got, ref, dt, what):
 
 
 # -------------------------------------------------------------- channels ----
-@pytest.mark.parametrize("luma", ["y", "v"])
+CH = {"y": 1, "v": 2, "lstar": 3}
+
+
+@pytest.mark.parametrize("luma", ["y", "v", "lstar"])
 @pytest.mark.parametrize("kind", ["u8", "f16", "f32"])
 def test_channel_decolorize(dc, oracle_mod, luma, kind):
     import torch
     img = _img(kind, 203, 61, 21)
-    ch = {"y": oracle_mod.LUMA_Y, "v": oracle_mod.LUMA_V}[luma]
+    ch = CH[luma]
     L64 = oracle_mod.decolorize(img, channel=ch)
     odt = "u8" if kind == "u8" else "f32"
     y = _empty(img.shape[:2], odt)
@@ -65,18 +68,23 @@ def test_channel_decolorize(dc, oracle_mod, luma, kind):
     check_out(y.cpu().numpy(), L64, odt, what="decolorize %s %s" % (luma, kind), rel=True)
 
 
-@pytest.mark.parametrize("luma", ["y", "v"])
+@pytest.mark.parametrize("luma", ["y", "v", "lstar"])
 @pytest.mark.parametrize("op", ["global", "histeq", "local"])
 @pytest.mark.parametrize("kind", ["u8", "f32"])
 def test_channel_tonemap(dc, oracle_mod, luma, op, kind):
     import torch
     img = _img(kind, 333, 190, 22)
-    ch = {"y": oracle_mod.LUMA_Y, "v": oracle_mod.LUMA_V}[luma]
+    ch = CH[luma]
     L64 = oracle_mod.decolorize(img, channel=ch)
     ldr = kind == "u8"
     for odt in ("u8", "f32"):
         y = _empty(img.shape[:2], odt)
         x = to_dev(img)
+        if op == "local" and luma == "lstar" and kind == "u8" and odt == "f32":
+            with pytest.raises(dc.DcError) as e:  # not offered: see DC_LUMA_LSTAR
+                dc.decolorize_tonemap_local(x, y, luma=luma, block_s=16)
+            assert e.value.status == 2
+            continue
         if op == "local":
             dc.decolorize_tonemap_local(x, y, luma=luma, block_s=16)
             ref = oracle_mod.tonemap_local_plane(L64, ldr=ldr, block_s=16)
