@@ -226,7 +226,7 @@ DC_API int dc_decolorize_tonemap_local(const dc_image_in* in, const dc_image_out
  * (two passes, the global call's result) and m = mu.  Records must be restarted
  * before their first use.  lambda in (0, 1]; gparams->mode must be DC_SIGMOID.
  * The outputs of a restarted frame equal dc_decolorize_tonemap_global's.  Outputs
- * are gray (channels 0 or 1). */
+ * may be gray or colour (channels 3). */
 typedef struct {
     float m;           /* carried log-mean estimate */
     float mu_last;     /* log-mean of the last frame */
@@ -250,8 +250,8 @@ DC_API int dc_decolorize_tonemap_video(const dc_image_in* in, const dc_image_out
  * `state` is a caller-owned device buffer of dc_video_local_state_bytes() bytes
  * (256-byte aligned) holding one record per image of the batch in input order (a
  * 256-byte header and the image's tables); keep it, the images' sizes and lparams
- * unchanged between the frames of a sequence.  ws: as for DC_OP_LOCAL.  Outputs are
- * gray (channels 0 or 1).  Errors: DC_ERR_INVALID_ARG for a NULL, misaligned or
+ * unchanged between the frames of a sequence.  ws: as for DC_OP_LOCAL.  Outputs may be
+ * gray or colour (channels 3: the colour reconstruction of each frame).  Errors: DC_ERR_INVALID_ARG for a NULL, misaligned or
  * too small state buffer, restart not 0 or 1, or the local call's argument errors. */
 DC_API size_t dc_video_local_state_bytes(const dc_image_in* in, int32_t n, const dc_local_params* lparams);
 DC_API int dc_decolorize_tonemap_local_video(const dc_image_in* in, const dc_image_out* out, int32_t n,

@@ -384,3 +384,10 @@ def tonemap_video_local(frames, block_s: int = 32, radius_blocks: int = 2, bins:
         edge = local_tables(u, block_s, radius_blocks, bins)
         rng = own
     return ys
+
+
+def video_color(frames, ys, s: float = 1.0, beta_R: float = BETA_R, beta_k: float = BETA_K,
+                channel: int = LUMA_OURS):
+    """Colour reconstruction of every frame of a sequence from its tone-mapped plane:
+    [(H, W, 3)] = min(1, y (C/L)^s) per frame."""
+    return [color_reconstruct(f, decolorize(f, beta_R, beta_k, channel), y, s) for f, y in zip(frames, ys)]

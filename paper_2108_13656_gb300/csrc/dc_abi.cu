@@ -128,7 +128,7 @@ int64_t lvs_record_bytes(const dc_image_in& in, const dc_local_params& l)
 
 int out_channels(const dc_image_out& o) { return o.channels == 3 ? 3 : 1; }
 
-int validate_image(const dc_image_in& in, const dc_image_out* out, bool local, bool tonemap, bool video)
+int validate_image(const dc_image_in& in, const dc_image_out* out, bool local, bool tonemap)
 {
     if (!dt_ok(in.dtype)) return DC_ERR_UNSUPPORTED_DTYPE;
     if (in.reserved != 0 || in.width < 1 || in.height < 1) return DC_ERR_INVALID_ARG;
@@ -141,7 +141,7 @@ int validate_image(const dc_image_in& in, const dc_image_out* out, bool local, b
         if (!dt_ok(out->dtype)) return DC_ERR_UNSUPPORTED_DTYPE;
         if (out->data == nullptr || (out->channels != 0 && out->channels != 1 && out->channels != 3))
             return DC_ERR_INVALID_ARG;
-        if (out->channels == 3 && (!tonemap || video)) return DC_ERR_INVALID_ARG;  // colour needs a tone-mapped y
+        if (out->channels == 3 && !tonemap) return DC_ERR_INVALID_ARG;  // colour needs a tone-mapped y
         const int oe = esz(out->dtype) * out_channels(*out);
         if (out->stride_bytes < (int64_t)in.width * oe) return DC_ERR_INVALID_ARG;
         if ((reinterpret_cast<uintptr_t>(out->data) % esz(out->dtype)) != 0 || (out->stride_bytes % esz(out->dtype)) != 0)
@@ -556,7 +556,7 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
         // reduction the call uses (statistics passes)
         const int pl = kind == PK_STATS       ? (b->need_minmax == 0 ? 1 : 0)
                        : kind == PK_STATS_LOG ? (b->need_logsum == 0 ? 1 : 0)
-                       : (color && (kind == PK_APPLY_G || kind == PK_APPLY_L)) ? 2
+                       : (color && (kind == PK_APPLY_G || kind == PK_APPLY_L || kind == PK_VIDEO || kind == PK_VIDEO_L)) ? 2
                                               : ((plane && reads_plane(kind, in_dt)) ? 1 : 0);
         int occ = in_dt == DC_U8 ? occupancy_u8(CAP, op.opk, kind, pl)
                                  : (in_dt == DC_F16 ? occupancy_f16(CAP, op.opk, kind, pl) : occupancy_f32(CAP, op.opk, kind, pl));
@@ -589,7 +589,7 @@ int run(const dc_image_in* in, const dc_image_out* out, int32_t n, const dc_deco
     int rc = validate_params(p, op);
     if (rc != DC_OK) return rc;
     for (int k = 0; k < n; ++k) {
-        rc = validate_image(in[k], query ? nullptr : &out[k], op.opk == kOpkLocal, op.opk != kOpkDecolor, op.video());
+        rc = validate_image(in[k], query ? nullptr : &out[k], op.opk == kOpkLocal, op.opk != kOpkDecolor);
         if (rc != DC_OK) return rc;
     }
     if (!query && p->luma == DC_LUMA_LSTAR && op.opk == kOpkLocal) {

@@ -720,7 +720,8 @@ __device__ void tile_apply_global_color(const DcBatch<CAP>& P, const DcImage& im
 // Frame sequences: the centred sigmoid around the carried log-mean m of the image's
 // stream (one pass), and the frame's own log-sum for the next estimate, rounded per
 // group to 2^-24 exactly as the statistics pass sums it.
-template <int IN_DT, int CAP>
+// COLOR: interleaved RGB output (the colour reconstruction of each pixel).
+template <int IN_DT, bool COLOR, int CAP>
 __device__ void tile_video(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* ic, const TileRect& t,
                            const Beta& be, const Derived& d, unsigned char* smem)
 {
@@ -729,18 +730,34 @@ __device__ void tile_video(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* 
     const float delta = P.delta, mu = d.mu, exp_mu = d.exp_mu, k = P.gain_k;
     const bool one = P.gain_is_one != 0;
     long long acc = 0;
-    consume_tile<IN_DT, false>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+    // y of a group in place and its log-sum; Lv: the luminance
+    auto curve = [&](int n, float (&Lv)[G], float (&y)[G]) __attribute__((always_inline)) {
         float v[G];
 #pragma unroll
         for (int j = 0; j < G; ++j) {
             const float x = Lv[j] + delta;
             const float lx = ln_fast(x);
             v[j] = j < n ? lx : 0.0f;
-            Lv[j] = one ? __fdividef(x, x + exp_mu) : rcp_fast(1.0f + exp_fast(-k * (lx - mu)));
+            y[j] = one ? __fdividef(x, x + exp_mu) : rcp_fast(1.0f + exp_fast(-k * (lx - mu)));
         }
-        GroupIO<IN_DT>::store(im, r, c, n, vec, Lv);
         acc += __float2ll_rn(pairwise_sum<G>(v) * (float)(1 << kLogFixedShift));
-    });
+    };
+    if constexpr (COLOR) {
+        const float cs = P.color_s;
+        const bool s_one = P.color_s_one != 0;
+        walk_tile<IN_DT, false, true>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G], const uint32_t (&w)[12])
+                                                     __attribute__((always_inline)) {
+            float y[G], o[3 * G];
+            curve(n, Lv, y);
+            GroupIO<IN_DT>::color_values(w, Lv, y, be, cs, s_one, o);
+            GroupIO<IN_DT>::store_rgb(im, r, c, n, vec, o);
+        });
+    } else {
+        consume_tile<IN_DT, false>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+            curve(n, Lv, Lv);
+            GroupIO<IN_DT>::store(im, r, c, n, vec, Lv);
+        });
+    }
     acc = warp_sum_ll(acc);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (lane == 0) S.wsum[warp] = acc;
@@ -1211,7 +1228,7 @@ __device__ __forceinline__ void stage_curves(const DcBatch<CAP>& P, const DcImag
 // pass) and through the bilinear blend of the staged curves (the output).  HDR
 // coordinates are taken in the carried range, clamped; the frame's own range is
 // accumulated for the next frame.
-template <int IN_DT, int CAP>
+template <int IN_DT, bool COLOR, int CAP>
 __device__ void tile_video_local(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* ic, const TileRect& t, int I,
                                  const Beta& be, const Derived& d, unsigned char* smem)
 {
@@ -1294,6 +1311,11 @@ __device__ void tile_video_local(const DcBatch<CAP>& P, const DcImage& im, DcImg
             atomicAdd(&Hs.fs[cur], rf);
         }
         // the previous frame's curves (bilinear blend, as the apply pass)
+        float Lk[COLOR ? G : 1];  // colour output: the luminance, for the channel ratios
+        if constexpr (COLOR) {
+#pragma unroll
+            for (int k = 0; k < G; ++k) Lk[k] = Lv[k];
+        }
         const int2 ri = S.row[r - t.r0];
         const float2* rowp = S.tab + ri.x;
         const float wy = __int_as_float(ri.y);
@@ -1325,12 +1347,23 @@ __device__ void tile_video_local(const DcBatch<CAP>& P, const DcImage& im, DcImg
             const float F = fmaf(wy, bot - top, top);
             Lv[k] = alpha_one ? F : fmaf(alpha, F - u, u);
         }
-        GroupIO<IN_DT>::store(im, r, c, n, vec, Lv);
+        if constexpr (COLOR) {
+            float o[3 * G];
+            GroupIO<IN_DT>::color_values(*wp, Lk, Lv, be, P.color_s, P.color_s_one != 0, o);
+            GroupIO<IN_DT>::store_rgb(im, r, c, n, vec, o);
+        } else {
+            GroupIO<IN_DT>::store(im, r, c, n, vec, Lv);
+        }
     };
-    if (precise) {
+    if (precise || COLOR) {  // the raw samples are needed
         walk_block_patches<IN_DT, false, true>(im, t, s, be,
                                                [&](int r, int c, int n, bool vec, float (&Lv)[G], const uint32_t (&w)[12])
-                                                   __attribute__((always_inline)) { group_fn(true, r, c, n, vec, Lv, &w); });
+                                                   __attribute__((always_inline)) {
+                                                       if (precise)
+                                                           group_fn(true, r, c, n, vec, Lv, &w);
+                                                       else
+                                                           group_fn(false, r, c, n, vec, Lv, &w);
+                                                   });
     } else {
         walk_block_patches<IN_DT, false>(im, t, s, be, [&](int r, int c, int n, bool vec, float (&Lv)[G])
                                                             __attribute__((always_inline)) {
@@ -1505,9 +1538,9 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
         } else if constexpr (KIND == PK_CDF) {
             tile_cdf(P, im, ic, I, lt, tr, smem);
         } else if constexpr (KIND == PK_VIDEO) {
-            tile_video<IN_DT>(P, im, ic, tr, be, s_d, smem);
+            tile_video<IN_DT, PL == 2>(P, im, ic, tr, be, s_d, smem);
         } else if constexpr (KIND == PK_VIDEO_L) {
-            tile_video_local<IN_DT>(P, im, ic, tr, I, be, s_d, smem);
+            tile_video_local<IN_DT, PL == 2>(P, im, ic, tr, I, be, s_d, smem);
         } else {
             tile_apply_local<IN_DT, PL>(P, im, tr, I, be, s_d, smem);
         }
@@ -1593,16 +1626,18 @@ int occupancy_one()
     X(OPK_DECOLOR, PK_DECOLOR, 0) X(OPK_GLOBAL, PK_STATS, 0) X(OPK_GLOBAL, PK_STATS, 1)              \
         X(OPK_GLOBAL, PK_STATS_LOG, 0) X(OPK_GLOBAL, PK_STATS_LOG, 1) X(OPK_GLOBAL, PK_LOGHIST, 0)    \
         X(OPK_GLOBAL, PK_LOGHIST, 1) X(OPK_GLOBAL, PK_APPLY_G, 0) X(OPK_GLOBAL, PK_APPLY_G, 1)        \
-        X(OPK_GLOBAL, PK_APPLY_G, 2) X(OPK_GLOBAL, PK_VIDEO, 0) X(OPK_LOCAL, PK_STATS_LOG, 0)         \
+        X(OPK_GLOBAL, PK_APPLY_G, 2) X(OPK_GLOBAL, PK_VIDEO, 0) X(OPK_GLOBAL, PK_VIDEO, 2)            \
+        X(OPK_LOCAL, PK_STATS_LOG, 0)                                                                 \
         X(OPK_LOCAL, PK_STATS_LOG, 1) X(OPK_LOCAL, PK_BLOCKH, 0) X(OPK_LOCAL, PK_BLOCKH, 1)           \
         X(OPK_LOCAL, PK_CDF, 0) X(OPK_LOCAL, PK_APPLY_L, 0) X(OPK_LOCAL, PK_APPLY_L, 1)               \
-        X(OPK_LOCAL, PK_APPLY_L, 2) X(OPK_LOCAL, PK_VIDEO_L, 0)
+        X(OPK_LOCAL, PK_APPLY_L, 2) X(OPK_LOCAL, PK_VIDEO_L, 0) X(OPK_LOCAL, PK_VIDEO_L, 2)
 
 template <int IN_DT>
 int launch_dispatch(const void* batch, int cap, int opk, int kind, int ph, int pl, LaunchShape ls, void* stream)
 {
 #define DC_CASE(OP, K, PL)                                                                               \
-    if constexpr (!PL || IN_DT != DC_U8 || K == PK_APPLY_G || K == PK_APPLY_L || K == PK_STATS) {       \
+    if constexpr (!PL || IN_DT != DC_U8 || K == PK_APPLY_G || K == PK_APPLY_L || K == PK_STATS || K == PK_VIDEO || \
+                  K == PK_VIDEO_L) {       \
         if (opk == OP && kind == K && pl == PL) {                                                       \
             if (cap == kCapSmall) return launch_one<IN_DT, OP, K, kCapSmall, PL>(batch, ph, ls, stream); \
             if (cap == kCapMid) return launch_one<IN_DT, OP, K, kCapMid, PL>(batch, ph, ls, stream);     \
@@ -1618,7 +1653,8 @@ template <int IN_DT>
 int occupancy_dispatch(int cap, int opk, int kind, int pl)
 {
 #define DC_CASE(OP, K, PL)                                                                 \
-    if constexpr (!PL || IN_DT != DC_U8 || K == PK_APPLY_G || K == PK_APPLY_L || K == PK_STATS) { \
+    if constexpr (!PL || IN_DT != DC_U8 || K == PK_APPLY_G || K == PK_APPLY_L || K == PK_STATS || K == PK_VIDEO || \
+                  K == PK_VIDEO_L) { \
         if (opk == OP && kind == K && pl == PL) {                                         \
             if (cap == kCapSmall) return occupancy_one<IN_DT, OP, K, kCapSmall, PL>(); \
             if (cap == kCapMid) return occupancy_one<IN_DT, OP, K, kCapMid, PL>();     \

@@ -328,3 +328,22 @@ def test_local_video_odd_layouts(dc, oracle_mod, H, W, pad, off):
             vs(x, y)
             torch.cuda.synchronize()
             check_f32(y.cpu().numpy(), ys64[t], what="local video odd %dx%d %s frame %d" % (H, W, kind, t))
+
+
+@pytest.mark.parametrize("kind,odt", [("u8", "u8"), ("u8", "f32"), ("f32", "f32"), ("f16", "u8")])
+@pytest.mark.parametrize("op", ["global", "local"])
+def test_video_colour(dc, oracle_mod, kind, odt, op):
+    import torch
+    frames = _frames(kind, 3, 260, 150)
+    if op == "global":
+        ys, _ = oracle_mod.tonemap_video_global(frames, lam=0.5)
+        vs = dc.VideoStreams(1, lam=0.5)
+    else:
+        ys = oracle_mod.tonemap_video_local(frames, block_s=16, bins=24)
+        vs = dc.VideoLocalStreams(1, block_s=16, bins=24)
+    refs = oracle_mod.video_color(frames, ys)
+    for t, f in enumerate(frames):
+        out = _empty(f.shape[:2] + (3,), odt)
+        vs(to_dev(f), out)
+        torch.cuda.synchronize()
+        _check_rgb(out.cpu().numpy(), refs[t], odt, "colour video %s %s -> %s frame %d" % (op, kind, odt, t))

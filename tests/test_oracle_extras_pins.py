@@ -237,3 +237,14 @@ def test_lstar_decodes_8bit_srgb():
     assert L[2] == pytest.approx(116 * (Y / (3 * D * D)) / 100, rel=1e-12)
     Y = ((200 / 255 + 0.055) / 1.055) ** 2.4
     assert L[3] == pytest.approx((116 * Y ** (1 / 3) - 16) / 100, rel=1e-12)
+
+
+def test_video_colour_of_a_still_sequence_is_the_colour_call():
+    from paper_2108_13656_gb300 import synth
+    img = synth.s_ldr(40, 24, seed=12)
+    ys, _ = oracle.tonemap_video_global([img] * 3, lam=0.4)
+    for c in oracle.video_color([img] * 3, ys, s=0.7):
+        np.testing.assert_array_equal(c, oracle.tonemap_global_color(img, s=0.7))
+    ysl = oracle.tonemap_video_local([img] * 2, block_s=8)
+    for c in oracle.video_color([img] * 2, ysl):
+        np.testing.assert_array_equal(c, oracle.tonemap_local_color(img, block_s=8))
