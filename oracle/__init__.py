@@ -391,3 +391,33 @@ def video_color(frames, ys, s: float = 1.0, beta_R: float = BETA_R, beta_k: floa
     """Colour reconstruction of every frame of a sequence from its tone-mapped plane:
     [(H, W, 3)] = min(1, y (C/L)^s) per frame."""
     return [color_reconstruct(f, decolorize(f, beta_R, beta_k, channel), y, s) for f, y in zip(frames, ys)]
+
+
+def tonemap_video_histeq(frames, delta: float = 1e-4, beta_R: float = BETA_R, beta_k: float = BETA_K,
+                         channel: int = LUMA_OURS):
+    """A frame sequence through global histogram equalisation with the previous frame's
+    histogram: frame 0 is equalised with its own (and, HDR, in its own log range);
+    frame t >= 1 is mapped through frame t-1's cumulative histogram, its HDR coordinate
+    taken in frame t-1's log range (clamped), and its own histogram - binned in that
+    same range - and its own range go to frame t+1.  Returns [y_t]."""
+    lib = _load()
+    ys = []
+    hist = None
+    rng = (0.0, 0.0)
+    for img in frames:
+        ldr = img.dtype == np.uint8
+        L = np.ascontiguousarray(decolorize(img, beta_R, beta_k, channel))
+        _, lo, hi = log_stats(L, delta)
+        if hist is None:
+            rng = (lo, hi)
+            hist = gray_hist(L) if ldr else log_hist(L, delta, *rng)
+        y = np.empty_like(L)
+        if ldr:
+            lib.oracle_tone_histeq_ldr(_dptr(L), L.size, _uptr(hist), _dptr(y))
+            hist = gray_hist(L)
+        else:
+            lib.oracle_tone_histeq_hdr(_dptr(L), L.size, delta, rng[0], rng[1], _uptr(hist), _dptr(y))
+            hist = log_hist(L, delta, *rng)
+            rng = (lo, hi)
+        ys.append(y)
+    return ys

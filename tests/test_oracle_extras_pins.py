@@ -248,3 +248,38 @@ def test_video_colour_of_a_still_sequence_is_the_colour_call():
     ysl = oracle.tonemap_video_local([img] * 2, block_s=8)
     for c in oracle.video_color([img] * 2, ysl):
         np.testing.assert_array_equal(c, oracle.tonemap_local_color(img, block_s=8))
+
+
+@pytest.mark.parametrize("kind", ["u8", "f32"])
+def test_histeq_still_sequence_equals_per_frame(kind):
+    from paper_2108_13656_gb300 import synth
+    img = synth.s_ldr(50, 30, 4) if kind == "u8" else synth.s_hdr(50, 30, 4)
+    ref, _ = oracle.tonemap_global(img, mode=oracle.MODE_HISTEQ)
+    for y in oracle.tonemap_video_histeq([img] * 3):
+        np.testing.assert_array_equal(y, ref)
+
+
+def test_histeq_sequence_through_a_two_level_frame_closed_form():
+    # frame 0: half black (code 0), half white (code 255): its cumulative histogram is
+    # 1/2 for every code below 255 and 1 at 255, so frame 1 (a gray ramp) maps to 1/2
+    # everywhere except its white pixels
+    H, W = 8, 64
+    f0 = np.zeros((H, W, 3), np.uint8)
+    f0[:, W // 2:] = 255
+    ramp = np.tile((np.arange(W) * 255 // (W - 1)).astype(np.uint8)[None, :], (H, 1))
+    f1 = np.repeat(ramp[:, :, None], 3, axis=2)
+    ys = oracle.tonemap_video_histeq([f0, f1])
+    expect = np.where(ramp == 255, 1.0, 0.5)
+    np.testing.assert_allclose(ys[1], expect, rtol=0, atol=1e-15)
+
+
+def test_histeq_sequence_range_follows_one_frame_behind():
+    from paper_2108_13656_gb300 import synth
+    f0 = synth.s_hdr(40, 24, 6)
+    f1 = f0.copy()
+    f1[3, 5] = f0.max() * 1e3  # beyond frame 0's range: clamps to u = 1
+    ys = oracle.tonemap_video_histeq([f0, f1])
+    other = np.ones(f0.shape[:2], bool)
+    other[3, 5] = False
+    np.testing.assert_array_equal(ys[1][other], ys[0][other])
+    assert ys[1][3, 5] == 1.0
