@@ -224,13 +224,20 @@ DC_API int dc_decolorize_tonemap_local(const dc_image_in* in, const dc_image_out
  * the next frame of its own stream), caller-owned and written by the call.
  * restart = 1 starts the streams afresh: each frame is centred on its own log-mean
  * (two passes, the global call's result) and m = mu.  Records must be restarted
- * before their first use.  lambda in (0, 1]; gparams->mode must be DC_SIGMOID.
+ * before their first use.  lambda in (0, 1].
+ * DC_HISTEQ: a frame of a running sequence is mapped through the previous frame's
+ * cumulative histogram (8-bit: of gray codes; HDR: of u in the previous frame's log
+ * range, its coordinate clamped to that range) and its own histogram, binned the same
+ * way, and its own log range go to the next frame (lambda unused); again one pass.
  * The outputs of a restarted frame equal dc_decolorize_tonemap_global's.  Outputs
  * may be gray or colour (channels 3). */
 typedef struct {
-    float m;           /* carried log-mean estimate */
-    float mu_last;     /* log-mean of the last frame */
+    float m;           /* carried log-mean estimate (DC_SIGMOID) */
+    float mu_last;     /* log-mean of the last frame (DC_SIGMOID) */
     int64_t frames;    /* frames seen since the restart */
+    int32_t vmin, vmax; /* DC_HISTEQ, HDR input: the last frame's range of round(ln(L + delta) 2^24) */
+    int64_t npix;      /* DC_HISTEQ: pixels of the last frame */
+    uint32_t hist[256]; /* DC_HISTEQ: the last frame's histogram */
 } dc_video_state;
 
 DC_API int dc_decolorize_tonemap_video(const dc_image_in* in, const dc_image_out* out, int32_t n,

@@ -24,7 +24,7 @@ DC_LUMA_OURS, DC_LUMA_Y, DC_LUMA_V, DC_LUMA_LSTAR = 0, 1, 2, 3
 DC_PRESET_PAPER, DC_PRESET_TM1, DC_PRESET_TM2 = 0, 1, 2
 BETA_R, BETA_K = 0.55, 0.8
 LUMA = {"ours": DC_LUMA_OURS, "y": DC_LUMA_Y, "v": DC_LUMA_V, "lstar": DC_LUMA_LSTAR}
-VIDEO_STATE_BYTES = 16  # sizeof(dc_video_state)
+VIDEO_STATE_BYTES = 1056  # sizeof(dc_video_state)
 
 
 class DcError(RuntimeError):
@@ -52,7 +52,9 @@ class dc_decolor_params(ctypes.Structure):
 
 
 class dc_video_state(ctypes.Structure):
-    _fields_ = [("m", ctypes.c_float), ("mu_last", ctypes.c_float), ("frames", ctypes.c_int64)]
+    _fields_ = [("m", ctypes.c_float), ("mu_last", ctypes.c_float), ("frames", ctypes.c_int64),
+                ("vmin", ctypes.c_int32), ("vmax", ctypes.c_int32), ("npix", ctypes.c_int64),
+                ("hist", ctypes.c_uint32 * 256)]
 
 
 class dc_global_params(ctypes.Structure):
@@ -390,14 +392,15 @@ class VideoStreams:
     state lives in a device tensor owned here."""
 
     def __init__(self, n: int, lam: float = 1.0, gain_k: float = 1.0, delta: float = 1e-4,
-                 beta_r: float = BETA_R, beta_k: float = BETA_K, luma="ours", device=None, workspace=None):
+                 beta_r: float = BETA_R, beta_k: float = BETA_K, luma="ours", device=None, workspace=None,
+                 mode="sigmoid"):
         torch = _torch()
         self.lib = load()
         self.n = int(n)
         self.lam = float(lam)
         self.state = torch.zeros(self.n * VIDEO_STATE_BYTES, dtype=torch.uint8, device=device or "cuda")
         self.p = dc_decolor_params(beta_r, beta_k, LUMA.get(luma, luma), 1.0)
-        self.g = dc_global_params(DC_SIGMOID, gain_k, delta, 0)
+        self.g = dc_global_params(int({"sigmoid": DC_SIGMOID, "histeq": DC_HISTEQ}.get(mode, mode)), gain_k, delta, 0)
         self.ws = workspace
         self._restart = True
 
@@ -434,9 +437,9 @@ class VideoStreams:
         raw = self.state.cpu().numpy().tobytes()
         out = []
         for i in range(self.n):
-            f = np.frombuffer(raw[i * 16:i * 16 + 8], dtype=np.float32)
-            q = np.frombuffer(raw[i * 16 + 8:i * 16 + 16], dtype=np.int64)
-            out.append({"m": float(f[0]), "mu_last": float(f[1]), "frames": int(q[0])})
+            r = dc_video_state.from_buffer_copy(raw[i * VIDEO_STATE_BYTES:(i + 1) * VIDEO_STATE_BYTES])
+            out.append({"m": r.m, "mu_last": r.mu_last, "frames": int(r.frames), "vmin": r.vmin, "vmax": r.vmax,
+                        "npix": int(r.npix), "hist": np.array(r.hist[:], dtype=np.uint32)})
         return out
 
 

@@ -156,7 +156,6 @@ int validate_params(const dc_decolor_params* p, const OpArgs& op)
     if (p->luma < DC_LUMA_OURS || p->luma > DC_LUMA_LSTAR || !finite_in(p->color_s, 0.f, 8.f)) return DC_ERR_INVALID_ARG;
     if (op.vstate) {
         if (op.opk != kOpkGlobal || !finite_in(op.lambda, 0.f, 1.f) || !(op.lambda > 0.f)) return DC_ERR_INVALID_ARG;
-        if (op.g && op.g->mode != DC_SIGMOID) return DC_ERR_INVALID_ARG;
     }
     if (op.lvs && op.opk != kOpkLocal) return DC_ERR_INVALID_ARG;
     if (op.opk == kOpkGlobal) {

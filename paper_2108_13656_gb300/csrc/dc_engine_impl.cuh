@@ -186,6 +186,14 @@ __device__ __forceinline__ uint32_t bin_coord(int v, const Derived& d)
     return dv * (uint32_t)(m >> 32) + __umulhi(dv, (uint32_t)m);
 }
 
+// Bin coordinate of a fixed-point log value in a carried range, clamped to it (a
+// frame's own values may lie outside the previous frame's range).
+template <int S>
+__device__ __forceinline__ uint32_t bin_coord_clamped(int v, const Derived& d)
+{
+    return bin_coord<S>(min(max(v, d.vmin), d.vmax), d);
+}
+
 // Bin coordinate of a value a histogram pass sees: from the plane's fixed-point
 // log (a histogram pass then keeps the coordinate in the plane for the apply
 // pass), or from L recomputed from RGB.
@@ -720,11 +728,104 @@ __device__ void tile_apply_global_color(const DcBatch<CAP>& P, const DcImage& im
 // Frame sequences: the centred sigmoid around the carried log-mean m of the image's
 // stream (one pass), and the frame's own log-sum for the next estimate, rounded per
 // group to 2^-24 exactly as the statistics pass sums it.
+// Histogram equalisation of a frame of a running sequence: the cumulative table of
+// the previous frame's histogram (the stream's record) maps every pixel - 8-bit: its
+// gray code; HDR: its u-bin in the previous frame's log range, clamped - and the
+// frame's own histogram (binned the same way) and own log range are accumulated.
+template <int IN_DT, bool COLOR, int CAP>
+__device__ void tile_video_histeq(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* ic, const dc_video_state* vs,
+                                  const TileRect& t, const Beta& be, const Derived& d, unsigned char* smem)
+{
+    constexpr int G = InT<IN_DT>::G;
+    constexpr bool ldr = IN_DT == DC_U8;
+    SmemStats& S = *reinterpret_cast<SmemStats*>(smem);
+    SmemApplyG& A = *reinterpret_cast<SmemApplyG*>(smem + sizeof(SmemStats));
+    const uint32_t h = ld_cg_u32(&vs->hist[threadIdx.x]);
+    const uint32_t cum = block_incl_scan(h, S.scan);
+    const long long Np = max((long long)ld_cg_u64(reinterpret_cast<const unsigned long long*>(&vs->npix)), 1ll);
+    const float invN = 1.0f / __ll2float_rn(Np);
+    if (ldr) {
+        A.lut[threadIdx.x] = __uint2float_rn(cum) * invN;  // code q: count(<= q) / N
+    } else {
+        A.lut[threadIdx.x] = __uint2float_rn(cum - h) * invN;  // edge b: count(bins < b) / N
+        if (threadIdx.x == 0) A.lut[256] = 1.0f;
+    }
+    S.hist[threadIdx.x] = 0u;
+    const float delta = P.delta;
+    int qmin = INT_MAX, qmax = INT_MIN;
+    cta_sync();
+    auto curve = [&](int n, const float (&Lv)[G], float (&y)[G]) __attribute__((always_inline)) {
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if (ldr) {
+                const uint32_t q = quant_u8(Lv[j]);
+                y[j] = A.lut[q];
+                if (j < n) atomicAdd(&S.hist[q], 1u);
+            } else {
+                const int v = ln_q24(Lv[j] + delta);
+                if (j < n) {
+                    qmin = min(qmin, v);
+                    qmax = max(qmax, v);
+                }
+                const uint32_t q = bin_coord_clamped<kGlobTS>(v, d);
+                const uint32_t b = min(q >> kGlobTS, 255u);
+                const float frac = (float)(q - (b << kGlobTS)) * (1.0f / (float)(1u << kGlobTS));
+                const float e0 = A.lut[b], e1 = A.lut[b + 1];
+                y[j] = fmaf(frac, e1 - e0, e0);
+                if (j < n) atomicAdd(&S.hist[b], 1u);
+            }
+        }
+    };
+    if constexpr (COLOR) {
+        const float cs = P.color_s;
+        const bool s_one = P.color_s_one != 0;
+        walk_tile<IN_DT, false, true>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G], const uint32_t (&w)[12])
+                                                     __attribute__((always_inline)) {
+            float y[G], o[3 * G];
+            curve(n, Lv, y);
+            GroupIO<IN_DT>::color_values(w, Lv, y, be, cs, s_one, o);
+            GroupIO<IN_DT>::store_rgb(im, r, c, n, vec, o);
+        });
+    } else {
+        consume_tile<IN_DT, false>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
+            float y[G];
+            curve(n, Lv, y);
+            GroupIO<IN_DT>::store(im, r, c, n, vec, y);
+        });
+    }
+    cta_sync();
+    if (S.hist[threadIdx.x]) atomicAdd(&ic->hist[threadIdx.x], S.hist[threadIdx.x]);
+    if constexpr (!ldr) {
+        qmin = __reduce_min_sync(0xffffffffu, qmin);
+        qmax = __reduce_max_sync(0xffffffffu, qmax);
+        if ((threadIdx.x & 31) == 0) {
+            S.wmin[threadIdx.x >> 5] = __int_as_float(qmin);
+            S.wmax[threadIdx.x >> 5] = __int_as_float(qmax);
+        }
+        cta_sync();
+        if (threadIdx.x == 0) {
+            int mn = INT_MAX, mx = INT_MIN;
+            for (int w = 0; w < kThreads / 32; ++w) {
+                mn = min(mn, __float_as_int(S.wmin[w]));
+                mx = max(mx, __float_as_int(S.wmax[w]));
+            }
+            if (mx >= mn) {
+                atomicMax(&ic->lmax_ord, (uint32_t)mx ^ 0x80000000u);
+                atomicMax(&ic->lmin_nord, ~((uint32_t)mn ^ 0x80000000u));
+            }
+        }
+    }
+}
+
 // COLOR: interleaved RGB output (the colour reconstruction of each pixel).
 template <int IN_DT, bool COLOR, int CAP>
 __device__ void tile_video(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* ic, const TileRect& t,
-                           const Beta& be, const Derived& d, unsigned char* smem)
+                           const Beta& be, const Derived& d, unsigned char* smem, int img)
 {
+    if (P.mode == DC_HISTEQ) {
+        tile_video_histeq<IN_DT, COLOR>(P, im, ic, &P.vstate[P.stats_index[img]], t, be, d, smem);
+        return;
+    }
     constexpr int G = InT<IN_DT>::G;
     SmemStats& S = *reinterpret_cast<SmemStats*>(smem);
     const float delta = P.delta, mu = d.mu, exp_mu = d.exp_mu, k = P.gain_k;
@@ -1171,14 +1272,6 @@ __device__ void tile_apply_local(const DcBatch<CAP>& P, const DcImage& im, const
 }
 
 // ------------------------------------------------- phase: local frame sequence --
-// Bin coordinate of a fixed-point log value in a carried range, clamped to it (a
-// frame's own values may lie outside the previous frame's range).
-template <int S>
-__device__ __forceinline__ uint32_t bin_coord_clamped(int v, const Derived& d)
-{
-    return bin_coord<S>(min(max(v, d.vmin), d.vmax), d);
-}
-
 // Staging of the tables of block row I and its neighbours (value, slope pairs) and
 // of the tile's bilinear geometry, as the apply pass does it.
 template <int IN_DT, int CAP>
@@ -1411,8 +1504,8 @@ static_assert(kThreads == 256, "per-bin work uses one consumer thread per histog
 
 template <int KIND>
 struct PassSmem {
-    static constexpr size_t value = KIND == PK_STATS || KIND == PK_STATS_LOG || KIND == PK_LOGHIST || KIND == PK_VIDEO
-                                        ? sizeof(SmemStats)
+    static constexpr size_t value = KIND == PK_STATS || KIND == PK_STATS_LOG || KIND == PK_LOGHIST ? sizeof(SmemStats)
+                                    : KIND == PK_VIDEO                     ? sizeof(SmemStats) + sizeof(SmemApplyG)
                                     : KIND == PK_APPLY_G                   ? sizeof(SmemApplyG) + sizeof(SmemStats)
                                     : KIND == PK_BLOCKH                    ? sizeof(SmemBlockH)
                                     : KIND == PK_CDF                       ? sizeof(SmemCdf)
@@ -1429,6 +1522,24 @@ template <int CAP>
 __device__ void video_update(const DcBatch<CAP>& P)
 {
     constexpr float unit = 1.0f / (float)(1 << kLogFixedShift);
+    if (P.mode == DC_HISTEQ) {  // the frame's histogram, pixel count and (HDR) own range
+        static_assert(kThreads == 256, "a thread per histogram bin");
+        for (int i = 0; i < P.n_img; ++i) {
+            const DcImage& im = P.img[i];
+            const DcImgCtrl* ic = img_ctrl(P.ctrl, i);
+            dc_video_state* st = &P.vstate[P.stats_index[i]];
+            st->hist[threadIdx.x] = ld_cg_u32(&ic->hist[threadIdx.x]);
+            if (threadIdx.x == 0) {
+                st->npix = (long long)im.prow * (long long)im.pcol;
+                st->frames += 1;
+                if (!P.ldr) {
+                    st->vmax = (int)(ld_cg_u32(&ic->lmax_ord) ^ 0x80000000u);
+                    st->vmin = (int)(~ld_cg_u32(&ic->lmin_nord) ^ 0x80000000u);
+                }
+            }
+        }
+        return;
+    }
     for (int i = threadIdx.x; i < P.n_img; i += kThreads) {
         const DcImage& im = P.img[i];
         const long long N = (long long)im.prow * (long long)im.pcol;
@@ -1500,8 +1611,12 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
         if constexpr (KIND == PK_VIDEO) {
             if (img != cached) {  // the stream's carried estimate (updated only after the pass)
                 if (threadIdx.x == 0) {
-                    s_d.mu = ld_cg_f(&P.vstate[P.stats_index[img]].m);
+                    const dc_video_state* vs = &P.vstate[P.stats_index[img]];
+                    s_d.mu = ld_cg_f(&vs->m);
                     s_d.exp_mu = expf(s_d.mu);
+                    if (P.mode == DC_HISTEQ && !P.ldr)  // coordinates in the previous frame's range
+                        derive_range(s_d, (int)ld_cg_u32(reinterpret_cast<const uint32_t*>(&vs->vmin)),
+                                     (int)ld_cg_u32(reinterpret_cast<const uint32_t*>(&vs->vmax)), false, 256);
                 }
                 cta_sync();
                 cached = img;
@@ -1523,11 +1638,17 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
             tile_loghist<IN_DT, PL == 1>(P, im, ic, tr, be, s_d, smem);
         } else if constexpr (KIND == PK_APPLY_G) {
             if (P.stats && lt == 0) write_stats(P, im, ic, img, s_d);
-            if (P.vstate && lt == 0 && threadIdx.x == 0) {  // a restarted stream: m = this frame's mu
+            if (P.vstate && lt == 0) {  // a restarted stream: this frame's statistics start the record
                 dc_video_state* st = &P.vstate[P.stats_index[img]];
-                st->m = s_d.mu;
-                st->mu_last = s_d.mu;
-                st->frames = 1;
+                if (P.mode == DC_HISTEQ) st->hist[threadIdx.x] = ld_cg_u32(&ic->hist[threadIdx.x]);
+                if (threadIdx.x == 0) {
+                    st->m = s_d.mu;
+                    st->mu_last = s_d.mu;
+                    st->frames = 1;
+                    st->npix = (long long)im.prow * (long long)im.pcol;
+                    st->vmax = (int)(ld_cg_u32(&ic->lmax_ord) ^ 0x80000000u);
+                    st->vmin = (int)(~ld_cg_u32(&ic->lmin_nord) ^ 0x80000000u);
+                }
             }
             if constexpr (PL == 2)
                 tile_apply_global_color<IN_DT>(P, im, ic, tr, be, s_d, smem);
@@ -1538,7 +1659,7 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
         } else if constexpr (KIND == PK_CDF) {
             tile_cdf(P, im, ic, I, lt, tr, smem);
         } else if constexpr (KIND == PK_VIDEO) {
-            tile_video<IN_DT, PL == 2>(P, im, ic, tr, be, s_d, smem);
+            tile_video<IN_DT, PL == 2>(P, im, ic, tr, be, s_d, smem, img);
         } else if constexpr (KIND == PK_VIDEO_L) {
             tile_video_local<IN_DT, PL == 2>(P, im, ic, tr, I, be, s_d, smem);
         } else {

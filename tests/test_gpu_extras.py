@@ -347,3 +347,56 @@ def test_video_colour(dc, oracle_mod, kind, odt, op):
         vs(to_dev(f), out)
         torch.cuda.synchronize()
         _check_rgb(out.cpu().numpy(), refs[t], odt, "colour video %s %s -> %s frame %d" % (op, kind, odt, t))
+
+
+def _near_edge(x, eps):
+    """True where x lies within eps of an integer (a gray-code or bin edge)."""
+    return np.abs(x - np.round(x)) < eps
+
+
+@pytest.mark.parametrize("kind,odt", [("u8", "u8"), ("u8", "f32"), ("f16", "f32"), ("f32", "f32")])
+def test_video_histeq_sequence(dc, oracle_mod, kind, odt):
+    # frame t is mapped through frame t-1's cumulative histogram: pixels whose own code
+    # or bin is within rounding of an edge are exempt, and the previous frame's such
+    # pixels (which may have landed in a neighbouring bin of its histogram) bound the
+    # slack of every output, as in the single-image histogram-equalisation tests
+    import torch
+    from _cmp import TOL_F32, check_u8
+    frames = _frames(kind, 4, 300, 170)
+    ys64 = oracle_mod.tonemap_video_histeq(frames)
+    vs = dc.VideoStreams(1, mode="histeq")
+    ldr = kind == "u8"
+    prev_amb, rng = 0, None
+    for t, f in enumerate(frames):
+        y = _empty(f.shape[:2], odt)
+        vs(to_dev(f), y)
+        assert dc.last_launch_count() == ((2 if ldr else 3) if t == 0 else 1)
+        torch.cuda.synchronize()
+        L64 = oracle_mod.decolorize(f)
+        _, lo, hi = oracle_mod.log_stats(L64, 1e-4)
+        if ldr:
+            amb = _near_edge(255.0 * L64 + 0.5, 255 * 1e-5)
+        else:
+            r = (lo, hi) if rng is None else rng
+            amb = _near_edge(256.0 * np.clip((np.log(L64 + 1e-4) - r[0]) / (r[1] - r[0]), 0, 1), 256 * 1e-6)
+        slack = max(int(amb.sum()) if t == 0 else 0, prev_amb) / L64.size
+        got = y.cpu().numpy()
+        if odt == "f32":
+            err = np.abs(got.astype(np.float64) - ys64[t])
+            assert np.all(err[~amb] <= TOL_F32 + slack), (t, float(err[~amb].max()))
+        else:
+            check_u8(got, ys64[t], "histeq video frame %d" % t,
+                     extra_exempt=amb | oracle_mod.u8_boundary_mask(ys64[t], 1e-5 + slack))
+        prev_amb, rng = int(amb.sum()), (lo, hi)
+        st = vs.states()[0]
+        assert st["frames"] == t + 1 and int(st["hist"].sum()) == L64.size
+
+
+def test_video_histeq_restart_equals_the_global_call(dc):
+    import torch
+    f = _frames("f32", 1)[0]
+    a, b = _empty(f.shape[:2], "f32"), _empty(f.shape[:2], "f32")
+    dc.VideoStreams(1, mode="histeq")(to_dev(f), a)
+    dc.decolorize_tonemap_global(to_dev(f), b, mode="histeq")
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
