@@ -298,7 +298,7 @@ int phase_list(const OpArgs& op, bool ldr, int32_t* kinds)
     }
     if (op.opk == kOpkGlobal) {
         if (op.vstate && !op.restart) {  // a frame of a running sequence: one pass
-            kinds[0] = PK_VIDEO;
+            kinds[0] = op.g->mode == DC_HISTEQ ? PK_VIDEO_H : PK_VIDEO;
             return 1;
         }
         kinds[0] = PK_STATS;
@@ -555,7 +555,8 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
         // reduction the call uses (statistics passes)
         const int pl = kind == PK_STATS       ? (b->need_minmax == 0 ? 1 : 0)
                        : kind == PK_STATS_LOG ? (b->need_logsum == 0 ? 1 : 0)
-                       : (color && (kind == PK_APPLY_G || kind == PK_APPLY_L || kind == PK_VIDEO || kind == PK_VIDEO_L)) ? 2
+                       : (color && (kind == PK_APPLY_G || kind == PK_APPLY_L || kind == PK_VIDEO || kind == PK_VIDEO_L ||
+                                   kind == PK_VIDEO_H)) ? 2
                                               : ((plane && reads_plane(kind, in_dt)) ? 1 : 0);
         int occ = in_dt == DC_U8 ? occupancy_u8(CAP, op.opk, kind, pl)
                                  : (in_dt == DC_F16 ? occupancy_f16(CAP, op.opk, kind, pl) : occupancy_f32(CAP, op.opk, kind, pl));

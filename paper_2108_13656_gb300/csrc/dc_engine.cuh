@@ -167,6 +167,9 @@ __device__ __forceinline__ float lg2_ftz(float x)
 }
 // ln x = log2(x) ln 2, for x >= FLT_MIN.
 __device__ __forceinline__ float ln_fast(float x) { return lg2_ftz(x) * 0.693147180559945309f; }
+// ln 2 in units of 2^-24: a group's sum of base-2 logarithms times this is its sum of
+// natural logarithms in the 2^-24 fixed point of the log-sum.
+constexpr float kLn2Q24 = 0.693147180559945309f * 16777216.0f;
 __device__ __forceinline__ float exp_fast(float x) { return __expf(x); }
 
 // ------------------------------------------------------------- Eq. 1-6 -------
@@ -255,7 +258,10 @@ __device__ __forceinline__ float luminance_f32(float R, float G, float B, const 
 }
 
 // Eq. 1-6 for two pixels: the additions and products in f32x2, the square roots
-// and the reciprocal per lane.
+// and the reciprocal per lane.  U8: samples are 8-bit codes, so S = R+G+B is 0 or at
+// least 1; the reciprocal of max(S, 1/2) then gives every term of a black pixel as 0
+// (and the other pixels the same bits), with no select.
+template <bool U8 = false>
 __device__ __forceinline__ void luminance_x2(F2 R, F2 G, F2 B, const Beta& be, float& L0, float& L1, float& s0,
                                              float& s1)
 {
@@ -267,19 +273,25 @@ __device__ __forceinline__ void luminance_x2(F2 R, F2 G, F2 B, const Beta& be, f
     f2split(f2fma(f2s(be.bR), R2, f2s(be.one_m_bR) * G2), c0, c1);
     const F2 L_GR = f2(sqrt_fast(c0), sqrt_fast(c1));                         // Eq. 3
     f2split(S, s0, s1);
-    const F2 inv = f2(rcp_fast(s0), rcp_fast(s1));
+    const F2 inv = U8 ? f2(rcp_fast(fmaxf(s0, 0.5f)), rcp_fast(fmaxf(s1, 0.5f))) : f2(rcp_fast(s0), rcp_fast(s1));
     const F2 r = R * inv, b = B * inv;
     const F2 L_WARM = f2fma(r, L_GR - L_WHITE, L_WHITE);                      // Eq. 4
     const F2 L_COOL = f2fma(b, L_WHITE - B, B);                               // Eq. 5 (L_B = B)
     f2split(f2fma(f2s(be.bk), L_WARM * L_WARM, (f2s(be.one_m_bk) * L_COOL) * L_COOL), a0, a1);
-    L0 = s0 > 0.0f ? sqrt_fast(a0) : 0.0f;                                    // Eq. 6
-    L1 = s1 > 0.0f ? sqrt_fast(a1) : 0.0f;
+    if (U8) {
+        L0 = sqrt_fast(a0);                                                   // Eq. 6
+        L1 = sqrt_fast(a1);
+    } else {
+        L0 = s0 > 0.0f ? sqrt_fast(a0) : 0.0f;
+        L1 = s1 > 0.0f ? sqrt_fast(a1) : 0.0f;
+    }
 }
 
+template <bool U8 = false>
 __device__ __forceinline__ void luminance_x2(F2 R, F2 G, F2 B, const Beta& be, float& L0, float& L1)
 {
     float s0, s1;
-    luminance_x2(R, G, B, be, L0, L1, s0, s1);
+    luminance_x2<U8>(R, G, B, be, L0, L1, s0, s1);
 }
 
 // Linear samples of arbitrary magnitude: Eq. 1-6 are 1-homogeneous, so a pixel
@@ -501,7 +513,7 @@ struct GroupIO {
 #pragma unroll
             for (int k = 0; k < G; k += 2) {
                 float L0, L1;
-                luminance_x2(u8_pair(w, 3 * k), u8_pair(w, 3 * k + 1), u8_pair(w, 3 * k + 2), be, L0, L1);
+                luminance_x2<true>(u8_pair(w, 3 * k), u8_pair(w, 3 * k + 1), u8_pair(w, 3 * k + 2), be, L0, L1);
                 f2split(f2(L0, L1) * f2s(1.0f / 255.0f), Lv[k], Lv[k + 1]);
             }
         } else if constexpr (IN_DT == DC_F16) {

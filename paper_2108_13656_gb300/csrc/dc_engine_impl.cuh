@@ -502,10 +502,12 @@ __device__ void tile_stats(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* 
             }
             if (plane_out) GroupIO<IN_DT>::store_plane(im, r, c, n, vec, plane_log ? v : Lv);
         } else {
+            // base-2 logarithms: the group's sum is scaled to natural units once, and
+            // min / max (monotone in the scaling) when the record is written
 #pragma unroll
             for (int k = 0; k < G; ++k) {
                 if (k < n) {
-                    v[k] = ln_fast(Lv[k] + delta);
+                    v[k] = lg2_ftz(Lv[k] + delta);
                     if constexpr (MM) {
                         vmin = fminf(vmin, v[k]);
                         vmax = fmaxf(vmax, v[k]);
@@ -516,7 +518,7 @@ __device__ void tile_stats(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* 
                 }
             }
             if (plane_out) GroupIO<IN_DT>::store_plane(im, r, c, n, vec, Lv);
-            acc += __float2ll_rn(pairwise_sum<G>(v) * (float)(1 << kLogFixedShift));
+            acc += __float2ll_rn(pairwise_sum<G>(v) * kLn2Q24);
         }
     });
     acc = warp_sum_ll(acc);
@@ -530,8 +532,8 @@ __device__ void tile_stats(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* 
             S.wmax[warp] = __int_as_float(qmax);
         }
     } else {
-        vmin = warp_min(vmin);
-        vmax = warp_max(vmax);
+        vmin = warp_min(vmin) * 0.693147180559945309f;  // (the natural logarithm of each pixel's)
+        vmax = warp_max(vmax) * 0.693147180559945309f;
         if (lane == 0) {
             S.wsum[warp] = acc;
             S.wmin[warp] = vmin;
@@ -820,12 +822,8 @@ __device__ void tile_video_histeq(const DcBatch<CAP>& P, const DcImage& im, DcIm
 // COLOR: interleaved RGB output (the colour reconstruction of each pixel).
 template <int IN_DT, bool COLOR, int CAP>
 __device__ void tile_video(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* ic, const TileRect& t,
-                           const Beta& be, const Derived& d, unsigned char* smem, int img)
+                           const Beta& be, const Derived& d, unsigned char* smem)
 {
-    if (P.mode == DC_HISTEQ) {
-        tile_video_histeq<IN_DT, COLOR>(P, im, ic, &P.vstate[P.stats_index[img]], t, be, d, smem);
-        return;
-    }
     constexpr int G = InT<IN_DT>::G;
     SmemStats& S = *reinterpret_cast<SmemStats*>(smem);
     const float delta = P.delta, mu = d.mu, exp_mu = d.exp_mu, k = P.gain_k;
@@ -837,11 +835,12 @@ __device__ void tile_video(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* 
 #pragma unroll
         for (int j = 0; j < G; ++j) {
             const float x = Lv[j] + delta;
-            const float lx = ln_fast(x);
-            v[j] = j < n ? lx : 0.0f;
-            y[j] = one ? __fdividef(x, x + exp_mu) : rcp_fast(1.0f + exp_fast(-k * (lx - mu)));
+            const float l2 = lg2_ftz(x);  // (summed as the statistics pass sums it)
+            v[j] = j < n ? l2 : 0.0f;
+            y[j] = one ? __fdividef(x, x + exp_mu)
+                       : rcp_fast(1.0f + exp_fast(-k * (l2 * 0.693147180559945309f - mu)));
         }
-        acc += __float2ll_rn(pairwise_sum<G>(v) * (float)(1 << kLogFixedShift));
+        acc += __float2ll_rn(pairwise_sum<G>(v) * kLn2Q24);
     };
     if constexpr (COLOR) {
         const float cs = P.color_s;
@@ -1505,7 +1504,8 @@ static_assert(kThreads == 256, "per-bin work uses one consumer thread per histog
 template <int KIND>
 struct PassSmem {
     static constexpr size_t value = KIND == PK_STATS || KIND == PK_STATS_LOG || KIND == PK_LOGHIST ? sizeof(SmemStats)
-                                    : KIND == PK_VIDEO                     ? sizeof(SmemStats) + sizeof(SmemApplyG)
+                                    : KIND == PK_VIDEO                     ? sizeof(SmemStats)
+                                    : KIND == PK_VIDEO_H                   ? sizeof(SmemStats) + sizeof(SmemApplyG)
                                     : KIND == PK_APPLY_G                   ? sizeof(SmemApplyG) + sizeof(SmemStats)
                                     : KIND == PK_BLOCKH                    ? sizeof(SmemBlockH)
                                     : KIND == PK_CDF                       ? sizeof(SmemCdf)
@@ -1608,7 +1608,7 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
                 cached = img;
             }
         }
-        if constexpr (KIND == PK_VIDEO) {
+        if constexpr (KIND == PK_VIDEO || KIND == PK_VIDEO_H) {
             if (img != cached) {  // the stream's carried estimate (updated only after the pass)
                 if (threadIdx.x == 0) {
                     const dc_video_state* vs = &P.vstate[P.stats_index[img]];
@@ -1659,7 +1659,9 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
         } else if constexpr (KIND == PK_CDF) {
             tile_cdf(P, im, ic, I, lt, tr, smem);
         } else if constexpr (KIND == PK_VIDEO) {
-            tile_video<IN_DT, PL == 2>(P, im, ic, tr, be, s_d, smem, img);
+            tile_video<IN_DT, PL == 2>(P, im, ic, tr, be, s_d, smem);
+        } else if constexpr (KIND == PK_VIDEO_H) {
+            tile_video_histeq<IN_DT, PL == 2>(P, im, ic, &P.vstate[P.stats_index[img]], tr, be, s_d, smem);
         } else if constexpr (KIND == PK_VIDEO_L) {
             tile_video_local<IN_DT, PL == 2>(P, im, ic, tr, I, be, s_d, smem);
         } else {
@@ -1677,7 +1679,7 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
     // itself; the one that counts last clears the block, counter included.  No CTA
     // waits for another.
     // A frame-sequence pass's last CTA also updates every stream's estimate first.
-    if ((P.reset_bytes > 0 || KIND == PK_VIDEO) && ph == P.n_phase - 1) {
+    if ((P.reset_bytes > 0 || KIND == PK_VIDEO || KIND == PK_VIDEO_H) && ph == P.n_phase - 1) {
         __shared__ uint32_t s_last;
         cta_sync();
         if (threadIdx.x == 0) {
@@ -1687,7 +1689,7 @@ __global__ void __launch_bounds__(kThreads, DC_MIN_CTAS) pass_kernel(const __gri
         cta_sync();
         if (s_last) {
             __threadfence();
-            if constexpr (KIND == PK_VIDEO) {
+            if constexpr (KIND == PK_VIDEO || KIND == PK_VIDEO_H) {
                 video_update(P);
                 cta_sync();
             }
@@ -1748,6 +1750,7 @@ int occupancy_one()
         X(OPK_GLOBAL, PK_STATS_LOG, 0) X(OPK_GLOBAL, PK_STATS_LOG, 1) X(OPK_GLOBAL, PK_LOGHIST, 0)    \
         X(OPK_GLOBAL, PK_LOGHIST, 1) X(OPK_GLOBAL, PK_APPLY_G, 0) X(OPK_GLOBAL, PK_APPLY_G, 1)        \
         X(OPK_GLOBAL, PK_APPLY_G, 2) X(OPK_GLOBAL, PK_VIDEO, 0) X(OPK_GLOBAL, PK_VIDEO, 2)            \
+        X(OPK_GLOBAL, PK_VIDEO_H, 0) X(OPK_GLOBAL, PK_VIDEO_H, 2)                                     \
         X(OPK_LOCAL, PK_STATS_LOG, 0)                                                                 \
         X(OPK_LOCAL, PK_STATS_LOG, 1) X(OPK_LOCAL, PK_BLOCKH, 0) X(OPK_LOCAL, PK_BLOCKH, 1)           \
         X(OPK_LOCAL, PK_CDF, 0) X(OPK_LOCAL, PK_APPLY_L, 0) X(OPK_LOCAL, PK_APPLY_L, 1)               \
@@ -1758,7 +1761,7 @@ int launch_dispatch(const void* batch, int cap, int opk, int kind, int ph, int p
 {
 #define DC_CASE(OP, K, PL)                                                                               \
     if constexpr (!PL || IN_DT != DC_U8 || K == PK_APPLY_G || K == PK_APPLY_L || K == PK_STATS || K == PK_VIDEO || \
-                  K == PK_VIDEO_L) {       \
+                  K == PK_VIDEO_L || K == PK_VIDEO_H) {       \
         if (opk == OP && kind == K && pl == PL) {                                                       \
             if (cap == kCapSmall) return launch_one<IN_DT, OP, K, kCapSmall, PL>(batch, ph, ls, stream); \
             if (cap == kCapMid) return launch_one<IN_DT, OP, K, kCapMid, PL>(batch, ph, ls, stream);     \
@@ -1775,7 +1778,7 @@ int occupancy_dispatch(int cap, int opk, int kind, int pl)
 {
 #define DC_CASE(OP, K, PL)                                                                 \
     if constexpr (!PL || IN_DT != DC_U8 || K == PK_APPLY_G || K == PK_APPLY_L || K == PK_STATS || K == PK_VIDEO || \
-                  K == PK_VIDEO_L) { \
+                  K == PK_VIDEO_L || K == PK_VIDEO_H) { \
         if (opk == OP && kind == K && pl == PL) {                                         \
             if (cap == kCapSmall) return occupancy_one<IN_DT, OP, K, kCapSmall, PL>(); \
             if (cap == kCapMid) return occupancy_one<IN_DT, OP, K, kCapMid, PL>();     \

@@ -38,6 +38,8 @@ enum PhaseKind : int32_t {
     PK_VIDEO = 8,     // frame sequences: sigmoid around the carried log-mean + this frame's log-sum
     PK_VIDEO_L = 9,   // local frame sequences: block histograms of the frame and its mapping
                       // through the previous frame's tables, in one pass
+    PK_VIDEO_H = 10,  // histogram-equalisation frame sequences: the previous frame's cumulative
+                      // histogram + this frame's histogram, in one pass
 };
 
 // Per-image record of a local frame sequence (caller-owned state buffer): this header,
