@@ -406,17 +406,25 @@ def precision_8k(dev, peak: float) -> dict:
     return out
 
 
+# Device sleeps (cycles, about 30 ms) that keep the host ahead of the device: the
+# per-call timings enqueue in chunks of HOST_AHEAD_ROUNDS rounds, each behind its own
+# sleep (outside every timed event pair), so no timed call waits on the host.
+SLEEP_CYCLES = 60_000_000
+HOST_AHEAD_ROUNDS = 16
+
+
 def _alone_ms(calls, flush, reps: int) -> list:
-    """Mean device time of each call alone, after an L2-flushing write: everything is
-    enqueued behind a 20 ms device sleep so the host is ahead and the events time the
+    """Mean device time of each call alone, after an L2-flushing write: the host
+    enqueues ahead of the device (device sleeps between chunks), so the events time the
     device only."""
     import torch
     stream = torch.cuda.current_stream()
     ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
           for _ in calls]
     torch.cuda.synchronize()
-    torch.cuda._sleep(20_000_000)
     for k in range(reps):
+        if k % HOST_AHEAD_ROUNDS == 0:
+            torch.cuda._sleep(SLEEP_CYCLES)
         for i, fn in enumerate(calls):
             flush.fill_(k & 0xFF)
             a, b = ev[i][k]
@@ -640,8 +648,9 @@ def run_native(args):
     KC = min(K, 200)
     ev = {name: [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(KC)]
           for name, *_ in OPS}
-    torch.cuda._sleep(20_000_000)
     for k in range(KC):
+        if k % HOST_AHEAD_ROUNDS == 0:
+            torch.cuda._sleep(SLEEP_CYCLES)
         for name, var, op, _, _ in OPS:
             flush.fill_(k & 0xFF)
             s0, s1 = ev[name][k]
