@@ -7,8 +7,10 @@ Workload (one "step"): the 3840x2160 image in its two variants - 8-bit sRGB
 centred-sigmoid tone map and decolorize -> local smoothed-LHE tone map, i.e. four
 C-ABI calls per step and every step of the hot path.  Inputs are synthetic and
 resident in HBM before timing.  `value` times K steps back to back between two CUDA
-events, rotating through 8 copies of every input and output so that no step finds
-its data in L2; the per-call breakdown and the roofline time each call alone
+events, the four calls of a step (independent images, a workspace each) on four side
+streams so that their pass chains overlap, rotating through 8 copies of every input
+and output so that no step finds its data in L2; the same steps on one stream give
+`config.serial_value`.  The per-call breakdown and the roofline time each call alone
 between two events after a 256 MiB L2-flushing write.
 
 Prints ONE JSON line (rank 0).  `value` is whole-job Gpix/s (output pixels of all
@@ -622,26 +624,43 @@ def run_native(args):
             call(name, var, op, outs[name])
         torch.cuda.synchronize()
 
-    # steady state: K steps back to back on rotating buffers, one pair of events
+    # steady state: K steps back to back on rotating buffers, one pair of events.  The
+    # four calls of a step are independent images with workspaces of their own: each
+    # runs on a side stream of its own (dc.CallStreams, forked from and joined back to
+    # the timing stream), so that one call's pass fills the SMs another call leaves
+    # idle between its passes.  The same steps on one stream give the serial figure.
     K = args.steps
-    launches = 0
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    torch.cuda._sleep(20_000_000)  # let the host queue run ahead of the device
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for k in range(K):
-        r = k % ROT
-        for name, *_ in OPS:
-            calls_r[name][r]()
-            launches += dc.last_launch_count()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    step_ms = e0.elapsed_time(e1) / K
+    cs = dc.CallStreams(len(OPS), device=dev)
+
+    def steps(concurrent: bool) -> tuple[float, int]:
+        n_launch = 0
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        torch.cuda._sleep(20_000_000)  # let the host queue run ahead of the device
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        if concurrent:
+            cs.fork(stream)
+        for k in range(K):
+            r = k % ROT
+            for j, (name, *_) in enumerate(OPS):
+                if concurrent:
+                    cs.run(j, calls_r[name][r])
+                else:
+                    calls_r[name][r]()
+                n_launch += dc.last_launch_count()
+        if concurrent:
+            cs.join(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        return e0.elapsed_time(e1) / K, n_launch
+
+    serial_step_ms, _ = steps(False)
+    step_ms, launches = steps(True)
 
     # per call, for the roofline and the breakdown: L2 flushed (256 MiB write) before
     # each call, the call alone between two events
@@ -691,6 +710,7 @@ def run_native(args):
         return float(t.item())
 
     t_max, gpix = aggregate(step_ms, world, reduce_max)
+    serial_t_max, _ = aggregate(serial_step_ms, world, reduce_max)
 
     # end to end through the public API with pinned host buffers: every step copies
     # both inputs in and all four outputs out.  Steps one after another on one stream
@@ -758,6 +778,9 @@ def run_native(args):
                              ROT, ROT * (sum(v.nbytes for v in imgs.values()) +
                                          sum(t.numel() * t.element_size() for t in outs.values())) / 1e9),
                    "per_op_sum_ms": sum(op_ms.values()),
+                   "streams": "the four calls of a step on four side streams (CallStreams)",
+                   "serial_ms_per_step": serial_t_max,
+                   "serial_value": world * 4 * NPIX / (serial_t_max * 1e-3) / 1e9,
                    "parallelism": "replicas" if world > 1 else "single GPU", "per_op": per_op,
                    "per_pass": per_pass},
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -47,4 +47,4 @@ from ._abi import (  # noqa: F401
     status_string,
     workspace_bytes,
 )
-from .pipeline import HostPipeline  # noqa: F401
+from .pipeline import CallStreams, HostPipeline  # noqa: F401

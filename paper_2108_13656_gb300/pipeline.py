@@ -13,6 +13,12 @@ gives exactly what it gives when the steps run one after another.
 Host buffers: a step's host inputs are read by its input copy, which runs after
 `submit` returns, so they must not change until `input_consumed(step)` is true (or
 the pipeline is synchronised); its host outputs are complete once `done(step)` is.
+
+`CallStreams` runs independent calls (different images, different workspaces) on
+streams of their own, so that the device works on one call while another is between
+passes: a call's passes depend on the whole previous pass of that call, and the
+launch, the ramp-up and the tail of each pass leave SMs idle that a concurrent
+call's pass fills.
 """
 from __future__ import annotations
 
@@ -90,3 +96,46 @@ class HostPipeline:
     def synchronize(self):
         for s in (self.s_in, self.s_run, self.s_out):
             s.synchronize()
+
+
+class CallStreams:
+    """n CUDA streams for independent calls.  `fork(stream)` makes every side stream
+    wait for what `stream` (default: the current stream) has enqueued so far;
+    `run(i, call)` enqueues `call` (anything called with a stream, e.g. a
+    PreparedCall) on side stream i; `join(stream)` makes `stream` wait for everything
+    enqueued on the side streams.  Calls on one side stream run in order; calls on
+    different side streams may overlap, so they must not share a workspace or write
+    a buffer another one reads - `run` refuses a workspace already used on another
+    side stream since the last fork."""
+
+    def __init__(self, n: int, device=None):
+        import torch
+        if n < 1:
+            raise ValueError("need at least one stream")
+        dev = torch.device(device or "cuda")
+        self.streams = [torch.cuda.Stream(device=dev) for _ in range(n)]
+        self._owner = {}
+
+    def fork(self, stream=None):
+        import torch
+        src = stream or torch.cuda.current_stream()
+        ev = torch.cuda.Event()
+        ev.record(src)
+        for s in self.streams:
+            s.wait_event(ev)
+        self._owner = {}
+
+    def run(self, i: int, call):
+        ws = getattr(call, "ws_ptr", None)  # the device address of a PreparedCall's workspace
+        if ws is not None:
+            if self._owner.setdefault(ws, i) != i:
+                raise ValueError("a workspace is in use on another side stream; give each stream its own")
+        return call(self.streams[i])
+
+    def join(self, stream=None):
+        import torch
+        dst = stream or torch.cuda.current_stream()
+        for s in self.streams:
+            ev = torch.cuda.Event()
+            ev.record(s)
+            dst.wait_event(ev)

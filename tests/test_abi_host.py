@@ -226,6 +226,37 @@ def test_host_pipeline_rejects_zero_depth():
         HostPipeline({}, {}, [], depth=0)
 
 
+def test_call_streams_rejects_zero_streams():
+    from paper_2108_13656_gb300.pipeline import CallStreams
+    with pytest.raises(ValueError):
+        CallStreams(0)
+
+
+def test_call_streams_workspace_ownership_without_a_device():
+    # run() checks the workspace before it touches a stream: a fake call whose
+    # workspace address is taken by another side stream is refused, and fork()
+    # (emulated by clearing the table) releases it
+    from paper_2108_13656_gb300.pipeline import CallStreams
+    cs = CallStreams.__new__(CallStreams)
+    cs.streams = ["s0", "s1"]
+    cs._owner = {}
+    seen = []
+
+    class Fake:
+        ws_ptr = 0x1000
+
+        def __call__(self, stream):
+            seen.append(stream)
+
+    cs.run(0, Fake())
+    cs.run(0, Fake())
+    with pytest.raises(ValueError):
+        cs.run(1, Fake())
+    cs._owner = {}
+    cs.run(1, Fake())
+    assert seen == ["s0", "s0", "s1"]
+
+
 def test_new_fields_validated(abi):
     lib = abi.load()
     ins = (abi.dc_image_in * 1)(_img(16, 4))

@@ -69,3 +69,47 @@ def test_pipelined_steps_equal_calls_alone(dc, depth):
         for name, ref in expect[which].items():
             assert torch.equal(hy[name], ref), "step %d output %s differs from the call alone" % (k, name)
     assert all(dc.query_status(w) == 0 for w in pipe.workspaces)
+
+
+def test_call_streams_equal_calls_alone(dc):
+    # the four calls on four side streams, several steps over rotating inputs and
+    # outputs without a join between steps: every output is the call's alone
+    import torch
+    inputs = [host_inputs(s) for s in range(3)]
+    expect = [alone(dc, hx) for hx in inputs]
+    dev_in = [{k: v.cuda() for k, v in hx.items()} for hx in inputs]
+    wss = [dc.Workspace() for _ in CALLS]
+    outs, calls = [], []
+    for s in range(3):
+        y = {o: torch.full(inputs[s][i].shape[:2], 7, dtype=torch.uint8 if i == "ldr" else torch.float32,
+                           device="cuda") for op, i, o, params in CALLS}
+        outs.append(y)
+        calls.append([dc.PreparedCall(op, dev_in[s][i], y[o], workspace=w, **params)
+                      for (op, i, o, params), w in zip(CALLS, wss)])
+    cs = dc.CallStreams(len(CALLS))
+    cs.fork()
+    for k in range(9):
+        for j, c in enumerate(calls[k % 3]):
+            cs.run(j, c)
+    cs.join()
+    torch.cuda.synchronize()
+    for s in range(3):
+        for name, ref in expect[s].items():
+            assert torch.equal(outs[s][name].cpu(), ref), "input set %d output %s differs from the call alone" % (s, name)
+    assert all(dc.query_status(w) == 0 for w in wss)
+
+
+def test_call_streams_refuse_a_shared_workspace(dc):
+    import torch
+    x = host_inputs(0)["ldr"].cuda()
+    y = torch.empty(x.shape[:2], dtype=torch.uint8, device="cuda")
+    w = dc.Workspace()
+    a = dc.PreparedCall("global", x, y, workspace=w)
+    cs = dc.CallStreams(2)
+    cs.fork()
+    cs.run(0, a)
+    cs.run(0, a)  # the same stream: in order, allowed
+    with pytest.raises(ValueError):
+        cs.run(1, a)
+    cs.join()
+    torch.cuda.synchronize()
