@@ -28,7 +28,7 @@ constexpr int kLocMaxBlocksX = 32;
 // is small enough for the plane to stay in L2 between passes (12 Mpx = 48 MB).
 constexpr int64_t kU8PlaneMaxPixels = int64_t(12) << 20;
 constexpr int kLocMaxCols = 1024;
-constexpr int kCdfChunk = 16;
+constexpr int kCdfMaxChunk = 64;  // block columns of a window-CDF tile, at most (shared-memory staging)
 
 std::mutex g_mu;
 // tile_cols 0: sized per launch so the pass's tiles split evenly over the CTAs
@@ -184,6 +184,22 @@ int local_tile_cols(int s, int want)
     return l * m;
 }
 
+// Block columns per window-CDF tile.  The pass is latency-bound: a tile waits for
+// its L2 loads (the block histograms of 2R + 1 block rows) before its scans, and a
+// CTA's tiles follow one another.  So the narrowest chunk whose tiles all fit the
+// persistent grid at once wins (more tiles, shorter ones); when even the widest
+// needs several rounds, the widest (the fewest rounds).
+int cdf_cols_auto(const std::vector<std::pair<int, int>>& hbwb, int64_t slots)
+{
+    static const int cand[] = {16, 24, 32, 48, kCdfMaxChunk};
+    for (int c : cand) {
+        int64_t T = 0;
+        for (const auto& d : hbwb) T += (int64_t)d.first * ((d.second + c - 1) / c);
+        if (T <= slots) return c;
+    }
+    return kCdfMaxChunk;
+}
+
 // Local tile width when none is tuned: among the widths above, the one whose tiles
 // spread most evenly over the persistent grid.  Model: CTA c takes tiles c,
 // c + grid, ... and a tile costs its pixels plus 3/4 of a block for the curve
@@ -326,7 +342,7 @@ int phase_list(const OpArgs& op, bool ldr, int32_t* kinds)
 
 void make_geometry(const dc_image_in& in, const dc_image_out& out, const OpArgs& op, const dc_tuning& tu,
                    int n_phase, const int32_t* kinds, Geometry& g, int tile_rows, int tile_cols, int loc_cols,
-                   bool u8_plane)
+                   int cdf_cols, bool u8_plane)
 {
     DcImage& im = g.im;
     std::memset(&im, 0, sizeof(im));
@@ -382,7 +398,7 @@ void make_geometry(const dc_image_in& in, const dc_image_out& out, const OpArgs&
     (void)tu;
     for (int p = 0; p < n_phase; ++p) {
         if (op.opk == kOpkLocal)
-            g.tiles[p] = kinds[p] == PK_CDF ? im.Hb * ((im.Wb + kCdfChunk - 1) / kCdfChunk) : im.Hb * im.tiles_x_loc;
+            g.tiles[p] = kinds[p] == PK_CDF ? im.Hb * ((im.Wb + cdf_cols - 1) / cdf_cols) : im.Hb * im.tiles_x_loc;
         else
             g.tiles[p] = tiles_y * im.tiles_x;
     }
@@ -439,6 +455,13 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
             b->loc_tile_cols = local_tile_cols_auto(op.l->block_s, hw, nsm,
                                                     tu.ctas_per_sm > 0 ? tu.ctas_per_sm : kAutoCtasPerSm);
         }
+        std::vector<std::pair<int, int>> hbwb(n);
+        const int s = op.l->block_s;
+        for (int k = 0; k < n; ++k)
+            hbwb[k] = {(in[idx[k]].height + s - 1) / s, (in[idx[k]].width + s - 1) / s};
+        int nsm = 152, dev = 0;
+        if (launch && cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        b->cdf_cols = cdf_cols_auto(hbwb, (int64_t)nsm * (tu.ctas_per_sm > 0 ? tu.ctas_per_sm : kAutoCtasPerSm));
     }
     b->beta_r = p->beta_r;
     b->beta_k = p->beta_k;
@@ -481,7 +504,7 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
     std::vector<Geometry> geo(n);
     for (int k = 0; k < n; ++k) {
         make_geometry(in[idx[k]], out[idx[k]], op, tu, b->n_phase, b->phase_kind, geo[k], b->tile_rows,
-                      b->tile_cols, b->loc_tile_cols, u8_plane);
+                      b->tile_cols, b->loc_tile_cols, b->cdf_cols, u8_plane);
         geo[k].im.ws_hist = off;
         off += geo[k].local_bytes;
         if (geo[k].plane_bytes > 0) {

@@ -24,7 +24,7 @@ namespace dc {
 
 constexpr int kThreads = 256;
 constexpr int kLocMaxBlocksX = 32;    // max blocks per local tile row
-constexpr int kCdfChunk = 16;         // block columns per CDF tile
+constexpr int kCdfMaxChunk = 64;      // block columns per CDF tile, at most
 constexpr int kMaxRadius = 16;
 
 template <int IN_DT> struct InT;
@@ -974,7 +974,7 @@ struct SmemBlockH {
     uint32_t fs[kLocMaxBlocksX * (DC_MAX_BINS + 8)];   // their upper-bin fractions, units of 2^-20
 };
 struct SmemCdf {
-    unsigned long long v[(kCdfChunk + 2 * kMaxRadius) * DC_MAX_BINS];
+    unsigned long long v[(kCdfMaxChunk + 2 * kMaxRadius) * DC_MAX_BINS];
 };
 constexpr int kLocMaxCols = 1024;    // widest local tile
 // Geometry of the apply pass's curve table, fixed at compile time so that the four

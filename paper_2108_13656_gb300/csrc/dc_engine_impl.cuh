@@ -57,17 +57,17 @@ struct Unroll {
 };
 
 // ------------------------------------------------------------ tile geometry ---
-template <int OPK, int CAP>
-__device__ __forceinline__ int cdf_cols_tiles(const DcImage& im)
+template <int CAP>
+__device__ __forceinline__ int cdf_cols_tiles(const DcBatch<CAP>& P, const DcImage& im)
 {
-    return (im.Wb + kCdfChunk - 1) / kCdfChunk;
+    return (im.Wb + P.cdf_cols - 1) / P.cdf_cols;
 }
 
 template <int OPK, int CAP>
 __device__ __forceinline__ int phase_tiles(const DcBatch<CAP>& P, const DcImage& im, int kind)
 {
     if constexpr (OPK == OPK_LOCAL) {
-        return kind == PK_CDF ? im.Hb * cdf_cols_tiles<OPK, CAP>(im) : im.Hb * im.tiles_x_loc;
+        return kind == PK_CDF ? im.Hb * cdf_cols_tiles(P, im) : im.Hb * im.tiles_x_loc;
     } else {
         return ((im.rows + P.tile_rows - 1) / P.tile_rows) * im.tiles_x;
     }
@@ -89,11 +89,11 @@ __device__ __forceinline__ TileRect tile_rect(const DcBatch<CAP>& P, const DcIma
             tr.c0 = tx * P.loc_tile_cols;
             tr.c1 = min(tr.c0 + P.loc_tile_cols, im.pcol);
         } else {
-            const int ncc = cdf_cols_tiles<OPK, CAP>(im);
+            const int ncc = cdf_cols_tiles(P, im);
             I = lt / ncc;
             tr.r0 = tr.r1 = 0;
-            tr.c0 = (lt - I * ncc) * kCdfChunk;
-            tr.c1 = min(tr.c0 + kCdfChunk, im.Wb);
+            tr.c0 = (lt - I * ncc) * P.cdf_cols;
+            tr.c1 = min(tr.c0 + P.cdf_cols, im.Wb);
         }
     } else {
         const int ty = lt / im.tiles_x;

@@ -133,6 +133,7 @@ struct DcBatch {
     int32_t phase_kind[kMaxPhases];
     int32_t tile_rows, tile_cols;      // pixelwise phases
     int32_t loc_tile_cols;             // local phases (tile height = block_s)
+    int32_t cdf_cols;                  // block columns per window-CDF tile (<= kCdfMaxChunk)
     float beta_r, beta_k;
     int32_t ldr;                       // 8-bit input
     int32_t mode;                      // DC_SIGMOID / DC_HISTEQ
