@@ -301,10 +301,10 @@ DC_API int dc_decolorize_tonemap_global_noalloc(const dc_image_in* in, const dc_
  * NULL (DC_OP_DECOLORIZE, DC_OP_GLOBAL) or a dc_local_params* (DC_OP_LOCAL).
  * Returns 0 when the arguments are invalid.  The workspace must be 256-byte
  * aligned; its contents need no initialisation (each call resets what it uses).
- * For 8-bit input of up to 12 Mpx per call (per input sample type) the size
- * includes an f32 luminance plane (4 bytes per pixel) that spares the later passes
- * from recomputing Eq. 1-6; a call given less (down to dc_workspace_min_bytes)
- * runs without it, with identical results. */
+ * For 8-bit input (global and local tone mapping, gray output) the size includes
+ * an f32 luminance plane (4 bytes per pixel) that spares the later passes from
+ * recomputing Eq. 1-6; a call given less (down to dc_workspace_min_bytes) runs
+ * without it, with identical results. */
 DC_API size_t dc_workspace_bytes(int32_t op, const dc_image_in* in, int32_t n,
                                  const void* op_params);
 

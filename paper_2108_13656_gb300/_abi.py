@@ -227,14 +227,17 @@ def _stream_handle(stream):
 class Workspace:
     """Device workspace owned by torch's allocator (256-byte aligned): grown on demand
     to what each call asks for, or, when created with `nbytes`, exactly that size and
-    never grown (a call then keeps its optional planes only if they fit).  Each buffer
-    is registered with dc_workspace_prepare (calls keep its control block clean, no
-    per-call clearing memset) and released before it is dropped."""
+    never grown (a call then keeps its optional planes only if they fit).  With
+    `optional=False` it grows only to a call's least need (dc_workspace_min_bytes),
+    so that the optional 8-bit plane is used only while it fits the current size.
+    Each buffer is registered with dc_workspace_prepare (calls keep its control block
+    clean, no per-call clearing memset) and released before it is dropped."""
 
-    def __init__(self, device=None, nbytes: int | None = None):
+    def __init__(self, device=None, nbytes: int | None = None, optional: bool = True):
         self.device = device
         self.buf = None
         self.fixed = nbytes is not None
+        self.optional = optional
         if self.fixed:
             self._set(_torch().empty(max(int(nbytes), 256), dtype=_torch().uint8, device=device or "cuda"))
 
@@ -249,9 +252,12 @@ class Workspace:
         if rc != DC_OK:
             raise DcError(rc, "dc_workspace_prepare")
 
-    def get(self, nbytes: int):
+    def get(self, nbytes: int, min_bytes: int | None = None):
+        """The buffer for a call that asks for `nbytes` (and accepts `min_bytes`)."""
         torch = _torch()
         nbytes = max(int(nbytes), 256)
+        if not self.optional and min_bytes is not None and self.buf is not None:
+            nbytes = max(int(min_bytes), 256)
         if not self.fixed and (self.buf is None or self.buf.numel() < nbytes):
             self._set(torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device or "cuda"))
         ptr = self.buf.data_ptr()
@@ -278,7 +284,10 @@ def _workspace(op, ins, n, lp, ws):
         torch = _torch()
         dev = torch.cuda.current_device()
         ws = _default_ws.setdefault(dev, Workspace(device="cuda:%d" % dev))
-    ptr, size = ws.get(need)
+    least = None
+    if not getattr(ws, "optional", True):  # (any object with get() serves as a workspace)
+        least = lib.dc_workspace_min_bytes(op, ins, n, ctypes.byref(lp) if lp is not None else None)
+    ptr, size = ws.get(need, least) if least is not None else ws.get(need)
     return ptr, size, ws.buf
 
 

@@ -24,9 +24,6 @@ constexpr int64_t kHeaderBytes = 256;
 constexpr int64_t kMaxPixels = int64_t(1) << 28;
 constexpr int kMaxLocalSide = 1 << 16;
 constexpr int kLocMaxBlocksX = 32;
-// 8-bit input keeps an f32 luminance plane in the workspace when the launch group
-// is small enough for the plane to stay in L2 between passes (12 Mpx = 48 MB).
-constexpr int64_t kU8PlaneMaxPixels = int64_t(12) << 20;
 constexpr int kLocMaxCols = 1024;
 constexpr int kCdfMaxChunk = 64;  // block columns of a window-CDF tile, at most (shared-memory staging)
 
@@ -413,13 +410,12 @@ int build_and_launch(const dc_image_in* in, const dc_image_out* out, const std::
     const int in_dt = in[idx[0]].dtype;
     const bool ldr = in_dt == DC_U8;
     bool u8_plane = false;
-    // (not for colour outputs, whose apply pass re-reads RGB anyway, nor for a frame of
-    // a running sequence, which is a single pass)
-    if (allow_u8_plane && ldr && op.opk != kOpkDecolor && !color && !(op.video() && !op.restart)) {
-        int64_t px = 0;
-        for (int k = 0; k < n; ++k) px += (int64_t)in[idx[k]].width * in[idx[k]].height;
-        u8_plane = px <= kU8PlaneMaxPixels;
-    }
+    // 8-bit input keeps an f32 luminance plane in the workspace, whatever the launch
+    // group's size: the later passes are bound by instruction issue, so reading 4
+    // bytes a pixel (from L2, or from DRAM once the plane outgrows L2) beats
+    // recomputing Eq. 1-6 from the 3 RGB bytes.  (Not for colour outputs, whose apply
+    // pass re-reads RGB anyway, nor for a frame of a running sequence, a single pass.)
+    if (allow_u8_plane && ldr && op.opk != kOpkDecolor && !color && !(op.video() && !op.restart)) u8_plane = true;
     plane = plane || u8_plane;
     dc_tuning tu;
     {

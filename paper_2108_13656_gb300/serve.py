@@ -305,9 +305,11 @@ def serve_batched(trace, pool: HostPool, budget_bytes: int = 16 << 30, n_streams
     import torch
     dev = torch.device(device or "cuda")
     streams = [torch.cuda.Stream(device=dev) for _ in range(n_streams)]
-    wss = [_abi.Workspace(device=dev) for _ in range(n_streams)]
+    # sized up front and grown only when a batch's least need exceeds it (growing
+    # inside the loop would allocate); the optional 8-bit plane is used while it fits
+    wss = [_abi.Workspace(device=dev, optional=False) for _ in range(n_streams)]
     for w in wss:
-        w.get(WORKSPACE_BYTES)  # sized up front: growing it inside the loop would allocate
+        w.get(WORKSPACE_BYTES)
     adm = Admission(budget_bytes, reserved_bytes=sum(w.buf.numel() for w in wss), max_batch=max_batch,
                     inflight_cap=inflight_cap)
     outpool, devpool = pool.outpool, pool.devpool

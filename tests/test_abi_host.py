@@ -88,9 +88,10 @@ def test_workspace_bytes_sizes(abi):
         lib.dc_workspace_min_bytes(abi.DC_OP_DECOLORIZE, ins, 1, None)
     hdr = (abi.dc_image_in * 1)(_img(3840, 2160, dt=abi.DC_F32))
     assert lib.dc_workspace_bytes(abi.DC_OP_GLOBAL, hdr, 1, None) == lib.dc_workspace_min_bytes(abi.DC_OP_GLOBAL, hdr, 1, None)
-    # above 12 Mpx per call the 8-bit plane is not kept
+    # the 8-bit plane is asked for whatever the size (optional: the minimum omits it)
     big = (abi.dc_image_in * 1)(_img(4096, 3200))
-    assert lib.dc_workspace_bytes(abi.DC_OP_GLOBAL, big, 1, None) == lib.dc_workspace_min_bytes(abi.DC_OP_GLOBAL, big, 1, None)
+    assert lib.dc_workspace_bytes(abi.DC_OP_GLOBAL, big, 1, None) >= \
+        lib.dc_workspace_min_bytes(abi.DC_OP_GLOBAL, big, 1, None) + 4096 * 3200 * 4
     assert lib.dc_workspace_bytes(7, ins, 1, None) == 0
     many = (abi.dc_image_in * 300)(*[_img(64 + i, 32) for i in range(300)])
     assert lib.dc_workspace_bytes(abi.DC_OP_GLOBAL, many, 300, None) > 0
