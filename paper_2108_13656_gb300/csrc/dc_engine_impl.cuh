@@ -1026,25 +1026,34 @@ __device__ void tile_cdf(const DcBatch<CAP>& P, const DcImage& im, const DcImgCt
     const int lo = max(0, J0 - R), hi = min(Wb, t.c1 + R);
     const int ncol = hi - lo;
     // column sums over the window's block rows: a warp per staged column and a lane
-    // per bin (B <= 32), two columns per round so that their loads are in flight
-    // together; no integer division
+    // per bin (B <= 32), three columns per round so that their loads are in flight
+    // together (the 16 + 2R columns of a default tile take one round); no integer
+    // division
     {
-        constexpr int NW = kThreads / 32;
+        constexpr int NW = kThreads / 32, NC = 3;
         const size_t rs = (size_t)Wb * B;
         if (lane < B) {
-            for (int c0 = warp; c0 < ncol; c0 += 2 * NW) {
-                const int c1 = c0 + NW;
-                const bool has1 = c1 < ncol;
-                const unsigned long long* q0 = H + ((size_t)i0 * Wb + lo + c0) * B + lane;
-                const unsigned long long* q1 = H + ((size_t)i0 * Wb + lo + (has1 ? c1 : c0)) * B + lane;
-                unsigned long long v0 = 0ull, v1 = 0ull;
-#pragma unroll 5
-                for (int I2 = i0; I2 <= i1; ++I2, q0 += rs, q1 += rs) {
-                    v0 += bc_ok(q0, 8, P.ws, P.ws_bytes, BC_WS) ? ld_cg_u64(q0) : 0ull;
-                    v1 += (has1 && bc_ok(q1, 8, P.ws, P.ws_bytes, BC_WS)) ? ld_cg_u64(q1) : 0ull;
+            for (int c0 = warp; c0 < ncol; c0 += NC * NW) {
+                // column c0 + h NW sits h NW B entries after column c0
+                const unsigned long long* q = H + ((size_t)i0 * Wb + lo + c0) * B + lane;
+                bool has[NC];
+                unsigned long long v[NC];
+#pragma unroll
+                for (int h = 0; h < NC; ++h) {
+                    has[h] = c0 + h * NW < ncol;
+                    v[h] = 0ull;
                 }
-                S.v[c0 * B + lane] = v0;
-                if (has1) S.v[c1 * B + lane] = v1;
+#pragma unroll 5
+                for (int I2 = i0; I2 <= i1; ++I2, q += rs) {
+#pragma unroll
+                    for (int h = 0; h < NC; ++h) {
+                        const unsigned long long* qh = q + h * NW * B;
+                        v[h] += (has[h] && bc_ok(qh, 8, P.ws, P.ws_bytes, BC_WS)) ? ld_cg_u64(qh) : 0ull;
+                    }
+                }
+#pragma unroll
+                for (int h = 0; h < NC; ++h)
+                    if (has[h]) S.v[(c0 + h * NW) * B + lane] = v[h];
             }
         }
     }
