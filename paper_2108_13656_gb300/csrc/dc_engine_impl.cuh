@@ -488,16 +488,21 @@ __device__ void tile_stats(const DcBatch<CAP>& P, const DcImage& im, DcImgCtrl* 
     consume_tile<IN_DT, false>(im, t, be, [&](int r, int c, int n, bool vec, float (&Lv)[G]) __attribute__((always_inline)) {
         float v[G];
         if constexpr (LOGQ) {
+            auto px = [&](int k) __attribute__((always_inline)) {
+                const int q = ln_q24(Lv[k] + delta);
+                if constexpr (SUM) acc += q;
+                qmin = min(qmin, q);
+                qmax = max(qmax, q);
+                v[k] = __int_as_float(q);
+            };
+            if (n == G) {  // a full group (the common case) without a guard per pixel
 #pragma unroll
-            for (int k = 0; k < G; ++k) {
-                if (k < n) {
-                    const int q = ln_q24(Lv[k] + delta);
-                    if constexpr (SUM) acc += q;
-                    qmin = min(qmin, q);
-                    qmax = max(qmax, q);
-                    v[k] = __int_as_float(q);
-                } else {
-                    v[k] = 0.0f;
+                for (int k = 0; k < G; ++k) px(k);
+            } else {
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                    if (k < n) px(k);
+                    else v[k] = 0.0f;
                 }
             }
             if (plane_out) GroupIO<IN_DT>::store_plane(im, r, c, n, vec, plane_log ? v : Lv);
@@ -910,40 +915,47 @@ __device__ void tile_blockh(const DcBatch<CAP>& P, const DcImage& im, const Tile
         const int blk0 = group_in_block ? (int)__umulhi((uint32_t)(c - t.c0), magic) : 0;
         int cur = -1;
         uint32_t rc = 0u, rf = 0u;
-#pragma unroll
-        for (int k = 0; k < G; ++k) {
-            if (k < n) {
-                int x;
-                if (PREC) {
-                    // t - 1/2 from 2^-24 to 2^-20 units, rounded (as for HDR input)
-                    x = min(max(((int)__float_as_uint(qv[k]) - (1 << (kLocTS - 1)) + 8) >> (kLocTS - 20), 0), xmax);
-                } else if (ldr) {
-                    x = min(max(__float2int_rn(fmaf(fminf(fmaxf(Lv[k], 0.0f), 1.0f), scale, -524288.0f)), 0), xmax);
-                } else {
-                    // t - 1/2 from 2^-24 to 2^-20 units, rounded
-                    const uint32_t q = coord_of<kLocTS>(Lv[k], is_log, delta, d);
-                    x = min(max(((int)q - (1 << (kLocTS - 1)) + 8) >> (kLocTS - 20), 0), xmax);
-                }
-                int blk = blk0;
-                if (!group_in_block) {
-                    const uint32_t off = (uint32_t)(c + k - t.c0);
-                    blk = magic ? (int)__umulhi(off, magic) : (int)off;
-                }
-                const int key = blk * BS + (x >> 20);
-                const uint32_t f = (uint32_t)x & 0xFFFFFu;
-                if (key == cur) {
-                    ++rc;
-                    rf += f;
-                } else {
-                    if (cur >= 0) {
-                        atomicAdd(&S.cnt[cur], rc);
-                        atomicAdd(&S.fs[cur], rf);
-                    }
-                    cur = key;
-                    rc = 1u;
-                    rf = f;
-                }
+        auto px = [&](int k) __attribute__((always_inline)) {
+            int x;
+            if (PREC) {
+                // t - 1/2 from 2^-24 to 2^-20 units, rounded (as for HDR input)
+                x = min(max(((int)__float_as_uint(qv[k]) - (1 << (kLocTS - 1)) + 8) >> (kLocTS - 20), 0), xmax);
+            } else if (ldr) {
+                x = min(max(__float2int_rn(fmaf(fminf(fmaxf(Lv[k], 0.0f), 1.0f), scale, -524288.0f)), 0), xmax);
+            } else {
+                // t - 1/2 from 2^-24 to 2^-20 units, rounded
+                const uint32_t q = coord_of<kLocTS>(Lv[k], is_log, delta, d);
+                x = min(max(((int)q - (1 << (kLocTS - 1)) + 8) >> (kLocTS - 20), 0), xmax);
             }
+            int blk = blk0;
+            if (!group_in_block) {
+                const uint32_t off = (uint32_t)(c + k - t.c0);
+                blk = magic ? (int)__umulhi(off, magic) : (int)off;
+            }
+            const int key = blk * BS + (x >> 20);
+            const uint32_t f = (uint32_t)x & 0xFFFFFu;
+            if (key == cur) {
+                ++rc;
+                rf += f;
+            } else {
+                if (cur >= 0) {
+                    atomicAdd(&S.cnt[cur], rc);
+                    atomicAdd(&S.fs[cur], rf);
+                }
+                cur = key;
+                rc = 1u;
+                rf = f;
+            }
+        };
+        // an RGB walk's full group (the common case) without a guard per pixel (for
+        // the plane walk this measured slower)
+        if (!PLANE && n == G) {
+#pragma unroll
+            for (int k = 0; k < G; ++k) px(k);
+        } else {
+#pragma unroll
+            for (int k = 0; k < G; ++k)
+                if (k < n) px(k);
         }
         if (cur >= 0) {
             atomicAdd(&S.cnt[cur], rc);
