@@ -343,3 +343,41 @@ def test_local_video_arguments_validated(abi):
     narrow = (abi.dc_image_out * 1)(abi.dc_image_out(1 << 24, 1199, 2, 3))
     assert call(ins, narrow, 1, ctypes.byref(p), ctypes.byref(lp), 1, ctypes.c_void_p(st), need, ws, 1 << 20,
                 None) == abi.DC_ERR_INVALID_ARG
+
+
+def test_workspace_growth_rules_without_a_device():
+    # the sizes a Workspace grows to, with a small host buffer standing in for device
+    # memory: optional=False (the serving loop) grows only to a call's least need, so
+    # the optional 8-bit plane is used only while it fits; the default grows to the
+    # size the call asks for
+    from paper_2108_13656_gb300 import _abi
+
+    class FakeBuf:
+        def __init__(self, n):
+            self.n = n
+
+        def numel(self):
+            return self.n
+
+        def data_ptr(self):
+            return 1 << 20
+
+    def make(optional):
+        w = _abi.Workspace.__new__(_abi.Workspace)
+        w.device, w.buf, w.fixed, w.optional = "cpu", None, False, optional
+        w._set = lambda buf: setattr(w, "buf", FakeBuf(buf.numel()))
+        return w
+
+    K = 1 << 10
+    w = make(optional=False)
+    w.get(128 * K)                     # sized up front
+    n0 = w.buf.numel()
+    assert n0 >= 128 * K
+    w.get(400 * K, 64 * K)             # asks for more, accepts less than it holds: no growth
+    assert w.buf.numel() == n0
+    w.get(400 * K, 200 * K)            # its least need is more: grows to that, not to what it asks
+    assert 200 * K <= w.buf.numel() < 400 * K
+    g = make(optional=True)
+    g.get(128 * K)
+    g.get(400 * K, 64 * K)
+    assert g.buf.numel() >= 400 * K
