@@ -106,7 +106,8 @@ class CallStreams:
     enqueued on the side streams.  Calls on one side stream run in order; calls on
     different side streams may overlap, so they must not share a workspace or write
     a buffer another one reads - `run` refuses a workspace already used on another
-    side stream since the last fork."""
+    side stream since the last join (after a join, and a fork from the joined stream,
+    every side stream's earlier work is ordered before the new calls)."""
 
     def __init__(self, n: int, device=None):
         import torch
@@ -123,7 +124,6 @@ class CallStreams:
         ev.record(src)
         for s in self.streams:
             s.wait_event(ev)
-        self._owner = {}
 
     def run(self, i: int, call):
         ws = getattr(call, "ws_ptr", None)  # the device address of a PreparedCall's workspace
@@ -139,3 +139,4 @@ class CallStreams:
             ev = torch.cuda.Event()
             ev.record(s)
             dst.wait_event(ev)
+        self._owner = {}

@@ -235,7 +235,7 @@ def test_call_streams_rejects_zero_streams():
 
 def test_call_streams_workspace_ownership_without_a_device():
     # run() checks the workspace before it touches a stream: a fake call whose
-    # workspace address is taken by another side stream is refused, and fork()
+    # workspace address is taken by another side stream is refused until a join
     # (emulated by clearing the table) releases it
     from paper_2108_13656_gb300.pipeline import CallStreams
     cs = CallStreams.__new__(CallStreams)

@@ -112,4 +112,8 @@ def test_call_streams_refuse_a_shared_workspace(dc):
     with pytest.raises(ValueError):
         cs.run(1, a)
     cs.join()
+    cs.fork()  # after a join every earlier call is ordered before the new ones
+    cs.run(1, a)
+    cs.join()
     torch.cuda.synchronize()
+    assert dc.query_status(w) == 0
